@@ -1,0 +1,340 @@
+"""Pins of the oracle's group walk, force and leapfrog.
+
+Anchors: theta -> 0 collapsing the tree onto the direct sum; coverage of
+every particle exactly once; a brute-force, non-recursive reconstruction of
+the lists from the opening predicate; a hand-built opening case; the
+two-body closed form; momentum conservation; the analytic Plummer and
+Hernquist fields; the convergence order of the multipole expansion and
+a = -grad(phi); time reversibility of the leapfrog.
+"""
+import numpy as np
+import pytest
+
+import ics
+import oracle
+
+
+def _parents(nd):
+    parent = np.full(len(nd["level"]), -1)
+    for i in np.nonzero(nd["child_first"] >= 0)[0]:
+        parent[nd["child_first"][i]:nd["child_first"][i] + nd["nchild"][i]] = i
+    return parent
+
+
+def _clustered(n, seed):
+    rng = np.random.default_rng(seed)
+    pos = rng.normal(size=(n, 3)) * rng.uniform(0.05, 1.0, (n, 1))
+    return pos, rng.uniform(0.5, 1.5, n) / n, np.full(n, 0.02)
+
+
+def test_theta_zero_opens_everything():
+    pos, m, e = _clustered(600, 1)
+    t = oracle.Tree(pos, m, e, theta=0.0, n_leaf=4, n_grp=32)
+    for g in range(t.n_groups):
+        epj, spj = t.walk(g)
+        assert len(spj) == 0
+        np.testing.assert_array_equal(np.sort(epj), np.arange(600))
+
+
+@pytest.mark.parametrize("theta,quad", [(0.3, False), (0.5, True), (0.7, True), (1.2, False)])
+def test_every_particle_covered_once(theta, quad):
+    pos, m, e = _clustered(3000, 2)
+    t = oracle.Tree(pos, m, e, theta=theta, n_leaf=8, n_grp=64, quad=quad)
+    nd = t.nodes()
+    for g in range(0, t.n_groups, 3):
+        epj, spj = t.walk(g)
+        cover = np.zeros(3000, np.int64)
+        np.add.at(cover, epj, 1)
+        for c in spj:
+            cover[nd["first"][c]:nd["first"][c] + nd["count"][c]] += 1
+        assert np.all(cover == 1)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_lists_equal_brute_force_characterisation(seed):
+    """A cell is an SPJ of group g iff every proper ancestor is opened and it
+    is not; a particle is an EPJ iff its leaf and all the leaf's ancestors
+    are opened.  Checked node by node, without a traversal."""
+    n = 64
+    pos, m, e = _clustered(n, 100 + seed)
+    t = oracle.Tree(pos, m, e, theta=[0.3, 0.5, 0.7, 0.9, 0.4, 0.6][seed], n_leaf=2, n_grp=8)
+    nd = t.nodes()
+    par = _parents(nd)
+    for g in range(t.n_groups):
+        opened = np.array([t.open_cell(c, g) for c in range(t.n_nodes)])
+        anc_open = np.ones(t.n_nodes, bool)
+        for c in range(1, t.n_nodes):  # BFS order: parents come first
+            anc_open[c] = anc_open[par[c]] and opened[par[c]]
+        want_spj = np.nonzero(anc_open & ~opened)[0]
+        leaf = nd["child_first"] < 0
+        want_epj = np.concatenate([np.arange(nd["first"][c], nd["first"][c] + nd["count"][c])
+                                   for c in np.nonzero(anc_open & opened & leaf)[0]] + [np.zeros(0, int)])
+        epj, spj = t.walk(g)
+        np.testing.assert_array_equal(np.sort(spj), want_spj)
+        np.testing.assert_array_equal(np.sort(epj), np.sort(want_epj))
+
+
+def test_accepted_cells_never_meet_the_group_box():
+    pos, m, e = _clustered(4000, 3)
+    t = oracle.Tree(pos, m, e, theta=0.9, n_leaf=8, n_grp=64)
+    nd = t.nodes()
+    g = t.groups()
+    for k in range(0, t.n_groups, 5):
+        _, spj = t.walk(k)
+        qmin, qmax = g["qbox"][k, :3].astype(np.int64), g["qbox"][k, 3:].astype(np.int64)
+        for c in spj:
+            lev, pre = int(nd["level"][c]), int(nd["prefix"][c])
+            lo = np.zeros(3, np.int64)
+            for b in range(lev):  # de-interleave the prefix digits
+                for ax in range(3):
+                    lo[ax] |= ((pre >> (3 * b + 2 - ax)) & 1) << b
+            lo <<= 21 - lev
+            hi = lo + (1 << (21 - lev)) - 1
+            assert np.any((lo > qmax) | (hi < qmin))
+
+
+def test_opening_angle_threshold_hand_built():
+    """Group A: 4 particles near the origin; cluster B: 4 particles near
+    (1, 0, 0) filling the level-1 cell [0.5, 1] x [0, 0.5] x [0, 0.5] of the
+    root cube [0, 1]^3 (the set spans the unit cube).  B's level-1 cell has
+    side 1/2 and its COM is B's mean position; with n_grp = 4 group A is the
+    first group.  The cell is accepted exactly when 1/2 < theta * d, d the
+    gap between B's COM and A's box along x (the other axes overlap)."""
+    A = np.array([[0.0, 0.0, 0.0], [0.01, 0.02, 0.0], [0.02, 0.0, 0.01], [0.0, 0.01, 0.02]])
+    B = np.array([[0.98, 0.02, 0.01], [1.0, 0.0, 0.0], [0.97, 0.01, 0.02], [0.99, 0.0, 0.01]])
+    C = np.array([[0.01, 0.98, 0.99], [0.0, 1.0, 1.0], [0.02, 0.99, 0.98], [0.01, 0.97, 1.0]])
+    pos = np.concatenate([A, B, C])
+    m = np.ones(12)
+    comB = B.mean(0)
+    d = comB[0] - A[:, 0].max()
+    for theta, accepted in [(0.5 / d * 1.001, True), (0.5 / d * 0.999, False)]:
+        t = oracle.Tree(pos, m, np.full(12, 0.01), theta=theta, n_leaf=4, n_grp=4)
+        nd = t.nodes()
+        cellB = [c for c in range(t.n_nodes) if nd["level"][c] == 1 and nd["count"][c] == 4
+                 and np.allclose(nd["com"][c], comB)]
+        assert len(cellB) == 1
+        g = t.groups()
+        ga = int(np.nonzero(g["first"] == 0)[0][0])
+        _, spj = t.walk(ga)
+        assert (cellB[0] in spj) == accepted
+
+
+def test_large_theta_opens_only_cells_meeting_the_box():
+    pos, m, e = _clustered(2000, 4)
+    t = oracle.Tree(pos, m, e, theta=1e6, n_leaf=8, n_grp=64)
+    nd = t.nodes()
+    par = _parents(nd)
+    for k in range(0, t.n_groups, 7):
+        epj, spj = t.walk(k)
+        # every list entry's parent was opened and met the box; SPJ cells did not
+        leaf_of = {}
+        for c in np.nonzero(nd["child_first"] < 0)[0]:
+            for p in range(nd["first"][c], nd["first"][c] + nd["count"][c]):
+                leaf_of[p] = c
+        for c in spj:
+            assert not t.open_cell(c, k)
+        for p in epj:
+            assert t.open_cell(leaf_of[p], k)
+        assert len(spj) > 0
+
+
+def test_two_body_closed_form():
+    r, eps, m1, m2 = 0.75, 0.1, 0.3, 1.7
+    pos = np.array([[0.0, 0.0, 0.0], [r, 0.0, 0.0]])
+    mass = np.array([m1, m2])
+    e = np.full(2, eps)
+    acc, pot = oracle.direct(pos, mass, e)
+    f = (r * r + eps * eps) ** -1.5
+    np.testing.assert_allclose(acc[0], [m2 * r * f, 0, 0], rtol=1e-15)
+    np.testing.assert_allclose(acc[1], [-m1 * r * f, 0, 0], rtol=1e-15)
+    np.testing.assert_allclose(pot, [-m2 / np.hypot(r, eps), -m1 / np.hypot(r, eps)], rtol=1e-15)
+    t = oracle.Tree(pos, mass, e, theta=0.5, n_leaf=1, n_grp=1)
+    a2, p2, _ = t.force()
+    np.testing.assert_allclose(a2, acc, rtol=1e-15, atol=1e-300)
+    np.testing.assert_allclose(p2, pot, rtol=1e-14)
+
+
+def test_direct_sum_conserves_momentum():
+    pos, m, _ = _clustered(2000, 5)
+    e = np.full(2000, 0.01)
+    acc, _ = oracle.direct(pos, m, e)
+    scale = (m[:, None] * np.abs(acc)).sum()
+    assert np.abs((m[:, None] * acc).sum(0)).max() < 1e-13 * scale
+
+
+@pytest.mark.parametrize("quad", [False, True])
+def test_theta_zero_tree_equals_direct_sum(quad):
+    pos, m, e = _clustered(1500, 6)
+    e = np.random.default_rng(0).uniform(0.005, 0.05, 1500)  # per-particle softening
+    t = oracle.Tree(pos, m, e, theta=0.0, n_leaf=4, n_grp=16, quad=quad)
+    acc, pot, tot = t.force()
+    ad, pd = oracle.direct(pos, m, e)
+    assert tot[1] == 0 and tot[0] == t.n_groups * 1500 and tot[2] == 1500 * 1500
+    np.testing.assert_allclose(acc, ad, rtol=1e-11, atol=1e-12 * np.abs(ad).max())
+    np.testing.assert_allclose(pot, pd, rtol=1e-11)
+
+
+def _shells(r, val, per):
+    o = np.argsort(r)
+    k = len(r) // per
+    rs = r[o][: k * per].reshape(k, per)
+    vs = val[o][: k * per].reshape(k, per)
+    return rs.mean(1), vs.mean(1), vs.std(1) / np.sqrt(per)
+
+
+def test_direct_sum_matches_plummer_field():
+    n = 1 << 15
+    pos, vel, mass = ics.plummer(n, 42)
+    eps = np.full(n, 1e-3)
+    acc, pot = oracle.direct(pos, mass, eps)
+    r = np.linalg.norm(pos, axis=1)
+    ar = (acc * pos).sum(1) / r
+    norm = 22.8 ** 3 / (22.8 ** 2 + 1) ** 1.5
+    # compare shell means of (measured - analytic at each particle's radius)
+    rr, dm, de = _shells(r, ar + r / (r * r + 1) ** 1.5 / norm, 1024)
+    _, am, _ = _shells(r, r / (r * r + 1) ** 1.5 / norm, 1024)
+    sel = (rr > 0.2) & (rr < 5)
+    assert np.all(np.abs(dm[sel]) < 5 * de[sel] + 0.01 * am[sel])
+    rr, pm, _ = _shells(r, pot + 1 / np.sqrt(r * r + 1) / norm, 1024)
+    _, pw, _ = _shells(r, 1 / np.sqrt(r * r + 1) / norm, 1024)
+    sel = rr < 5
+    assert np.all(np.abs(pm[sel]) < 0.01 * pw[sel])
+
+
+def test_direct_sum_matches_hernquist_field():
+    n = 1 << 15
+    pos, vel, mass = ics.hernquist(n, 43)
+    acc, _ = oracle.direct(pos, mass, np.full(n, 1e-3))
+    r = np.linalg.norm(pos, axis=1)
+    ar = (acc * pos).sum(1) / r
+    xmax = (100 / 101) ** 2
+    rr, dm, de = _shells(r, ar + 1.0 / (xmax * (r + 1) ** 2), 1024)
+    _, am, _ = _shells(r, 1.0 / (xmax * (r + 1) ** 2), 1024)
+    sel = (rr > 0.25) & (rr < 10)  # inside ~0.2 the cusp holds too few particles
+    assert np.all(np.abs(dm[sel]) < 5 * de[sel] + 0.01 * am[sel])
+
+
+def test_multipole_expansion_convergence_order():
+    """Exact field of an asymmetric particle cluster of size ~1 versus its
+    monopole and quadrupole superparticle at distance d: the monopole error
+    (the quadrupole term) falls as d^-4, the quadrupole error (octupole) as
+    d^-5 -- a wrong sign or coefficient anywhere in the quadrupole terms
+    leaves a d^-4 error."""
+    rng = np.random.default_rng(9)
+    pts = rng.uniform(-0.5, 0.5, (7, 3))
+    ms = rng.uniform(0.2, 1.0, 7)
+    M, com, Q = oracle.multipole(pts, ms)
+    direction = np.array([0.6, -0.48, 0.64])
+    ds = np.array([16.0, 32.0, 64.0, 128.0])
+    em, eq = [], []
+    for d in ds:
+        xi = com + d * direction
+        allp = np.concatenate([[xi], pts])
+        allm = np.concatenate([[1.0], ms])
+        exact, _ = oracle.direct(allp, allm, np.zeros(8), idx=[0])
+        am, _ = oracle.spj_force(xi, 0.0, M, com)
+        aq, _ = oracle.spj_force(xi, 0.0, M, com, Q)
+        em.append(np.linalg.norm(am - exact[0]))
+        eq.append(np.linalg.norm(aq - exact[0]))
+    sm = np.polyfit(np.log(ds), np.log(em), 1)[0]
+    sq = np.polyfit(np.log(ds), np.log(eq), 1)[0]
+    assert abs(sm + 4) < 0.15
+    assert abs(sq + 5) < 0.15
+    assert np.all(np.array(eq) < 0.3 * np.array(em))
+
+
+def test_superparticle_force_is_minus_grad_potential():
+    rng = np.random.default_rng(10)
+    pts = rng.uniform(-0.5, 0.5, (5, 3))
+    ms = rng.uniform(0.2, 1.0, 5)
+    M, com, Q = oracle.multipole(pts, ms)
+    xi = com + np.array([1.3, -0.7, 0.9])
+    eps = 0.3
+    a, _ = oracle.spj_force(xi, eps, M, com, Q)
+    h = 1e-5
+    g = np.zeros(3)
+    for ax in range(3):
+        dx = np.zeros(3)
+        dx[ax] = h
+        _, pp = oracle.spj_force(xi + dx, eps, M, com, Q)
+        _, pm = oracle.spj_force(xi - dx, eps, M, com, Q)
+        g[ax] = (pp - pm) / (2 * h)
+    np.testing.assert_allclose(a, -g, rtol=1e-7, atol=1e-9)
+    # with Q absent the superparticle is the softened point mass of
+    # Eq. ParticleSuperparticleNbody
+    a0, p0 = oracle.spj_force(xi, eps, M, com)
+    r = xi - com
+    R2 = r @ r + eps * eps
+    np.testing.assert_allclose(a0, -M * r / R2 ** 1.5, rtol=1e-14)
+    assert p0 == pytest.approx(-M / np.sqrt(R2), rel=1e-15)
+
+
+@pytest.mark.parametrize("quad,tol", [(False, 2e-3), (True, 5e-4)])
+def test_tree_accuracy_at_theta_half(quad, tol):
+    pos, vel, mass, eps = ics.make_config("plummer16k")
+    t = oracle.Tree(pos, mass, eps, theta=0.5, n_leaf=8, n_grp=64, quad=quad)
+    acc, pot, _ = t.force()
+    ad, pd = oracle.direct(pos, mass, eps)
+    err = np.linalg.norm(acc - ad, axis=1) / np.linalg.norm(ad, axis=1)
+    assert np.median(err) <= tol
+    perr = np.abs(pot - pd) / np.abs(pd)
+    assert np.median(perr) <= tol
+
+
+def test_leapfrog_is_time_reversible():
+    pos, m, e = _clustered(64, 8)
+    vel = np.random.default_rng(8).normal(size=(64, 3)) * 0.1
+    x, v = pos.copy(), vel.copy()
+    dt = 1.0 / 128.0
+
+    def acc_of(p):
+        return oracle.direct(p, m, e)[0]
+
+    a = acc_of(x)
+    for sgn in (+1, -1):
+        for _ in range(20):
+            v = oracle.kick(v, a, 0.5 * sgn * dt)
+            x = oracle.drift(x, v, sgn * dt)
+            a = acc_of(x)
+            v = oracle.kick(v, a, 0.5 * sgn * dt)
+        if sgn > 0:
+            assert np.abs(x - pos).max() > 1e-3
+    np.testing.assert_allclose(x, pos, atol=1e-12)
+    np.testing.assert_allclose(v, vel, atol=1e-12)
+
+
+def test_circular_two_body_orbit_energy_bounded():
+    # equal masses m at separation 1 on a circular orbit, no softening effect
+    m = 0.5
+    pos = np.array([[0.5, 0.0, 0.0], [-0.5, 0.0, 0.0]])
+    vc = np.sqrt(m / (2 * 1.0))  # v^2 / (1/2) = m / 1^2 for each body
+    vel = np.array([[0.0, vc, 0.0], [0.0, -vc, 0.0]])
+    mass = np.full(2, m)
+    eps = np.full(2, 1e-8)
+    acc, pot = oracle.direct(pos, mass, eps)
+    e0 = sum(oracle.energy(vel, mass, pot))
+    dt = 1.0 / 128.0
+    es = []
+    for _ in range(800):
+        vel = oracle.kick(vel, acc, 0.5 * dt)
+        pos = oracle.drift(pos, vel, dt)
+        acc, pot = oracle.direct(pos, mass, eps)
+        vel = oracle.kick(vel, acc, 0.5 * dt)
+        es.append(sum(oracle.energy(vel, mass, pot)))
+    assert np.abs(np.array(es) / e0 - 1).max() < 1e-5
+    assert abs(np.linalg.norm(pos[0] - pos[1]) - 1.0) < 1e-3
+
+
+@pytest.mark.parametrize("theta,n_grp", [(0.3, 32), (0.5, 64), (0.5, 128), (0.7, 64)])
+def test_list_length_follows_the_paper_model(theta, n_grp):
+    """Mean interaction-list length per particle against eq. nlist_long of
+    Sect. 5.5 (with n_p = 1), which the paper fits to its measured lengths
+    "reasonably well"; a factor 1.5 either way is allowed."""
+    pos, vel, mass, eps = ics.make_config("plummer16k")
+    n = len(pos)
+    t = oracle.Tree(pos, mass, eps, theta=theta, n_leaf=8, n_grp=n_grp)
+    _, _, tot = t.force()
+    ng, th = float(n_grp), theta
+    model = (ng + 14 * ng ** (2 / 3) / th + 21 * np.pi * ng ** (1 / 3) / th ** 2
+             + 28 * np.pi / (3 * th ** 3) * np.log2(th / 2.8 * (n ** (1 / 3) - ng ** (1 / 3))))
+    assert 1 / 1.5 < (tot[2] / n) / model < 1.5
