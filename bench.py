@@ -1,0 +1,358 @@
+"""Benchmark: leapfrog steps of the Barnes-Hut tree force on one GB300.
+
+Workload (default): Hernquist halo, N = 2^24, theta = 0.5, quadrupole
+superparticles, n_leaf = 16, n_grp = 128, eps = 0.005, dt = 1/512; FP32-
+relative pipeline, with the all-FP64 pipeline of the same library timed on
+one step beside it.  A step is kick + drift + the whole force calculation
+(root box, keys, sort, reorder, octree, moments, groups, walk, force) +
+kick.  Inputs are resident in HBM and far larger than L2.
+
+Metric: particle-particle + particle-superparticle interactions per second
+(sum over i-groups of n_i * (|EPJ| + |SPJ|)), with ms/step beside it.
+
+Under torchrun each rank steps its own replica (the single-system path has
+no data-parallel split without a domain decomposition); ``value`` is the sum
+over ranks, timed by the slowest rank.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# FP32-lane operations of one interaction as the kernels evaluate the
+# formulas (FMA = 1): particle-particle and monopole superparticle 13,
+# quadrupole superparticle 35; plus one MUFU reciprocal square root each.
+OPS_EPJ = 13
+OPS_SPJ_MONO = 13
+OPS_SPJ_QUAD = 35
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1 << 24)
+    ap.add_argument("--model", default="hernquist")
+    ap.add_argument("--theta", type=float, default=0.5)
+    ap.add_argument("--n-leaf", type=int, default=16)
+    ap.add_argument("--n-grp", type=int, default=128)
+    ap.add_argument("--eps", type=float, default=0.005)
+    ap.add_argument("--dt", type=float, default=1.0 / 512.0)
+    ap.add_argument("--mono", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "0x1", "1", "yes"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def make_inputs(args):
+    import ics
+    seed = ics.SEED_BASE + 3
+    return ics.make(args.model, args.n, seed, args.eps)
+
+
+def workload_name(args):
+    mom = "mono" if args.mono else "quad"
+    return (f"{args.model} N={args.n} theta={args.theta} {mom} n_leaf={args.n_leaf} "
+            f"n_grp={args.n_grp} eps={args.eps} dt={args.dt:.6g}")
+
+
+def cpu_sample(pos, mass, eps, args, seconds):
+    """The oracle as it stands on a bounded sample of the same workload:
+    full tree build, then walk + force for a random subset of i-groups sized
+    to about `seconds` of CPU work.  Returns a cpu_baseline dict."""
+    import oracle
+    t0 = time.perf_counter()
+    tree = oracle.Tree(pos, mass, eps, theta=args.theta, n_leaf=args.n_leaf, n_grp=args.n_grp,
+                       quad=not args.mono)
+    t_build = time.perf_counter() - t0
+    ng = tree.n_groups
+    rng = np.random.default_rng(1)
+    order = rng.permutation(ng)
+    done, inter, t_force, k = 0, 0, 0.0, 16
+    gcount = tree.groups()["count"]
+    while t_force < seconds and done < ng:
+        sel = order[done:done + k]
+        t1 = time.perf_counter()
+        _, _, tot = tree.force(sel)
+        t_force += time.perf_counter() - t1
+        inter += tot[2]
+        done += len(sel)
+        k *= 2
+    frac = gcount[order[:done]].sum() / len(pos)
+    t_eff = t_force + t_build * frac
+    return {"value": inter / t_eff, "unit": "interactions/s", "cores": oracle.get_threads(),
+            "kind": "oracle",
+            "sample": (f"FP64 C oracle: full tree build of the same {len(pos)}-particle set "
+                       f"({t_build:.1f} s, charged pro rata) + walk and force of {done} of {ng} "
+                       f"random i-groups ({frac * 100:.2f}% of particles, {inter:.3e} "
+                       f"interactions, {t_force:.1f} s)")}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    pos, vel, mass, eps = make_inputs(args)
+    import oracle
+    for _ in range(args.warmup):
+        cpu_sample(pos, mass, eps, args, 1.0)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_sample(pos, mass, eps, args, args.cpu_seconds / max(args.steps, 1)))
+    wall = time.perf_counter() - t0
+    v = statistics.median([c["value"] for c in vals])
+    line = {"impl": "reference", "metric": "particle-interactions/s", "value": v,
+            "unit": "interactions/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args), "l2": "inputs larger than L2"},
+            "cpu_baseline": {**vals[-1], "value": v},
+            "e2e": {"value": v, "unit": "interactions/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_1601_03138_gb300 as G
+    from paper_1601_03138_gb300 import build as B
+    B.build()
+    torch.cuda.set_device(local_rank)
+    pos, vel, mass, eps = make_inputs(args)
+    n = len(pos)
+    ctx = G.Context(local_rank)
+    ctx.set_profiling(True)
+    stream = torch.cuda.ExternalStream(ctx.stream)
+    ps = G.ParticleSystem(ctx, n)
+    tree = G.Tree(ctx, theta=args.theta, n_leaf=args.n_leaf, n_grp=args.n_grp, quad=not args.mono)
+    ps.set(pos, vel, mass, eps)
+    tree.calc_force_all_and_write_back(ps)
+    for _ in range(args.warmup):
+        tree.step(ps, args.dt)
+    dist = world > 1
+    if dist:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    per_step, inter, inter_e, inter_s, force_ms, stage = [], 0, 0, 0, [], []
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        tree.step(ps, args.dt)
+        ev[k][1].record(stream)
+        st = tree.stats()  # synchronises the stream; outside the events
+        inter_e += st["interactions_epj"]
+        inter_s += st["interactions_spj"]
+        force_ms.append(st["ms_force"])
+        stage.append(st)
+    torch.cuda.synchronize()
+    if dist:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    per_step = [a.elapsed_time(b) for a, b in ev]
+    t_total = sum(per_step) / 1e3
+    inter = inter_e + inter_s
+    t_max = t_total
+    if dist:
+        tt = torch.tensor([t_total, float(inter)], device="cuda", dtype=torch.float64)
+        gathered = [torch.zeros_like(tt) for _ in range(world)]
+        torch.distributed.all_gather(gathered, tt)
+        t_max = max(float(g[0]) for g in gathered)
+        inter = sum(float(g[1]) for g in gathered)
+    value = inter / t_max
+    last = stage[-1]
+
+    # roofline of the dominant kernel: the force kernel (FP32 ALU bound)
+    pk, pk_kind = peaks()
+    sm_count = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    f_ghz = pk.get("sm_max_mhz", 2070.0) / 1e3
+    peak_ops = sm_count * 128 * f_ghz * 1e9
+    ops_spj = OPS_SPJ_MONO if args.mono else OPS_SPJ_QUAD
+    ops_last = last["interactions_epj"] * OPS_EPJ + last["interactions_spj"] * ops_spj
+    f_s = statistics.median(force_ms) / 1e3
+    achieved = ops_last / f_s
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                "unit": "TFLOP/s", "frac": achieved / peak_ops, "traffic": None,
+                "kernel": "k_force_f32 (quadrupole)" if not args.mono else "k_force_f32",
+                "peak_source": f"{sm_count} SMs x 128 FP32 lanes x {f_ghz:.3f} GHz "
+                               f"(sm_max_mhz of {pk_kind} peaks), FMA = 1 op",
+                "ops_per_interaction": {"epj": OPS_EPJ, "spj": ops_spj}}
+    stages = {k: round(statistics.median([s[k] for s in stage]), 3) for k in stage[0]
+              if k.startswith("ms_")}
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        hp, hv, hm, he = pin(pos), pin(vel), pin(mass), pin(eps)
+        hacc = torch.zeros((n, 3), dtype=torch.float64).pin_memory().numpy()
+        hpot = torch.zeros(n, dtype=torch.float64).pin_memory().numpy()
+        ps2 = G.ParticleSystem(ctx, n)
+        ps2.set(hp, hv, hm, he)
+        tree.calc_force_all_and_write_back(ps2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ie = 0
+        for _ in range(args.e2e_steps):
+            ps2.set(hp, hv, hm, he)
+            tree.calc_force_all_and_write_back(ps2)
+            G.fdps_psys_get(ctx.h, ps2.h, None, None, hacc, hpot)
+            s2 = tree.stats()
+            ie += s2["interactions_epj"] + s2["interactions_spj"]
+        t_e2e = time.perf_counter() - t0
+        ps2.close()
+        e2e = {"value": ie / t_e2e, "unit": "interactions/s", "h2d_bytes_per_step": 64 * n,
+               "d2h_bytes_per_step": 32 * n, "steps": args.e2e_steps,
+               "what": "psys_set from pinned host + calcForceAllAndWriteBack + get(acc, pot)"}
+
+    # all-FP64 pipeline of the same library on the same particles: one step
+    fp64 = None
+    if not args.no_fp64:
+        ps3 = G.ParticleSystem(ctx, n)
+        tree64 = G.Tree(ctx, theta=args.theta, n_leaf=args.n_leaf, n_grp=args.n_grp,
+                        quad=not args.mono, fp64=True)
+        ps3.set(pos, vel, mass, eps)
+        tree64.calc_force_all_and_write_back(ps3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tree64.step(ps3, args.dt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s3 = tree64.stats()
+        ms64 = e0.elapsed_time(e1)
+        fp64 = {"ms_per_step": ms64,
+                "value": (s3["interactions_epj"] + s3["interactions_spj"]) / (ms64 / 1e3),
+                "ms_force": s3["ms_force"], "steps": 1}
+        tree64.close()
+        ps3.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_sample(pos, mass, eps, args, args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": "particle-interactions/s", "value": value, "unit": "interactions/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": workload_name(args), "l2": "inputs larger than L2",
+                           "replicas": world},
+                "gpu_launches": None, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clk, "fp64_variant": fp64, "stages_ms": stages,
+                "per_step": {"interactions": inter / args.steps,
+                             "n_nodes": last["n_nodes"], "n_groups": last["n_groups"],
+                             "fp64_fallbacks": last["fp64_fallbacks"]}}
+        line["gpu_launches"] = launches_per_step(args) * args.steps
+        print(json.dumps(line), flush=True)
+    tree.close()
+    ps.close()
+    ctx.close()
+
+
+def launches_per_step(args):
+    """Kernels of one step: kick, drift, kick + the force pipeline."""
+    force = 3 + 7 + 3 * 8 + 1 + 1 + 21 * 3 + 22 + 4 + 1 + 1 + 1 + 1
+    return 3 + force
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,228 @@
+/*
+ * fdps_gpu.h -- C ABI of a single-GPU (sm_103a) Barnes-Hut tree force for
+ * softened self-gravity, shaped after the public API of FDPS
+ * (Iwasawa et al. 2016, "Implementation and performance of FDPS",
+ * arXiv 1601.03138).
+ *
+ * The paper's user program (Sect. 2.2, the N-body example) creates a
+ * ParticleSystem, a TreeForForceLong object and calls
+ * calcForceAllAndWriteBack(f_epj, f_spj, psys, dinfo) between a predict
+ * (kick + drift) and a correct (kick) step.  This header offers the same
+ * pieces as opaque handles:
+ *
+ *   fdps_init / fdps_finalize            <- PS::Initialize / PS::Finalize
+ *   fdps_psys_*                          <- ParticleSystem<FP>
+ *   fdps_tree_create                     <- TreeForForceLong<...>::Monopole
+ *                                           (and the quadrupole variant)
+ *   fdps_tree_calc_force_all_and_write_back
+ *                                        <- calcForceAllAndWriteBack
+ *   fdps_kick / fdps_drift / fdps_step   <- the example's predict/correct
+ *
+ * Conventions shared by every call:
+ *   - Every function returning int returns FDPS_OK (0) or a negative
+ *     FDPS_E* code; fdps_last_error(ctx) then holds a one-line message.
+ *     No call exits the process or traps the GPU.
+ *   - Handles own all their device memory; *_destroy frees it.
+ *   - All work is issued on the context's CUDA stream (fdps_get_stream);
+ *     calls that return data to host memory synchronise that stream.
+ *   - Positions, velocities and accelerations are row-major [n][3] FP64
+ *     arrays ("pos3n"); masses, softenings and potentials are [n] FP64.
+ *   - Pointers flagged by on_device = 1 are device pointers borrowed for
+ *     the duration of the call only; on_device = 0 means host memory.
+ *   - Units: G = 1.
+ */
+#ifndef FDPS_GPU_H
+#define FDPS_GPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------- status codes */
+#define FDPS_OK 0
+#define FDPS_EINVAL (-1)    /* bad argument: see fdps_last_error */
+#define FDPS_ENOMEM (-2)    /* device or host allocation failed */
+#define FDPS_ECUDA (-3)     /* a CUDA runtime call failed */
+#define FDPS_EOVERFLOW (-4) /* an internal buffer bound was exceeded and the
+                               automatic resize-and-retry also failed */
+#define FDPS_ETIMEOUT (-5)  /* a bounded device-side wait gave up */
+#define FDPS_ESTATE (-6)    /* call out of order (e.g. data not set yet) */
+
+/* ------------------------------------------------------------- handles */
+typedef struct fdps_ctx fdps_ctx;
+typedef struct fdps_psys fdps_psys;
+typedef struct fdps_tree fdps_tree;
+
+/* --------------------------------------------------------- parameters */
+enum fdps_moment { FDPS_MONOPOLE = 0, FDPS_QUADRUPOLE = 1 };
+enum fdps_precision {
+    FDPS_FP32REL = 0, /* walk output converted to FP32 relative to each
+                         i-group's centre, FP32 force with compensated sums */
+    FDPS_FP64 = 1     /* FP64 absolute coordinates and FP64 sums */
+};
+
+/* Interaction kernels selectable at run time (Sect. 2.2: the user passes one
+   functor for particle-particle and one for particle-superparticle terms). */
+typedef enum {
+    FDPS_GRAV_EPJ = 0,      /* Eq. ParticleParticleNbody, softening eps_i */
+    FDPS_GRAV_SPJ_MONO = 1, /* Eq. ParticleSuperparticleNbody (monopole) */
+    FDPS_GRAV_SPJ_QUAD = 2  /* monopole + traceless quadrupole term */
+} fdps_kernel_id;
+
+/* Tree-for-force parameters (TreeForForceLong, Sect. 2.2; theta of the
+   "usual tree traversal", Sect. 3.2; n_grp of the modified tree algorithm,
+   Sect. 5.5).
+     theta      >= 0   opening angle; 0 opens every cell (direct summation)
+     n_leaf     1..16  a cell with <= n_leaf particles is a leaf
+     n_grp      >= n_leaf, <= 4096: a maximal cell with <= n_grp particles
+                       is one i-group sharing one interaction list
+     moment     enum fdps_moment
+     precision  enum fdps_precision
+     tile_depth 0 = default; otherwise j-entries staged per force tile
+                (32..1024, multiple of 32)                                */
+typedef struct {
+    double theta;
+    int32_t n_leaf;
+    int32_t n_grp;
+    int32_t moment;
+    int32_t precision;
+    int32_t tile_depth;
+    int32_t reserved[3];
+} fdps_tree_params;
+
+/* Per-call counters and stage times (milliseconds, CUDA events, valid when
+   profiling is on) of the last force calculation. */
+typedef struct {
+    int64_t n_particles;
+    int64_t n_nodes;
+    int64_t n_groups;
+    int64_t n_levels;          /* deepest level + 1 */
+    int64_t list_entries;      /* sum over groups of list entries
+                                  (SPJ cells + opened leaves) */
+    int64_t n_epj;             /* sum over groups of |EPJ| (particles) */
+    int64_t n_spj;             /* sum over groups of |SPJ| (cells) */
+    int64_t interactions_epj;  /* sum over groups of n_i |EPJ| */
+    int64_t interactions_spj;  /* sum over groups of n_i |SPJ| */
+    int64_t fp64_fallbacks;    /* opening tests decided in FP64 */
+    int64_t retries;           /* buffer resize-and-retry count */
+    double ms_box_keys;        /* root box + Morton keys */
+    double ms_sort;            /* radix sort */
+    double ms_permute;         /* reorder into key order */
+    double ms_build;           /* octree levels */
+    double ms_moments;         /* bottom-up moments */
+    double ms_groups;          /* i-group selection and boxes */
+    double ms_walk;            /* interaction lists */
+    double ms_force;           /* force kernel */
+    double ms_total;
+} fdps_tree_stats;
+
+/* ------------------------------------------------------- PS::Initialize */
+
+/* Select CUDA device `device`, create a stream and return a context.
+   Errors: FDPS_EINVAL (no such device or not sm_103), FDPS_ECUDA. */
+int fdps_init(int device, fdps_ctx** out);
+/* Free the context (psys and tree handles must be destroyed first). */
+int fdps_finalize(fdps_ctx* ctx);
+/* Message of the last failing call on this context ("" if none). */
+const char* fdps_last_error(const fdps_ctx* ctx);
+/* The cudaStream_t every call is issued on (as void*). */
+void* fdps_get_stream(const fdps_ctx* ctx);
+/* Issue all further work on a caller-owned cudaStream_t (NULL = back to the
+   context's own stream).  The caller keeps ownership. */
+int fdps_set_stream(fdps_ctx* ctx, void* stream);
+/* Enable (1) / disable (0) per-stage CUDA-event timing in fdps_tree_stats. */
+int fdps_set_profiling(fdps_ctx* ctx, int on);
+
+/* ------------------------------------------------ ParticleSystem<FP> */
+
+/* A particle system of n >= 1 particles (the example's class Nbody: mass,
+   eps, pos, vel, acc, plus the potential).  Contents are undefined until
+   fdps_psys_set.  Errors: FDPS_EINVAL, FDPS_ENOMEM. */
+int fdps_psys_create(fdps_ctx* ctx, int64_t n, fdps_psys** out);
+int fdps_psys_destroy(fdps_psys* ps);
+/* getNumberOfParticleLocal: number of particles (or -1 for NULL). */
+int64_t fdps_psys_size(const fdps_psys* ps);
+/* Copy particle data in (the example's readAscii / copyFromFP).  pos3n and
+   vel3n are [n][3]; mass [n] >= 0; eps [n] > 0 (the softening of Eq.
+   ParticleParticleNbody, eps_i of the receiving particle).  vel3n may be
+   NULL (zero velocities).  Values are validated on the device: NaN/Inf,
+   negative mass or non-positive eps give FDPS_EINVAL.  Resets the
+   particle order to the caller's order. */
+int fdps_psys_set(fdps_psys* ps, const double* pos3n, const double* vel3n,
+                  const double* mass, const double* eps, int on_device);
+/* Copy particle data out in the caller's order (rows as passed to
+   fdps_psys_set).  Any output pointer may be NULL.  acc3n and pot are the
+   results of the last force calculation (copyFromForce); the potential has
+   the self term removed.  FDPS_ESTATE if acc/pot are requested before any
+   force calculation. */
+int fdps_psys_get(const fdps_psys* ps, double* pos3n, double* vel3n,
+                  double* acc3n, double* pot, int on_device);
+
+/* --------------------------------------------- TreeForForceLong<...> */
+
+/* Create a tree-for-force object (Sect. 2.2, grav.initialize).  Errors:
+   FDPS_EINVAL for out-of-range parameters (see fdps_tree_params). */
+int fdps_tree_create(fdps_ctx* ctx, const fdps_tree_params* params,
+                     fdps_tree** out);
+int fdps_tree_destroy(fdps_tree* tree);
+
+/* calcForceAllAndWriteBack (Sect. 2.2; steps of Sect. 3.2 on one GPU):
+   root box -> Morton keys -> radix sort -> reorder -> octree -> moments ->
+   i-groups -> interaction lists -> forces, written back into ps
+   (acceleration and potential of every particle, overwriting old values).
+   k_epj must be FDPS_GRAV_EPJ; k_spj FDPS_GRAV_SPJ_MONO, or
+   FDPS_GRAV_SPJ_QUAD for a quadrupole tree.  The particles are left in
+   Morton order internally; fdps_psys_get still returns the caller's order.
+   Errors: FDPS_EINVAL, FDPS_ESTATE (no data), FDPS_ENOMEM,
+   FDPS_EOVERFLOW, FDPS_ECUDA. */
+int fdps_tree_calc_force_all_and_write_back(fdps_tree* tree, fdps_psys* ps,
+                                            int k_epj, int k_spj);
+
+/* Leapfrog pieces of the example's predict/correct (Sect. 2.2):
+   fdps_kick: v += dt_half * a;  fdps_drift: x += dt * v  (FP64). */
+int fdps_kick(fdps_psys* ps, double dt_half);
+int fdps_drift(fdps_psys* ps, double dt);
+/* One kick-drift-kick step: kick(dt/2), drift(dt), force, kick(dt/2).
+   Needs valid forces from a previous force calculation (FDPS_ESTATE). */
+int fdps_step(fdps_tree* tree, fdps_psys* ps, double dt);
+/* Kinetic sum m v^2 / 2 and potential sum m phi / 2 (FP64), using the
+   potential of the last force calculation. */
+int fdps_psys_energy(fdps_psys* ps, double* kinetic, double* potential);
+
+/* --------------------------------------------------- introspection
+   Test and diagnostic access to the last force calculation's
+   intermediate data.  All outputs are host arrays; each call synchronises
+   the stream.  `cap` is the capacity of every output array in elements
+   (rows); FDPS_EOVERFLOW if too small.  Arrays may be NULL to skip them. */
+int fdps_tree_get_stats(const fdps_tree* tree, fdps_tree_stats* out);
+/* Root box {lo_x, lo_y, lo_z, L, s}: lo = per-axis minimum, L = largest
+   extent (1 if 0), s = 2^21 / L. */
+int fdps_tree_get_box(const fdps_tree* tree, double* out5);
+/* Morton keys in the particle order the call started from, and the stable
+   sort permutation (sorted position -> that order's index). */
+int fdps_tree_get_keys(const fdps_tree* tree, uint64_t* keys, uint32_t* perm,
+                       int64_t cap);
+/* Node table in BFS order (level-major, key prefix ascending).  child_first
+   is -1 for a leaf; com is [n][3]; quad [n][6] (xx yy zz xy xz yz, zero for
+   a monopole tree).  *n_out receives the node count. */
+int fdps_tree_get_nodes(const fdps_tree* tree, int64_t cap, int64_t* n_out,
+                        int32_t* level, int64_t* first, int64_t* count,
+                        int64_t* child_first, int32_t* nchild, double* mass,
+                        double* com, double* quad);
+/* i-groups in order of their first particle: first, count, node id and FP64
+   bounding box [g][6] (lo xyz, hi xyz).  *n_out receives the group count. */
+int fdps_tree_get_groups(const fdps_tree* tree, int64_t cap, int64_t* n_out,
+                         int64_t* first, int64_t* count, int64_t* node,
+                         double* box6);
+/* Interaction lists of groups [g0, g1): offsets [g1-g0+1] into `entries`.
+   An entry is a node id; bit 31 set marks an opened leaf (its particles
+   are EPJ), clear marks a superparticle (SPJ).  `cap` bounds `entries`. */
+int fdps_tree_get_lists(const fdps_tree* tree, int64_t g0, int64_t g1,
+                        int64_t* offsets, uint32_t* entries, int64_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FDPS_GPU_H */

@@ -1,0 +1,409 @@
+"""Python binding of the single-GPU Barnes-Hut tree-force library (sm_103a).
+
+Thin ctypes marshalling over the C ABI of ``include/fdps_gpu.h``; every step
+of the force calculation runs in the CUDA library ``_build/libfdpsgpu.so``.
+If that library is missing, every call raises: there is no CPU fallback.
+
+The functions keep the C names (``fdps_init``, ``fdps_psys_set``,
+``fdps_tree_calc_force_all_and_write_back`` ...), take numpy host arrays or
+CUDA tensors (anything with ``data_ptr()``, passed as device pointers), and
+raise :class:`FdpsError` on a negative status.  ``Context``,
+``ParticleSystem`` and ``Tree`` wrap the handles for convenience; they follow
+FDPS's ``PS::Initialize`` / ``ParticleSystem`` / ``TreeForForceLong`` /
+``calcForceAllAndWriteBack`` (Iwasawa et al. 2016, Sect. 2.2).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfdpsgpu.so")
+
+FDPS_OK = 0
+FDPS_EINVAL = -1
+FDPS_ENOMEM = -2
+FDPS_ECUDA = -3
+FDPS_EOVERFLOW = -4
+FDPS_ETIMEOUT = -5
+FDPS_ESTATE = -6
+
+FDPS_MONOPOLE = 0
+FDPS_QUADRUPOLE = 1
+FDPS_FP32REL = 0
+FDPS_FP64 = 1
+FDPS_GRAV_EPJ = 0
+FDPS_GRAV_SPJ_MONO = 1
+FDPS_GRAV_SPJ_QUAD = 2
+
+_NAMES = {0: "FDPS_OK", -1: "FDPS_EINVAL", -2: "FDPS_ENOMEM", -3: "FDPS_ECUDA",
+          -4: "FDPS_EOVERFLOW", -5: "FDPS_ETIMEOUT", -6: "FDPS_ESTATE"}
+
+
+class FdpsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class fdps_tree_params(C.Structure):
+    _fields_ = [("theta", C.c_double), ("n_leaf", C.c_int32), ("n_grp", C.c_int32),
+                ("moment", C.c_int32), ("precision", C.c_int32), ("tile_depth", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
+
+
+class fdps_tree_stats(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in (
+        "n_particles", "n_nodes", "n_groups", "n_levels", "list_entries", "n_epj", "n_spj",
+        "interactions_epj", "interactions_spj", "fp64_fallbacks", "retries")] + [
+        (k, C.c_double) for k in (
+            "ms_box_keys", "ms_sort", "ms_permute", "ms_build", "ms_moments", "ms_groups",
+            "ms_walk", "ms_force", "ms_total")]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_vp = C.c_void_p
+_i64 = C.c_int64
+_i32 = C.c_int32
+_d = C.c_double
+_PROTOS = {
+    "fdps_init": (C.c_int, [C.c_int, C.POINTER(_vp)]),
+    "fdps_finalize": (C.c_int, [_vp]),
+    "fdps_last_error": (C.c_char_p, [_vp]),
+    "fdps_get_stream": (_vp, [_vp]),
+    "fdps_set_stream": (C.c_int, [_vp, _vp]),
+    "fdps_set_profiling": (C.c_int, [_vp, C.c_int]),
+    "fdps_psys_create": (C.c_int, [_vp, _i64, C.POINTER(_vp)]),
+    "fdps_psys_destroy": (C.c_int, [_vp]),
+    "fdps_psys_size": (_i64, [_vp]),
+    "fdps_psys_set": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_int]),
+    "fdps_psys_get": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_int]),
+    "fdps_tree_create": (C.c_int, [_vp, C.POINTER(fdps_tree_params), C.POINTER(_vp)]),
+    "fdps_tree_destroy": (C.c_int, [_vp]),
+    "fdps_tree_calc_force_all_and_write_back": (C.c_int, [_vp, _vp, C.c_int, C.c_int]),
+    "fdps_kick": (C.c_int, [_vp, _d]),
+    "fdps_drift": (C.c_int, [_vp, _d]),
+    "fdps_step": (C.c_int, [_vp, _vp, _d]),
+    "fdps_psys_energy": (C.c_int, [_vp, C.POINTER(_d), C.POINTER(_d)]),
+    "fdps_tree_get_stats": (C.c_int, [_vp, C.POINTER(fdps_tree_stats)]),
+    "fdps_tree_get_box": (C.c_int, [_vp, _vp]),
+    "fdps_tree_get_keys": (C.c_int, [_vp, _vp, _vp, _i64]),
+    "fdps_tree_get_nodes": (C.c_int, [_vp, _i64, C.POINTER(_i64), _vp, _vp, _vp, _vp, _vp, _vp,
+                                      _vp, _vp]),
+    "fdps_tree_get_groups": (C.c_int, [_vp, _i64, C.POINTER(_i64), _vp, _vp, _vp, _vp]),
+    "fdps_tree_get_lists": (C.c_int, [_vp, _i64, _i64, _vp, _vp, _i64]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"CUDA library {LIB_PATH} is missing; build it with "
+                "paper_1601_03138_gb300.build.build() (there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _PROTOS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return sorted(_PROTOS)
+
+
+def _ptr(a):
+    """(pointer, on_device) of a numpy array, a CUDA tensor or None."""
+    if a is None:
+        return None, None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr()), bool(getattr(a, "is_cuda", True))
+    if isinstance(a, np.ndarray):
+        if not (a.flags["C_CONTIGUOUS"] and a.dtype == np.float64):
+            raise ValueError("arrays must be C-contiguous float64")
+        return C.c_void_p(a.ctypes.data), False
+    raise TypeError(type(a))
+
+
+def _check(rc, ctx=None):
+    if rc < 0:
+        msg = lib().fdps_last_error(ctx).decode() if ctx else ""
+        raise FdpsError(rc, msg)
+    return rc
+
+
+# ------------------------------------------------------------ C-named calls
+
+def fdps_init(device: int = 0):
+    h = C.c_void_p()
+    _check(lib().fdps_init(device, C.byref(h)))
+    return h
+
+
+def fdps_finalize(ctx):
+    _check(lib().fdps_finalize(ctx))
+
+
+def fdps_last_error(ctx) -> str:
+    return lib().fdps_last_error(ctx).decode()
+
+
+def fdps_get_stream(ctx) -> int:
+    return lib().fdps_get_stream(ctx) or 0
+
+
+def fdps_set_stream(ctx, stream_ptr: int | None):
+    _check(lib().fdps_set_stream(ctx, C.c_void_p(stream_ptr) if stream_ptr else None), ctx)
+
+
+def fdps_set_profiling(ctx, on: bool):
+    _check(lib().fdps_set_profiling(ctx, 1 if on else 0), ctx)
+
+
+def fdps_psys_create(ctx, n: int):
+    h = C.c_void_p()
+    _check(lib().fdps_psys_create(ctx, int(n), C.byref(h)), ctx)
+    return h
+
+
+def fdps_psys_destroy(ps):
+    _check(lib().fdps_psys_destroy(ps))
+
+
+def fdps_psys_size(ps) -> int:
+    return int(lib().fdps_psys_size(ps))
+
+
+def fdps_psys_set(ctx, ps, pos, vel, mass, eps):
+    """pos/vel [n][3], mass/eps [n]: all numpy float64 or all CUDA float64 tensors."""
+    pp, dev = _ptr(pos)
+    vp, vdev = _ptr(vel)
+    mp, mdev = _ptr(mass)
+    ep, edev = _ptr(eps)
+    devs = {d for d in (dev, vdev, mdev, edev) if d is not None}
+    if len(devs) != 1:
+        raise ValueError("mix of host and device arrays")
+    _check(lib().fdps_psys_set(ps, pp, vp, mp, ep, int(devs.pop())), ctx)
+
+
+def fdps_psys_get(ctx, ps, pos=None, vel=None, acc=None, pot=None):
+    ptrs = [_ptr(a) for a in (pos, vel, acc, pot)]
+    devs = {d for _, d in ptrs if d is not None}
+    if len(devs) > 1:
+        raise ValueError("mix of host and device arrays")
+    dev = devs.pop() if devs else False
+    _check(lib().fdps_psys_get(ps, *[p for p, _ in ptrs], int(dev)), ctx)
+
+
+def fdps_tree_create(ctx, theta=0.5, n_leaf=8, n_grp=64, moment=FDPS_MONOPOLE,
+                     precision=FDPS_FP32REL, tile_depth=0):
+    p = fdps_tree_params(float(theta), int(n_leaf), int(n_grp), int(moment), int(precision),
+                         int(tile_depth))
+    h = C.c_void_p()
+    _check(lib().fdps_tree_create(ctx, C.byref(p), C.byref(h)), ctx)
+    return h
+
+
+def fdps_tree_destroy(tree):
+    _check(lib().fdps_tree_destroy(tree))
+
+
+def fdps_tree_calc_force_all_and_write_back(ctx, tree, ps, k_epj=FDPS_GRAV_EPJ,
+                                            k_spj=FDPS_GRAV_SPJ_MONO):
+    _check(lib().fdps_tree_calc_force_all_and_write_back(tree, ps, int(k_epj), int(k_spj)), ctx)
+
+
+def fdps_kick(ctx, ps, dt_half):
+    _check(lib().fdps_kick(ps, float(dt_half)), ctx)
+
+
+def fdps_drift(ctx, ps, dt):
+    _check(lib().fdps_drift(ps, float(dt)), ctx)
+
+
+def fdps_step(ctx, tree, ps, dt):
+    _check(lib().fdps_step(tree, ps, float(dt)), ctx)
+
+
+def fdps_psys_energy(ctx, ps):
+    k, p = C.c_double(), C.c_double()
+    _check(lib().fdps_psys_energy(ps, C.byref(k), C.byref(p)), ctx)
+    return k.value, p.value
+
+
+def fdps_tree_get_stats(ctx, tree) -> dict:
+    s = fdps_tree_stats()
+    _check(lib().fdps_tree_get_stats(tree, C.byref(s)), ctx)
+    return s.as_dict()
+
+
+def fdps_tree_get_box(ctx, tree):
+    out = np.zeros(5)
+    _check(lib().fdps_tree_get_box(tree, C.c_void_p(out.ctypes.data)), ctx)
+    return out[:3].copy(), float(out[3]), float(out[4])
+
+
+def fdps_tree_get_keys(ctx, tree, n):
+    keys = np.zeros(n, np.uint64)
+    perm = np.zeros(n, np.uint32)
+    _check(lib().fdps_tree_get_keys(tree, C.c_void_p(keys.ctypes.data),
+                                    C.c_void_p(perm.ctypes.data), n), ctx)
+    return keys, perm
+
+
+def fdps_tree_get_nodes(ctx, tree):
+    nn = C.c_int64()
+    rc = lib().fdps_tree_get_nodes(tree, 0, C.byref(nn), *([None] * 8))
+    if rc < 0 and rc != FDPS_EOVERFLOW:
+        _check(rc, ctx)
+    m = nn.value
+    d = dict(level=np.zeros(m, np.int32), first=np.zeros(m, np.int64), count=np.zeros(m, np.int64),
+             child_first=np.zeros(m, np.int64), nchild=np.zeros(m, np.int32), mass=np.zeros(m),
+             com=np.zeros((m, 3)), quad=np.zeros((m, 6)))
+    _check(lib().fdps_tree_get_nodes(tree, m, C.byref(nn), *[C.c_void_p(d[k].ctypes.data) for k in (
+        "level", "first", "count", "child_first", "nchild", "mass", "com", "quad")]), ctx)
+    return d
+
+
+def fdps_tree_get_groups(ctx, tree):
+    ng = C.c_int64()
+    rc = lib().fdps_tree_get_groups(tree, 0, C.byref(ng), None, None, None, None)
+    if rc < 0 and rc != FDPS_EOVERFLOW:
+        _check(rc, ctx)
+    m = ng.value
+    d = dict(first=np.zeros(m, np.int64), count=np.zeros(m, np.int64), node=np.zeros(m, np.int64),
+             box=np.zeros((m, 6)))
+    _check(lib().fdps_tree_get_groups(tree, m, C.byref(ng), *[C.c_void_p(d[k].ctypes.data) for k in (
+        "first", "count", "node", "box")]), ctx)
+    return d
+
+
+def fdps_tree_get_lists(ctx, tree, g0, g1):
+    """(offsets [g1-g0+1], entries): bit 31 of an entry marks an opened leaf."""
+    offs = np.zeros(g1 - g0 + 1, np.int64)
+    _check(lib().fdps_tree_get_lists(tree, g0, g1, C.c_void_p(offs.ctypes.data), None, 0), ctx)
+    ent = np.zeros(max(int(offs[-1]), 1), np.uint32)
+    _check(lib().fdps_tree_get_lists(tree, g0, g1, C.c_void_p(offs.ctypes.data),
+                                     C.c_void_p(ent.ctypes.data), len(ent)), ctx)
+    return offs, ent[: offs[-1]]
+
+
+# ------------------------------------------------------------ handle classes
+
+class Context:
+    """PS::Initialize / PS::Finalize for one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.h = fdps_init(device)
+
+    def close(self):
+        if getattr(self, "h", None):
+            fdps_finalize(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def stream(self) -> int:
+        return fdps_get_stream(self.h)
+
+    def set_profiling(self, on=True):
+        fdps_set_profiling(self.h, on)
+
+
+class ParticleSystem:
+    """ParticleSystem<FP>: n particles with pos, vel, mass, eps, acc, pot."""
+
+    def __init__(self, ctx: Context, n: int):
+        self.ctx = ctx
+        self.n = int(n)
+        self.h = fdps_psys_create(ctx.h, n)
+
+    def close(self):
+        if getattr(self, "h", None):
+            fdps_psys_destroy(self.h)
+            self.h = None
+
+    def set(self, pos, vel, mass, eps):
+        fdps_psys_set(self.ctx.h, self.h, pos, vel, mass, eps)
+
+    def get(self):
+        """(pos, vel, acc, pot) as numpy arrays in the caller's order."""
+        pos = np.zeros((self.n, 3))
+        vel = np.zeros((self.n, 3))
+        acc = np.zeros((self.n, 3))
+        pot = np.zeros(self.n)
+        fdps_psys_get(self.ctx.h, self.h, pos, vel, acc, pot)
+        return pos, vel, acc, pot
+
+    def get_state(self):
+        pos = np.zeros((self.n, 3))
+        vel = np.zeros((self.n, 3))
+        fdps_psys_get(self.ctx.h, self.h, pos, vel, None, None)
+        return pos, vel
+
+    def energy(self):
+        return fdps_psys_energy(self.ctx.h, self.h)
+
+    def kick(self, dt_half):
+        fdps_kick(self.ctx.h, self.h, dt_half)
+
+    def drift(self, dt):
+        fdps_drift(self.ctx.h, self.h, dt)
+
+
+class Tree:
+    """TreeForForceLong (monopole or quadrupole) with theta, n_leaf, n_grp."""
+
+    def __init__(self, ctx: Context, theta=0.5, n_leaf=8, n_grp=64, quad=False, fp64=False,
+                 tile_depth=0):
+        self.ctx = ctx
+        self.quad = bool(quad)
+        self.h = fdps_tree_create(ctx.h, theta, n_leaf, n_grp,
+                                  FDPS_QUADRUPOLE if quad else FDPS_MONOPOLE,
+                                  FDPS_FP64 if fp64 else FDPS_FP32REL, tile_depth)
+
+    def close(self):
+        if getattr(self, "h", None):
+            fdps_tree_destroy(self.h)
+            self.h = None
+
+    def calc_force_all_and_write_back(self, psys: ParticleSystem):
+        fdps_tree_calc_force_all_and_write_back(
+            self.ctx.h, self.h, psys.h, FDPS_GRAV_EPJ,
+            FDPS_GRAV_SPJ_QUAD if self.quad else FDPS_GRAV_SPJ_MONO)
+
+    def step(self, psys: ParticleSystem, dt: float):
+        fdps_step(self.ctx.h, self.h, psys.h, dt)
+
+    def stats(self):
+        return fdps_tree_get_stats(self.ctx.h, self.h)
+
+    def box(self):
+        return fdps_tree_get_box(self.ctx.h, self.h)
+
+    def keys(self, n):
+        return fdps_tree_get_keys(self.ctx.h, self.h, n)
+
+    def nodes(self):
+        return fdps_tree_get_nodes(self.ctx.h, self.h)
+
+    def groups(self):
+        return fdps_tree_get_groups(self.ctx.h, self.h)
+
+    def lists(self, g0, g1):
+        return fdps_tree_get_lists(self.ctx.h, self.h, g0, g1)

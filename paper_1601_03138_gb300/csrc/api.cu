@@ -1,0 +1,765 @@
+// api.cu -- the C ABI of include/fdps_gpu.h: handles, buffer management and
+// the force-calculation pipeline of calcForceAllAndWriteBack (Sect. 2.2 and
+// Sect. 3.2 of Iwasawa et al. 2016, on one GPU: local tree = global tree).
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "fdps_internal.cuh"
+
+namespace fdps {
+int walk_blocks(fdps_ctx* ctx);
+int walk_warps_per_block();
+unsigned long long walk_chunk();
+int launch_walk(fdps_tree* t, int blocks);
+int energy_scratch_doubles();
+}  // namespace fdps
+
+using namespace fdps;
+
+namespace {
+
+constexpr int kSortTile = 2048;
+
+void free_particles(fdps_tree* t) {
+    dev_free(t->keys_in);
+    dev_free(t->keys_a);
+    dev_free(t->keys_b);
+    dev_free(t->vals_a);
+    dev_free(t->vals_b);
+    dev_free(t->pf_hi);
+    dev_free(t->pf_lo);
+    dev_free(t->head);
+    dev_free(t->sort_hist);
+    t->cap_n = 0;
+    t->cap_tiles = 0;
+}
+
+int ensure_particles(fdps_tree* t, int64_t n) {
+    if (n <= t->cap_n) return FDPS_OK;
+    free_particles(t);
+    const int64_t tiles = (n + kSortTile - 1) / kSortTile;
+    bool ok = dev_alloc(&t->keys_in, n) == cudaSuccess && dev_alloc(&t->keys_a, n) == cudaSuccess &&
+              dev_alloc(&t->keys_b, n) == cudaSuccess && dev_alloc(&t->vals_a, n) == cudaSuccess &&
+              dev_alloc(&t->vals_b, n) == cudaSuccess && dev_alloc(&t->pf_hi, n) == cudaSuccess &&
+              dev_alloc(&t->pf_lo, n) == cudaSuccess && dev_alloc(&t->head, n) == cudaSuccess &&
+              dev_alloc(&t->sort_hist, 256 * tiles) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_particles(t);
+        return set_error(t->ctx, FDPS_ENOMEM, "device allocation for %lld particles failed",
+                         (long long)n);
+    }
+    t->cap_n = n;
+    t->cap_tiles = tiles;
+    return FDPS_OK;
+}
+
+void free_nodes(fdps_tree* t) {
+    dev_free(t->nd_first);
+    dev_free(t->nd_count);
+    dev_free(t->nd_child);
+    dev_free(t->nd_meta);
+    dev_free(t->nd_parent);
+    dev_free(t->nd_qlo);
+    dev_free(t->nd_prefix);
+    dev_free(t->nd_sx);
+    dev_free(t->nd_sy);
+    dev_free(t->nd_sz);
+    dev_free(t->nd_com);
+    dev_free(t->nd_quad);
+    dev_free(t->nd_fh);
+    dev_free(t->nd_fl);
+    dev_free(t->nd_fq0);
+    dev_free(t->nd_fq1);
+    dev_free(t->lvl_scratch);
+    t->cap_nodes = 0;
+}
+
+int ensure_nodes(fdps_tree* t, int64_t cap) {
+    if (cap <= t->cap_nodes) return FDPS_OK;
+    free_nodes(t);
+    bool ok = dev_alloc(&t->nd_first, cap) == cudaSuccess && dev_alloc(&t->nd_count, cap) == cudaSuccess &&
+              dev_alloc(&t->nd_child, cap) == cudaSuccess && dev_alloc(&t->nd_meta, cap) == cudaSuccess &&
+              dev_alloc(&t->nd_parent, cap) == cudaSuccess && dev_alloc(&t->nd_qlo, cap) == cudaSuccess &&
+              dev_alloc(&t->nd_prefix, cap) == cudaSuccess && dev_alloc(&t->nd_sx, cap) == cudaSuccess &&
+              dev_alloc(&t->nd_sy, cap) == cudaSuccess && dev_alloc(&t->nd_sz, cap) == cudaSuccess &&
+              dev_alloc(&t->nd_com, cap) == cudaSuccess && dev_alloc(&t->nd_quad, 6 * cap) == cudaSuccess &&
+              dev_alloc(&t->nd_fh, cap) == cudaSuccess && dev_alloc(&t->nd_fl, cap) == cudaSuccess &&
+              dev_alloc(&t->nd_fq0, cap) == cudaSuccess && dev_alloc(&t->nd_fq1, cap) == cudaSuccess &&
+              dev_alloc(&t->lvl_scratch, 16 * cap) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_nodes(t);
+        return set_error(t->ctx, FDPS_ENOMEM, "device allocation for %lld nodes failed", (long long)cap);
+    }
+    t->cap_nodes = cap;
+    return FDPS_OK;
+}
+
+void free_groups(fdps_tree* t) {
+    dev_free(t->g_first);
+    dev_free(t->g_count);
+    dev_free(t->g_node);
+    dev_free(t->g_box);
+    dev_free(t->g_qbox);
+    dev_free(t->g_ch);
+    dev_free(t->g_cl);
+    dev_free(t->g_blo);
+    dev_free(t->g_bhi);
+    dev_free(t->g_c64);
+    dev_free(t->g_off);
+    dev_free(t->g_len);
+    dev_free(t->g_nspj);
+    dev_free(t->g_nepj);
+    t->cap_groups = 0;
+}
+
+int ensure_groups(fdps_tree* t, int64_t cap) {
+    if (cap <= t->cap_groups) return FDPS_OK;
+    free_groups(t);
+    bool ok = dev_alloc(&t->g_first, cap) == cudaSuccess && dev_alloc(&t->g_count, cap) == cudaSuccess &&
+              dev_alloc(&t->g_node, cap) == cudaSuccess && dev_alloc(&t->g_box, 6 * cap) == cudaSuccess &&
+              dev_alloc(&t->g_qbox, 6 * cap) == cudaSuccess && dev_alloc(&t->g_ch, cap) == cudaSuccess &&
+              dev_alloc(&t->g_cl, cap) == cudaSuccess && dev_alloc(&t->g_blo, cap) == cudaSuccess &&
+              dev_alloc(&t->g_bhi, cap) == cudaSuccess && dev_alloc(&t->g_c64, cap) == cudaSuccess &&
+              dev_alloc(&t->g_off, cap) == cudaSuccess && dev_alloc(&t->g_len, cap) == cudaSuccess &&
+              dev_alloc(&t->g_nspj, cap) == cudaSuccess && dev_alloc(&t->g_nepj, cap) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_groups(t);
+        return set_error(t->ctx, FDPS_ENOMEM, "device allocation for %lld groups failed", (long long)cap);
+    }
+    t->cap_groups = cap;
+    return FDPS_OK;
+}
+
+int ensure_pool(fdps_tree* t, int64_t cap) {
+    if (cap <= t->cap_pool) return FDPS_OK;
+    dev_free(t->pool);
+    t->cap_pool = 0;
+    if (dev_alloc(&t->pool, cap) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(t->ctx, FDPS_ENOMEM, "device allocation of a %lld-entry list pool failed",
+                         (long long)cap);
+    }
+    t->cap_pool = cap;
+    return FDPS_OK;
+}
+
+int ensure_frontier(fdps_tree* t, int64_t per_warp) {
+    if (per_warp <= t->cap_frontier) return FDPS_OK;
+    dev_free(t->frontier);
+    t->cap_frontier = 0;
+    if (dev_alloc(&t->frontier, 2 * per_warp * t->n_walk_warps) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(t->ctx, FDPS_ENOMEM, "device allocation of walk frontiers failed");
+    }
+    t->cap_frontier = per_warp;
+    return FDPS_OK;
+}
+
+int read_state(fdps_tree* t) {
+    FDPS_CUDA_TRY(t->ctx, cudaMemcpyAsync(&t->h_st, t->st, sizeof(DevState), cudaMemcpyDeviceToHost,
+                                          t->ctx->stream));
+    FDPS_CUDA_TRY(t->ctx, cudaStreamSynchronize(t->ctx->stream));
+    return FDPS_OK;
+}
+
+__global__ void k_reset_counters(DevState* st, int what) {
+    if (threadIdx.x != 0) return;
+    if (what & 1) {  // walk
+        st->walk_counter = 0;
+        st->pool_cursor = 0;
+        st->pool_needed = 0;
+        st->list_entries = 0;
+        st->n_epj = 0;
+        st->n_spj = 0;
+        st->int_epj = 0;
+        st->int_spj = 0;
+        st->fallbacks = 0;
+        st->max_frontier = 0;
+        st->overflow &= ~(kOvfPool | kOvfChunk | kOvfFrontier);
+    }
+    if (what & 2) st->force_counter = 0;
+    if (what & 4) st->overflow &= ~(kOvfNodes | kOvfGroups);
+}
+
+void record(fdps_tree* t, int k) {
+    if (t->ev_ok && t->ctx->profiling) cudaEventRecord(t->ev[k], t->ctx->stream);
+}
+
+int run_force(fdps_tree* t, fdps_psys* ps, int k_spj) {
+    fdps_ctx* ctx = t->ctx;
+    const int64_t n = ps->n;
+    int rc;
+    if ((rc = ensure_particles(t, n))) return rc;
+    const int64_t nl = t->p.n_leaf, ng = t->p.n_grp;
+    if ((rc = ensure_nodes(t, std::min<int64_t>(8 * n / nl, 3 * n) + 1024))) return rc;
+    if ((rc = ensure_groups(t, std::min<int64_t>(n, 8 * n / ng + 1024)))) return rc;
+    if ((rc = ensure_pool(t, 32 * n + t->n_walk_warps * (int64_t)walk_chunk()))) return rc;
+    if ((rc = ensure_frontier(t, 4096))) return rc;
+    t->n = n;
+    t->valid = false;
+    cudaStream_t s = ctx->stream;
+    FDPS_CUDA_TRY(ctx, cudaMemsetAsync(t->st, 0, sizeof(DevState), s));
+    record(t, 0);
+    if ((rc = keys_and_sort(t, ps))) return rc;
+    record(t, 2);
+    if ((rc = reorder_particles(t, ps))) return rc;
+    record(t, 3);
+    for (int attempt = 0;; ++attempt) {
+        if ((rc = build_tree(t, ps))) return rc;
+        record(t, 4);
+        if ((rc = compute_moments(t, ps))) return rc;
+        record(t, 5);
+        if ((rc = select_groups(t, ps))) return rc;
+        record(t, 6);
+        if ((rc = read_state(t))) return rc;
+        const uint32_t ov = t->h_st.overflow;
+        if (!(ov & (kOvfNodes | kOvfGroups))) break;
+        if (attempt > 8)
+            return set_error(ctx, FDPS_EOVERFLOW, "tree build did not fit after %d resizes", attempt);
+        ++t->retries;
+        if (ov & kOvfNodes)
+            if ((rc = ensure_nodes(t, 2 * t->cap_nodes))) return rc;
+        if (ov & kOvfGroups)
+            if ((rc = ensure_groups(t, std::min<int64_t>(n, 2 * t->cap_groups)))) return rc;
+        k_reset_counters<<<1, 32, 0, s>>>(t->st, 4);
+        FDPS_LAUNCH_CHECK(ctx);
+    }
+    const int wblocks = (int)(t->n_walk_warps / walk_warps_per_block());
+    for (int attempt = 0;; ++attempt) {
+        k_reset_counters<<<1, 32, 0, s>>>(t->st, 1);
+        FDPS_LAUNCH_CHECK(ctx);
+        if ((rc = launch_walk(t, wblocks))) return rc;
+        record(t, 7);
+        if ((rc = read_state(t))) return rc;
+        const uint32_t ov = t->h_st.overflow;
+        if (!(ov & (kOvfPool | kOvfChunk | kOvfFrontier))) break;
+        if (attempt > 8)
+            return set_error(ctx, FDPS_EOVERFLOW, "interaction lists did not fit after %d resizes",
+                             attempt);
+        ++t->retries;
+        if (ov & kOvfChunk)
+            return set_error(ctx, FDPS_EOVERFLOW,
+                             "an interaction list exceeds %llu entries; lower theta or n_grp",
+                             walk_chunk());
+        if (ov & kOvfFrontier)
+            if ((rc = ensure_frontier(t, 2 * t->cap_frontier))) return rc;
+        if (ov & kOvfPool) {
+            const int64_t need = (int64_t)(t->h_st.pool_needed * 5 / 4) +
+                                 2 * t->n_walk_warps * (int64_t)walk_chunk();
+            if ((rc = ensure_pool(t, std::max<int64_t>(need, 2 * t->cap_pool)))) return rc;
+        }
+    }
+    k_reset_counters<<<1, 32, 0, s>>>(t->st, 2);
+    FDPS_LAUNCH_CHECK(ctx);
+    if ((rc = compute_forces(t, ps, k_spj))) return rc;
+    record(t, 8);
+    FDPS_CUDA_TRY(ctx, cudaGetLastError());
+    t->valid = true;
+    ps->has_forces = true;
+    return FDPS_OK;
+}
+
+bool valid_params(const fdps_tree_params* p) {
+    return p && p->theta >= 0.0 && p->theta < 1e6 && p->theta == p->theta && p->n_leaf >= 1 &&
+           p->n_leaf <= kMaxLeaf && p->n_grp >= p->n_leaf && p->n_grp <= kMaxGrp &&
+           (p->moment == FDPS_MONOPOLE || p->moment == FDPS_QUADRUPOLE) &&
+           (p->precision == FDPS_FP32REL || p->precision == FDPS_FP64) &&
+           (p->tile_depth == 0 || (p->tile_depth >= 32 && p->tile_depth <= 1024 && p->tile_depth % 32 == 0));
+}
+
+}  // namespace
+
+extern "C" {
+
+int fdps_init(int device, fdps_ctx** out) {
+    if (!out) return FDPS_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return FDPS_EINVAL;
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return FDPS_ECUDA;
+    if (!(prop.major == 10 && prop.minor == 3)) return FDPS_EINVAL;
+    fdps_ctx* ctx = new (std::nothrow) fdps_ctx();
+    if (!ctx) return FDPS_ENOMEM;
+    ctx->device = device;
+    ctx->sm_count = prop.multiProcessorCount;
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete ctx;
+        return FDPS_ECUDA;
+    }
+    ctx->stream = ctx->own_stream;
+    *out = ctx;
+    return FDPS_OK;
+}
+
+int fdps_finalize(fdps_ctx* ctx) {
+    if (!ctx) return FDPS_EINVAL;
+    cudaSetDevice(ctx->device);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    delete ctx;
+    return FDPS_OK;
+}
+
+const char* fdps_last_error(const fdps_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "no context"; }
+
+void* fdps_get_stream(const fdps_ctx* ctx) { return ctx ? (void*)ctx->stream : nullptr; }
+
+int fdps_set_stream(fdps_ctx* ctx, void* stream) {
+    if (!ctx) return FDPS_EINVAL;
+    ctx->stream = stream ? (cudaStream_t)stream : ctx->own_stream;
+    return FDPS_OK;
+}
+
+int fdps_set_profiling(fdps_ctx* ctx, int on) {
+    if (!ctx) return FDPS_EINVAL;
+    ctx->profiling = on != 0;
+    return FDPS_OK;
+}
+
+int fdps_psys_create(fdps_ctx* ctx, int64_t n, fdps_psys** out) {
+    if (!ctx || !out) return FDPS_EINVAL;
+    *out = nullptr;
+    if (n < 1 || n > 0x7FFFFFFFLL) return set_error(ctx, FDPS_EINVAL, "particle count %lld out of range", (long long)n);
+    cudaSetDevice(ctx->device);
+    fdps_psys* ps = new (std::nothrow) fdps_psys();
+    if (!ps) return FDPS_ENOMEM;
+    ps->ctx = ctx;
+    ps->n = n;
+    bool ok = true;
+    for (int b = 0; b < 2; ++b)
+        ok = ok && dev_alloc(&ps->x[b], n) == cudaSuccess && dev_alloc(&ps->y[b], n) == cudaSuccess &&
+             dev_alloc(&ps->z[b], n) == cudaSuccess && dev_alloc(&ps->vx[b], n) == cudaSuccess &&
+             dev_alloc(&ps->vy[b], n) == cudaSuccess && dev_alloc(&ps->vz[b], n) == cudaSuccess &&
+             dev_alloc(&ps->m[b], n) == cudaSuccess && dev_alloc(&ps->eps[b], n) == cudaSuccess &&
+             dev_alloc(&ps->id[b], n) == cudaSuccess;
+    ok = ok && dev_alloc(&ps->ax, n) == cudaSuccess && dev_alloc(&ps->ay, n) == cudaSuccess &&
+         dev_alloc(&ps->az, n) == cudaSuccess && dev_alloc(&ps->pot, n) == cudaSuccess &&
+         dev_alloc(&ps->d_flag, 1) == cudaSuccess &&
+         dev_alloc(&ps->d_red, energy_scratch_doubles()) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        fdps_psys_destroy(ps);
+        return set_error(ctx, FDPS_ENOMEM, "device allocation for %lld particles failed", (long long)n);
+    }
+    *out = ps;
+    return FDPS_OK;
+}
+
+int fdps_psys_destroy(fdps_psys* ps) {
+    if (!ps) return FDPS_EINVAL;
+    cudaSetDevice(ps->ctx->device);
+    for (int b = 0; b < 2; ++b) {
+        dev_free(ps->x[b]);
+        dev_free(ps->y[b]);
+        dev_free(ps->z[b]);
+        dev_free(ps->vx[b]);
+        dev_free(ps->vy[b]);
+        dev_free(ps->vz[b]);
+        dev_free(ps->m[b]);
+        dev_free(ps->eps[b]);
+        dev_free(ps->id[b]);
+    }
+    dev_free(ps->ax);
+    dev_free(ps->ay);
+    dev_free(ps->az);
+    dev_free(ps->pot);
+    dev_free(ps->d_flag);
+    dev_free(ps->d_red);
+    dev_free(ps->stage);
+    delete ps;
+    return FDPS_OK;
+}
+
+int64_t fdps_psys_size(const fdps_psys* ps) { return ps ? ps->n : -1; }
+
+int fdps_psys_set(fdps_psys* ps, const double* pos3n, const double* vel3n, const double* mass,
+                  const double* eps, int on_device) {
+    if (!ps) return FDPS_EINVAL;
+    fdps_ctx* ctx = ps->ctx;
+    if (!pos3n || !mass || !eps) return set_error(ctx, FDPS_EINVAL, "pos, mass and eps are required");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = ctx->stream;
+    const int64_t n = ps->n;
+    ps->cur = 0;
+    ps->has_data = false;
+    ps->has_forces = false;
+    if (on_device) {
+        int rc = launch_scatter_in(ps, pos3n, vel3n, mass, eps);
+        if (rc) return rc;
+    } else {
+        // host data is staged in the psys's transfer buffer
+        if (!ps->stage && dev_alloc(&ps->stage, 10 * n) != cudaSuccess) {
+            cudaGetLastError();
+            ps->stage = nullptr;
+            return set_error(ctx, FDPS_ENOMEM, "staging allocation failed");
+        }
+        double* st_pos = ps->stage;
+        double* st_vel = st_pos + 3 * n;
+        double* st_m = st_pos + 6 * n;
+        double* st_e = st_pos + 7 * n;
+        cudaError_t e1 = cudaMemcpyAsync(st_pos, pos3n, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s);
+        cudaError_t e2 = vel3n ? cudaMemcpyAsync(st_vel, vel3n, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s)
+                               : cudaSuccess;
+        cudaError_t e3 = cudaMemcpyAsync(st_m, mass, sizeof(double) * n, cudaMemcpyHostToDevice, s);
+        cudaError_t e4 = cudaMemcpyAsync(st_e, eps, sizeof(double) * n, cudaMemcpyHostToDevice, s);
+        int rc = FDPS_OK;
+        if (e1 || e2 || e3 || e4)
+            rc = set_error(ctx, FDPS_ECUDA, "host to device copy failed");
+        else
+            rc = launch_scatter_in(ps, st_pos, vel3n ? st_vel : nullptr, st_m, st_e);
+        cudaStreamSynchronize(s);
+        if (rc) return rc;
+    }
+    uint32_t bad = 0;
+    int rc = launch_validate(ps, &bad);
+    if (rc) return rc;
+    if (bad)
+        return set_error(ctx, FDPS_EINVAL, "invalid particle data:%s%s%s%s",
+                         (bad & 1) ? " non-finite position" : "", (bad & 2) ? " non-finite velocity" : "",
+                         (bad & 4) ? " negative or non-finite mass" : "",
+                         (bad & 8) ? " non-positive or non-finite eps" : "");
+    ps->has_data = true;
+    return FDPS_OK;
+}
+
+int fdps_psys_get(const fdps_psys* ps, double* pos3n, double* vel3n, double* acc3n, double* pot,
+                  int on_device) {
+    if (!ps) return FDPS_EINVAL;
+    fdps_ctx* ctx = ps->ctx;
+    if (!ps->has_data) return set_error(ctx, FDPS_ESTATE, "particle data not set");
+    if ((acc3n || pot) && !ps->has_forces)
+        return set_error(ctx, FDPS_ESTATE, "no force calculation yet");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = ctx->stream;
+    const int64_t n = ps->n;
+    if (on_device) {
+        int rc = launch_gather_out(ps, pos3n, vel3n, acc3n, pot);
+        if (rc) return rc;
+        FDPS_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        return FDPS_OK;
+    }
+    fdps_psys* pm = const_cast<fdps_psys*>(ps);
+    if (!pm->stage && dev_alloc(&pm->stage, 10 * n) != cudaSuccess) {
+        cudaGetLastError();
+        pm->stage = nullptr;
+        return set_error(ctx, FDPS_ENOMEM, "staging allocation failed");
+    }
+    double* stage = pm->stage;
+    int rc = launch_gather_out(ps, pos3n ? stage : nullptr, vel3n ? stage + 3 * n : nullptr,
+                               acc3n ? stage + 6 * n : nullptr, pot ? stage + 9 * n : nullptr);
+    cudaError_t e = cudaSuccess;
+    if (!rc) {
+        if (pos3n && !e) e = cudaMemcpyAsync(pos3n, stage, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s);
+        if (vel3n && !e) e = cudaMemcpyAsync(vel3n, stage + 3 * n, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s);
+        if (acc3n && !e) e = cudaMemcpyAsync(acc3n, stage + 6 * n, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s);
+        if (pot && !e) e = cudaMemcpyAsync(pot, stage + 9 * n, sizeof(double) * n, cudaMemcpyDeviceToHost, s);
+        cudaError_t e2 = cudaStreamSynchronize(s);
+        if (!e) e = e2;
+    }
+    if (rc) return rc;
+    if (e) return set_error(ctx, FDPS_ECUDA, "device to host copy failed: %s", cudaGetErrorString(e));
+    return FDPS_OK;
+}
+
+int fdps_tree_create(fdps_ctx* ctx, const fdps_tree_params* params, fdps_tree** out) {
+    if (!ctx || !out) return FDPS_EINVAL;
+    *out = nullptr;
+    if (!valid_params(params))
+        return set_error(ctx, FDPS_EINVAL,
+                         "invalid tree parameters (theta >= 0, 1 <= n_leaf <= %d, n_leaf <= n_grp <= %d)",
+                         kMaxLeaf, kMaxGrp);
+    cudaSetDevice(ctx->device);
+    fdps_tree* t = new (std::nothrow) fdps_tree();
+    if (!t) return FDPS_ENOMEM;
+    t->ctx = ctx;
+    t->p = *params;
+    t->box_blocks = std::min(1024, ctx->sm_count * 4);
+    t->n_walk_warps = (int64_t)walk_blocks(ctx) * walk_warps_per_block();
+    bool ok = dev_alloc(&t->st, 1) == cudaSuccess && dev_alloc(&t->box_part, t->box_blocks) == cudaSuccess &&
+              dev_alloc(&t->lvl_scan, t->box_blocks) == cudaSuccess &&
+              dev_alloc(&t->grp_scan, t->box_blocks) == cudaSuccess &&
+              dev_alloc(&t->sort_dtot, 256) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        fdps_tree_destroy(t);
+        return set_error(ctx, FDPS_ENOMEM, "tree allocation failed");
+    }
+    t->ev_ok = true;
+    for (int k = 0; k < 10; ++k)
+        if (cudaEventCreate(&t->ev[k]) != cudaSuccess) t->ev_ok = false;
+    cudaGetLastError();
+    *out = t;
+    return FDPS_OK;
+}
+
+int fdps_tree_destroy(fdps_tree* t) {
+    if (!t) return FDPS_EINVAL;
+    cudaSetDevice(t->ctx->device);
+    free_particles(t);
+    free_nodes(t);
+    free_groups(t);
+    dev_free(t->pool);
+    dev_free(t->frontier);
+    dev_free(t->st);
+    dev_free(t->box_part);
+    dev_free(t->lvl_scan);
+    dev_free(t->grp_scan);
+    dev_free(t->sort_dtot);
+    for (int k = 0; k < 10; ++k)
+        if (t->ev[k]) cudaEventDestroy(t->ev[k]);
+    delete t;
+    return FDPS_OK;
+}
+
+int fdps_tree_calc_force_all_and_write_back(fdps_tree* t, fdps_psys* ps, int k_epj, int k_spj) {
+    if (!t || !ps) return FDPS_EINVAL;
+    fdps_ctx* ctx = t->ctx;
+    if (ps->ctx != ctx) return set_error(ctx, FDPS_EINVAL, "tree and particle system belong to different contexts");
+    if (k_epj != FDPS_GRAV_EPJ) return set_error(ctx, FDPS_EINVAL, "unknown EPJ kernel id %d", k_epj);
+    if (k_spj != FDPS_GRAV_SPJ_MONO && k_spj != FDPS_GRAV_SPJ_QUAD)
+        return set_error(ctx, FDPS_EINVAL, "unknown SPJ kernel id %d", k_spj);
+    if (k_spj == FDPS_GRAV_SPJ_QUAD && t->p.moment != FDPS_QUADRUPOLE)
+        return set_error(ctx, FDPS_EINVAL, "quadrupole SPJ kernel needs a quadrupole tree");
+    if (!ps->has_data) return set_error(ctx, FDPS_ESTATE, "particle data not set");
+    cudaSetDevice(ctx->device);
+    return run_force(t, ps, k_spj);
+}
+
+int fdps_kick(fdps_psys* ps, double dt_half) {
+    if (!ps) return FDPS_EINVAL;
+    if (!ps->has_forces) return set_error(ps->ctx, FDPS_ESTATE, "no force calculation yet");
+    cudaSetDevice(ps->ctx->device);
+    return launch_kick(ps, dt_half);
+}
+
+int fdps_drift(fdps_psys* ps, double dt) {
+    if (!ps) return FDPS_EINVAL;
+    if (!ps->has_data) return set_error(ps->ctx, FDPS_ESTATE, "particle data not set");
+    cudaSetDevice(ps->ctx->device);
+    return launch_drift(ps, dt);
+}
+
+int fdps_step(fdps_tree* t, fdps_psys* ps, double dt) {
+    if (!t || !ps) return FDPS_EINVAL;
+    if (!ps->has_forces) return set_error(ps->ctx, FDPS_ESTATE, "no force calculation yet");
+    cudaSetDevice(ps->ctx->device);
+    int rc;
+    if ((rc = launch_kick(ps, 0.5 * dt))) return rc;
+    if ((rc = launch_drift(ps, dt))) return rc;
+    const int k_spj = t->p.moment == FDPS_QUADRUPOLE ? FDPS_GRAV_SPJ_QUAD : FDPS_GRAV_SPJ_MONO;
+    if ((rc = run_force(t, ps, k_spj))) return rc;
+    return launch_kick(ps, 0.5 * dt);
+}
+
+int fdps_psys_energy(fdps_psys* ps, double* kinetic, double* potential) {
+    if (!ps || !kinetic || !potential) return FDPS_EINVAL;
+    if (!ps->has_forces) return set_error(ps->ctx, FDPS_ESTATE, "no force calculation yet");
+    cudaSetDevice(ps->ctx->device);
+    return launch_energy(ps, kinetic, potential);
+}
+
+int fdps_tree_get_stats(const fdps_tree* tc, fdps_tree_stats* out) {
+    if (!tc || !out) return FDPS_EINVAL;
+    fdps_tree* t = const_cast<fdps_tree*>(tc);
+    if (!t->valid) return set_error(t->ctx, FDPS_ESTATE, "no force calculation yet");
+    int rc = read_state(t);
+    if (rc) return rc;
+    memset(out, 0, sizeof(*out));
+    const DevState& s = t->h_st;
+    out->n_particles = t->n;
+    out->n_nodes = s.n_nodes;
+    out->n_groups = s.n_groups;
+    out->n_levels = s.max_level + 1;
+    out->list_entries = (int64_t)s.list_entries;
+    out->n_epj = (int64_t)s.n_epj;
+    out->n_spj = (int64_t)s.n_spj;
+    out->interactions_epj = (int64_t)s.int_epj;
+    out->interactions_spj = (int64_t)s.int_spj;
+    out->fp64_fallbacks = (int64_t)s.fallbacks;
+    out->retries = t->retries;
+    if (t->ev_ok && t->ctx->profiling) {
+        float v[9] = {0};
+        for (int k = 0; k < 8; ++k)
+            if (cudaEventElapsedTime(&v[k], t->ev[k], t->ev[k + 1]) != cudaSuccess) v[k] = -1.f;
+        cudaGetLastError();
+        float tot = 0.f;
+        if (cudaEventElapsedTime(&tot, t->ev[0], t->ev[8]) != cudaSuccess) tot = -1.f;
+        cudaGetLastError();
+        out->ms_box_keys = v[0];
+        out->ms_sort = v[1];
+        out->ms_permute = v[2];
+        out->ms_build = v[3];
+        out->ms_moments = v[4];
+        out->ms_groups = v[5];
+        out->ms_walk = v[6];
+        out->ms_force = v[7];
+        out->ms_total = tot;
+    }
+    return FDPS_OK;
+}
+
+int fdps_tree_get_box(const fdps_tree* tc, double* out5) {
+    if (!tc || !out5) return FDPS_EINVAL;
+    fdps_tree* t = const_cast<fdps_tree*>(tc);
+    if (!t->valid) return set_error(t->ctx, FDPS_ESTATE, "no force calculation yet");
+    int rc = read_state(t);
+    if (rc) return rc;
+    for (int a = 0; a < 3; ++a) out5[a] = t->h_st.lo[a];
+    out5[3] = t->h_st.L;
+    out5[4] = t->h_st.s;
+    return FDPS_OK;
+}
+
+int fdps_tree_get_keys(const fdps_tree* tc, uint64_t* keys, uint32_t* perm, int64_t cap) {
+    if (!tc) return FDPS_EINVAL;
+    fdps_tree* t = const_cast<fdps_tree*>(tc);
+    if (!t->valid) return set_error(t->ctx, FDPS_ESTATE, "no force calculation yet");
+    if (cap < t->n) return set_error(t->ctx, FDPS_EOVERFLOW, "capacity %lld < %lld", (long long)cap, (long long)t->n);
+    cudaStream_t s = t->ctx->stream;
+    if (keys) FDPS_CUDA_TRY(t->ctx, cudaMemcpyAsync(keys, t->keys_in, 8 * t->n, cudaMemcpyDeviceToHost, s));
+    if (perm) FDPS_CUDA_TRY(t->ctx, cudaMemcpyAsync(perm, t->perm, 4 * t->n, cudaMemcpyDeviceToHost, s));
+    FDPS_CUDA_TRY(t->ctx, cudaStreamSynchronize(s));
+    return FDPS_OK;
+}
+
+int fdps_tree_get_nodes(const fdps_tree* tc, int64_t cap, int64_t* n_out, int32_t* level, int64_t* first,
+                        int64_t* count, int64_t* child_first, int32_t* nchild, double* mass, double* com,
+                        double* quad) {
+    if (!tc) return FDPS_EINVAL;
+    fdps_tree* t = const_cast<fdps_tree*>(tc);
+    if (!t->valid) return set_error(t->ctx, FDPS_ESTATE, "no force calculation yet");
+    int rc = read_state(t);
+    if (rc) return rc;
+    const int64_t nn = t->h_st.n_nodes;
+    if (n_out) *n_out = nn;
+    if (cap < nn) return set_error(t->ctx, FDPS_EOVERFLOW, "capacity %lld < %lld nodes", (long long)cap, (long long)nn);
+    cudaStream_t s = t->ctx->stream;
+    uint32_t* h32 = (uint32_t*)malloc(4 * (size_t)nn * 4 + 1);
+    double* h64 = (double*)malloc(sizeof(double) * (size_t)nn * 6 + 8);
+    if (!h32 || !h64) {
+        free(h32);
+        free(h64);
+        return set_error(t->ctx, FDPS_ENOMEM, "host allocation failed");
+    }
+    uint32_t *hf = h32, *hc = h32 + nn, *hch = h32 + 2 * nn, *hm = h32 + 3 * nn;
+    cudaError_t e = cudaMemcpyAsync(hf, t->nd_first, 4 * nn, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(hc, t->nd_count, 4 * nn, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(hch, t->nd_child, 4 * nn, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(hm, t->nd_meta, 4 * nn, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (!e) {
+        for (int64_t i = 0; i < nn; ++i) {
+            const bool leaf = (hm[i] >> 16) & 1u;
+            if (level) level[i] = (int32_t)(hm[i] & 0xFFu);
+            if (first) first[i] = hf[i];
+            if (count) count[i] = hc[i];
+            if (child_first) child_first[i] = leaf ? -1 : (int64_t)hch[i];
+            if (nchild) nchild[i] = leaf ? 0 : (int32_t)((hm[i] >> 8) & 0xFFu);
+        }
+        if (mass || com) {
+            e = cudaMemcpyAsync(h64, t->nd_com, sizeof(dvec4) * nn, cudaMemcpyDeviceToHost, s);
+            if (!e) e = cudaStreamSynchronize(s);
+            for (int64_t i = 0; !e && i < nn; ++i) {
+                if (mass) mass[i] = h64[4 * i + 3];
+                if (com)
+                    for (int a = 0; a < 3; ++a) com[3 * i + a] = h64[4 * i + a];
+            }
+        }
+        if (quad && !e) {
+            if (t->p.moment == FDPS_QUADRUPOLE) {
+                e = cudaMemcpyAsync(quad, t->nd_quad, sizeof(double) * 6 * nn, cudaMemcpyDeviceToHost, s);
+                if (!e) e = cudaStreamSynchronize(s);
+            } else {
+                memset(quad, 0, sizeof(double) * 6 * nn);
+            }
+        }
+    }
+    free(h32);
+    free(h64);
+    if (e) return set_error(t->ctx, FDPS_ECUDA, "node readback failed: %s", cudaGetErrorString(e));
+    return FDPS_OK;
+}
+
+int fdps_tree_get_groups(const fdps_tree* tc, int64_t cap, int64_t* n_out, int64_t* first, int64_t* count,
+                         int64_t* node, double* box6) {
+    if (!tc) return FDPS_EINVAL;
+    fdps_tree* t = const_cast<fdps_tree*>(tc);
+    if (!t->valid) return set_error(t->ctx, FDPS_ESTATE, "no force calculation yet");
+    int rc = read_state(t);
+    if (rc) return rc;
+    const int64_t ng = t->h_st.n_groups;
+    if (n_out) *n_out = ng;
+    if (cap < ng) return set_error(t->ctx, FDPS_EOVERFLOW, "capacity %lld < %lld groups", (long long)cap, (long long)ng);
+    cudaStream_t s = t->ctx->stream;
+    uint32_t* h = (uint32_t*)malloc(4 * (size_t)ng * 3 + 4);
+    if (!h) return set_error(t->ctx, FDPS_ENOMEM, "host allocation failed");
+    cudaError_t e = cudaMemcpyAsync(h, t->g_first, 4 * ng, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(h + ng, t->g_count, 4 * ng, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(h + 2 * ng, t->g_node, 4 * ng, cudaMemcpyDeviceToHost, s);
+    if (!e && box6) e = cudaMemcpyAsync(box6, t->g_box, sizeof(double) * 6 * ng, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (!e)
+        for (int64_t g = 0; g < ng; ++g) {
+            if (first) first[g] = h[g];
+            if (count) count[g] = h[ng + g];
+            if (node) node[g] = h[2 * ng + g];
+        }
+    free(h);
+    if (e) return set_error(t->ctx, FDPS_ECUDA, "group readback failed: %s", cudaGetErrorString(e));
+    return FDPS_OK;
+}
+
+int fdps_tree_get_lists(const fdps_tree* tc, int64_t g0, int64_t g1, int64_t* offsets, uint32_t* entries,
+                        int64_t cap) {
+    if (!tc || !offsets) return FDPS_EINVAL;
+    fdps_tree* t = const_cast<fdps_tree*>(tc);
+    if (!t->valid) return set_error(t->ctx, FDPS_ESTATE, "no force calculation yet");
+    int rc = read_state(t);
+    if (rc) return rc;
+    const int64_t ng = t->h_st.n_groups;
+    if (g0 < 0 || g1 < g0 || g1 > ng) return set_error(t->ctx, FDPS_EINVAL, "group range [%lld, %lld) out of [0, %lld)", (long long)g0, (long long)g1, (long long)ng);
+    const int64_t m = g1 - g0;
+    cudaStream_t s = t->ctx->stream;
+    unsigned long long* hoff = (unsigned long long*)malloc(8 * (size_t)m + 8);
+    uint32_t* hlen = (uint32_t*)malloc(4 * (size_t)m + 4);
+    if (!hoff || !hlen) {
+        free(hoff);
+        free(hlen);
+        return set_error(t->ctx, FDPS_ENOMEM, "host allocation failed");
+    }
+    cudaError_t e = cudaMemcpyAsync(hoff, t->g_off + g0, 8 * m, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(hlen, t->g_len + g0, 4 * m, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    int64_t tot = 0;
+    offsets[0] = 0;
+    for (int64_t k = 0; !e && k < m; ++k) {
+        tot += hlen[k];
+        offsets[k + 1] = tot;
+    }
+    if (!e && entries) {
+        if (tot > cap) {
+            free(hoff);
+            free(hlen);
+            return set_error(t->ctx, FDPS_EOVERFLOW, "capacity %lld < %lld entries", (long long)cap, (long long)tot);
+        }
+        for (int64_t k = 0; !e && k < m; ++k)
+            if (hlen[k]) e = cudaMemcpyAsync(entries + offsets[k], t->pool + hoff[k], 4 * (size_t)hlen[k], cudaMemcpyDeviceToHost, s);
+        if (!e) e = cudaStreamSynchronize(s);
+    }
+    free(hoff);
+    free(hlen);
+    if (e) return set_error(t->ctx, FDPS_ECUDA, "list readback failed: %s", cudaGetErrorString(e));
+    return FDPS_OK;
+}
+
+}  // extern "C"

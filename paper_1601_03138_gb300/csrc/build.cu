@@ -1,0 +1,553 @@
+// build.cu -- level-parallel octree build, bottom-up moments and i-groups.
+//
+// Octree (the Barnes-Hut tree of Sect. 3.2; its rules are this library's
+// reading): a node is a (level l, key prefix) pair holding >= 1 particle; it
+// is a leaf iff it holds <= n_leaf particles or l = 21; an internal node's
+// children are its non-empty octants in digit order.  Node ids are BFS
+// order: level-major, prefix ascending.  Level l+1 is produced from level l
+// in three launches: per (parent, octant) slot a binary search of the
+// sorted keys for the octant's first particle, a scan of non-empty slots,
+// and the writes.
+//
+// Moments: M and S = sum m x are accumulated in FP64 with explicitly
+// rounded adds and multiplies (no FMA), leaves sequentially over their
+// particles, internal nodes sequentially over their children in octant
+// order; COM = S / M.  These fixed orders make the centres of mass, and
+// thus the opening decisions of the walk, reproducible bit for bit.  The
+// traceless quadrupole Q_ab = sum m (3 d_a d_b - |d|^2 delta_ab) about the
+// COM (Sect. 2.1.2: "up to the quadrupole moment") is summed over particles
+// for leaves and combined from the children with the parallel-axis shift
+// for internal nodes.
+//
+// i-groups (Barnes 1990; Sect. 5.5): the maximal nodes with <= n_grp
+// particles, and leaves with more (possible only at level 21), in order of
+// their first particle.
+#include "fdps_internal.cuh"
+
+namespace fdps {
+namespace {
+
+constexpr int kB = 256;  // block size of the partitioned kernels
+
+// Contiguous tile range [t0, t1) of block b when `ntile` tiles of kB items
+// are split over gridDim.x blocks; the same split in every launch keeps the
+// per-block partial sums consistent between the count and write kernels.
+__device__ __forceinline__ void block_tiles(int64_t nitems, int64_t* t0, int64_t* t1) {
+    int64_t ntile = (nitems + kB - 1) / kB;
+    int64_t per = (ntile + gridDim.x - 1) / gridDim.x;
+    *t0 = blockIdx.x * per;
+    *t1 = *t0 + per < ntile ? *t0 + per : ntile;
+}
+
+__device__ __forceinline__ uint32_t block_sum(uint32_t v) {
+    __shared__ uint32_t s[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, off);
+    if (lane == 0) s[w] = v;
+    __syncthreads();
+    uint32_t r = 0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r += s[k];
+    __syncthreads();
+    return r;  // valid in thread 0
+}
+
+__device__ __forceinline__ uint32_t block_excl(uint32_t v, uint32_t* total) {
+    __shared__ uint32_t s_w[33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        uint32_t t = __shfl_up_sync(0xFFFFFFFFu, inc, off);
+        if (lane >= off) inc += t;
+    }
+    if (lane == 31) s_w[w] = inc;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    if (w == 0) {
+        uint32_t t = lane < nw ? s_w[lane] : 0u;
+        uint32_t ti = t;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            uint32_t u = __shfl_up_sync(0xFFFFFFFFu, ti, off);
+            if (lane >= off) ti += u;
+        }
+        if (lane < nw) s_w[lane] = ti - t;
+        if (lane == nw - 1) s_w[32] = ti;
+    }
+    __syncthreads();
+    uint32_t res = s_w[w] + inc - v;
+    *total = s_w[32];
+    __syncthreads();
+    return res;
+}
+
+// Exclusive scan of part[0..np) in one block; returns the total in *tot.
+__device__ void scan_partials(uint32_t* part, int np, uint32_t* tot) {
+    const int per = (np + blockDim.x - 1) / blockDim.x;
+    const int b = threadIdx.x * per;
+    uint32_t sum = 0;
+    for (int k = 0; k < per; ++k)
+        if (b + k < np) sum += part[b + k];
+    uint32_t total;
+    uint32_t off = block_excl(sum, &total);
+    for (int k = 0; k < per; ++k)
+        if (b + k < np) {
+            uint32_t c = part[b + k];
+            part[b + k] = off;
+            off += c;
+        }
+    *tot = total;
+}
+
+__device__ __forceinline__ uint32_t meta_level(uint32_t m) { return m & 0xFFu; }
+__device__ __forceinline__ uint32_t meta_nchild(uint32_t m) { return (m >> 8) & 0xFFu; }
+__device__ __forceinline__ bool meta_leaf(uint32_t m) { return (m >> 16) & 1u; }
+
+__global__ void k_root(DevState* st, int64_t n, int n_leaf, uint32_t* nd_first, uint32_t* nd_count,
+                       uint32_t* nd_child, uint32_t* nd_meta, uint32_t* nd_parent, uint64_t* nd_qlo,
+                       uint64_t* nd_prefix) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    nd_first[0] = 0;
+    nd_count[0] = (uint32_t)n;
+    nd_child[0] = 0xFFFFFFFFu;
+    nd_meta[0] = (n <= n_leaf ? 1u : 0u) << 16;
+    nd_parent[0] = 0xFFFFFFFFu;
+    nd_qlo[0] = 0;
+    nd_prefix[0] = 0;
+    st->lvl_start[0] = 0;
+    for (int l = 1; l < kMaxLevel + 3; ++l) st->lvl_start[l] = 1;
+    st->n_nodes = 1;
+    st->max_level = 0;
+}
+
+// Slot s = 8 * (parent - first parent of the level) + octant.
+__global__ void __launch_bounds__(kB) k_level_count(int l, const DevState* __restrict__ st,
+                                                    const uint64_t* __restrict__ keys,
+                                                    const uint32_t* __restrict__ nd_first,
+                                                    const uint32_t* __restrict__ nd_count,
+                                                    const uint32_t* __restrict__ nd_meta,
+                                                    uint32_t* __restrict__ slot_lb,
+                                                    uint32_t* __restrict__ slot_cnt,
+                                                    uint32_t* __restrict__ part) {
+    const int64_t P0 = st->lvl_start[l - 1], P1 = st->lvl_start[l];
+    const int64_t nslots = 8 * (P1 - P0);
+    int64_t t0, t1;
+    block_tiles(nslots, &t0, &t1);
+    const int shift = 63 - 3 * l;
+    uint32_t nonempty = 0;
+    for (int64_t t = t0; t < t1; ++t) {
+        const int64_t s = t * kB + threadIdx.x;
+        const int d = (int)(s & 7);
+        uint32_t lb = 0, end = 0;
+        bool internal = false;
+        if (s < nslots) {
+            const int64_t p = P0 + (s >> 3);
+            internal = !meta_leaf(nd_meta[p]);
+            const uint32_t f = nd_first[p];
+            end = f + nd_count[p];
+            if (internal) {
+                if (d == 0) {
+                    lb = f;
+                } else {  // first index in [f, end) whose digit at level l is >= d
+                    uint32_t lo = f, hi = end;
+                    while (lo < hi) {
+                        uint32_t mid = lo + ((hi - lo) >> 1);
+                        if ((uint32_t)((keys[mid] >> shift) & 7u) < (uint32_t)d)
+                            lo = mid + 1;
+                        else
+                            hi = mid;
+                    }
+                    lb = lo;
+                }
+            }
+        }
+        uint32_t nxt = __shfl_down_sync(0xFFFFFFFFu, lb, 1, 8);
+        if (d == 7) nxt = end;
+        uint32_t cnt = internal ? nxt - lb : 0u;
+        if (s < nslots) {
+            slot_lb[s] = lb;
+            slot_cnt[s] = cnt;
+        }
+        nonempty += cnt > 0 ? 1u : 0u;
+    }
+    uint32_t tot = block_sum(nonempty);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_level_scan(int l, DevState* st, uint32_t* part, int np,
+                                                     int64_t cap_nodes) {
+    uint32_t tot;
+    scan_partials(part, np, &tot);
+    if (threadIdx.x == 0) {
+        int64_t start = st->lvl_start[l];
+        int64_t end = start + tot;
+        if (end > cap_nodes) {
+            st->overflow |= kOvfNodes;
+            end = start;  // write no node of this level; later levels stay empty
+        }
+        for (int k = l + 1; k < kMaxLevel + 3; ++k) st->lvl_start[k] = (int32_t)end;
+        st->n_nodes = (int32_t)end;
+        if (end > start) st->max_level = l;
+    }
+}
+
+__global__ void __launch_bounds__(kB) k_level_write(
+    int l, int n_leaf, const DevState* __restrict__ st, const uint32_t* __restrict__ slot_lb,
+    const uint32_t* __restrict__ slot_cnt, const uint32_t* __restrict__ part,
+    uint32_t* __restrict__ nd_first, uint32_t* __restrict__ nd_count, uint32_t* __restrict__ nd_child,
+    uint32_t* __restrict__ nd_meta, uint32_t* __restrict__ nd_parent, uint64_t* __restrict__ nd_qlo,
+    uint64_t* __restrict__ nd_prefix) {
+    const int64_t P0 = st->lvl_start[l - 1], P1 = st->lvl_start[l];
+    const int64_t C0 = st->lvl_start[l], C1 = st->lvl_start[l + 1];
+    if (C1 == C0) return;  // empty level (or capacity exceeded): uniform exit
+    const int64_t nslots = 8 * (P1 - P0);
+    int64_t t0, t1;
+    block_tiles(nslots, &t0, &t1);
+    uint32_t running = part[blockIdx.x];
+    const int lane = threadIdx.x & 31;
+    const int sh = kMaxLevel - l;
+    for (int64_t t = t0; t < t1; ++t) {
+        const int64_t s = t * kB + threadIdx.x;
+        const uint32_t cnt = s < nslots ? slot_cnt[s] : 0u;
+        const uint32_t flag = cnt > 0 ? 1u : 0u;
+        uint32_t tile_tot;
+        const uint32_t rank = block_excl(flag, &tile_tot);
+        const uint32_t gm = (__ballot_sync(0xFFFFFFFFu, flag) >> (lane & ~7)) & 0xFFu;
+        if (flag) {
+            const int d = (int)(s & 7);
+            const int64_t p = P0 + (s >> 3);
+            const int64_t id = C0 + running + rank;
+            nd_first[id] = slot_lb[s];
+            nd_count[id] = cnt;
+            nd_child[id] = 0xFFFFFFFFu;
+            nd_meta[id] = (uint32_t)l | ((cnt <= (uint32_t)n_leaf || l == kMaxLevel) ? 1u : 0u) << 16;
+            nd_parent[id] = (uint32_t)p;
+            const uint64_t pq = nd_qlo[p];
+            const uint64_t add = ((uint64_t)((d >> 2) & 1) << (42 + sh)) |
+                                 ((uint64_t)((d >> 1) & 1) << (21 + sh)) | ((uint64_t)(d & 1) << sh);
+            nd_qlo[id] = pq | add;
+            nd_prefix[id] = (nd_prefix[p] << 3) | (uint64_t)d;
+            if (d == __ffs(gm) - 1) {  // first non-empty octant: parent's child range
+                nd_child[p] = (uint32_t)id;
+                nd_meta[p] = (uint32_t)(l - 1) | ((uint32_t)__popc(gm) << 8);
+            }
+        }
+        running += tile_tot;
+    }
+}
+
+// ------------------------------------------------------------ moments
+
+__device__ __forceinline__ void split_hilo(double v, float* hi, float* lo) {
+    float h = __double2float_rn(v);
+    *hi = h;
+    *lo = __double2float_rn(v - (double)h);
+}
+
+template <bool QUAD>
+__global__ void __launch_bounds__(256) k_moments_level(
+    int l, const DevState* __restrict__ st, const double* __restrict__ px,
+    const double* __restrict__ py, const double* __restrict__ pz, const double* __restrict__ pm,
+    const uint32_t* __restrict__ nd_first, const uint32_t* __restrict__ nd_count,
+    const uint32_t* __restrict__ nd_child, const uint32_t* __restrict__ nd_meta,
+    double* __restrict__ nd_sx, double* __restrict__ nd_sy, double* __restrict__ nd_sz,
+    dvec4* __restrict__ nd_com, double* __restrict__ nd_quad, float4* __restrict__ nd_fh,
+    float4* __restrict__ nd_fl, float4* __restrict__ nd_fq0, float2* __restrict__ nd_fq1) {
+    const int64_t a = st->lvl_start[l], b = st->lvl_start[l + 1];
+    const double c0x = st->c0[0], c0y = st->c0[1], c0z = st->c0[2];
+    for (int64_t i = a + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < b;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t meta = nd_meta[i];
+        double M = 0.0, Sx = 0.0, Sy = 0.0, Sz = 0.0;
+        const bool leaf = meta_leaf(meta);
+        const uint32_t f = nd_first[i], cnt = nd_count[i];
+        const uint32_t c0 = nd_child[i], nc = meta_nchild(meta);
+        if (leaf) {
+            for (uint32_t p = f; p < f + cnt; ++p) {
+                const double m = pm[p];
+                M = __dadd_rn(M, m);
+                Sx = __dadd_rn(Sx, __dmul_rn(m, px[p]));
+                Sy = __dadd_rn(Sy, __dmul_rn(m, py[p]));
+                Sz = __dadd_rn(Sz, __dmul_rn(m, pz[p]));
+            }
+        } else {
+            for (uint32_t c = c0; c < c0 + nc; ++c) {
+                M = __dadd_rn(M, nd_com[c].w);
+                Sx = __dadd_rn(Sx, nd_sx[c]);
+                Sy = __dadd_rn(Sy, nd_sy[c]);
+                Sz = __dadd_rn(Sz, nd_sz[c]);
+            }
+        }
+        double cx = 0.0, cy = 0.0, cz = 0.0;
+        if (M > 0.0) {
+            cx = __ddiv_rn(Sx, M);
+            cy = __ddiv_rn(Sy, M);
+            cz = __ddiv_rn(Sz, M);
+        }
+        nd_sx[i] = Sx;
+        nd_sy[i] = Sy;
+        nd_sz[i] = Sz;
+        nd_com[i] = make_dvec4(cx, cy, cz, M);
+        float hx, hy, hz, lx, ly, lz;
+        split_hilo(cx - c0x, &hx, &lx);
+        split_hilo(cy - c0y, &hy, &ly);
+        split_hilo(cz - c0z, &hz, &lz);
+        nd_fh[i] = make_float4(hx, hy, hz, __double2float_rn(M));
+        nd_fl[i] = make_float4(lx, ly, lz, 0.0f);
+        if (QUAD) {
+            double q[6] = {0, 0, 0, 0, 0, 0};
+            if (leaf) {
+                for (uint32_t p = f; p < f + cnt; ++p) {
+                    const double m = pm[p];
+                    const double dx = px[p] - cx, dy = py[p] - cy, dz = pz[p] - cz;
+                    const double d2 = dx * dx + dy * dy + dz * dz;
+                    q[0] += m * (3.0 * dx * dx - d2);
+                    q[1] += m * (3.0 * dy * dy - d2);
+                    q[2] += m * (3.0 * dz * dz - d2);
+                    q[3] += m * (3.0 * dx * dy);
+                    q[4] += m * (3.0 * dx * dz);
+                    q[5] += m * (3.0 * dy * dz);
+                }
+            } else {
+                for (uint32_t c = c0; c < c0 + nc; ++c) {
+                    const dvec4 cc = nd_com[c];
+                    const double dx = cc.x - cx, dy = cc.y - cy, dz = cc.z - cz;
+                    const double d2 = dx * dx + dy * dy + dz * dz;
+                    const double* qc = nd_quad + 6 * (int64_t)c;
+                    q[0] += qc[0] + cc.w * (3.0 * dx * dx - d2);
+                    q[1] += qc[1] + cc.w * (3.0 * dy * dy - d2);
+                    q[2] += qc[2] + cc.w * (3.0 * dz * dz - d2);
+                    q[3] += qc[3] + cc.w * (3.0 * dx * dy);
+                    q[4] += qc[4] + cc.w * (3.0 * dx * dz);
+                    q[5] += qc[5] + cc.w * (3.0 * dy * dz);
+                }
+            }
+            double* qo = nd_quad + 6 * i;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) qo[k] = q[k];
+            nd_fq0[i] = make_float4((float)q[0], (float)q[1], (float)q[2], (float)q[3]);
+            nd_fq1[i] = make_float2((float)q[4], (float)q[5]);
+        }
+    }
+}
+
+// ------------------------------------------------------------- groups
+
+__global__ void __launch_bounds__(256) k_group_mark(const DevState* __restrict__ st, int n_grp,
+                                                    const uint32_t* __restrict__ nd_first,
+                                                    const uint32_t* __restrict__ nd_count,
+                                                    const uint32_t* __restrict__ nd_meta,
+                                                    const uint32_t* __restrict__ nd_parent,
+                                                    uint32_t* __restrict__ head) {
+    const int64_t nn = st->n_nodes;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = nd_count[i];
+        const bool cand = c <= (uint32_t)n_grp || meta_leaf(nd_meta[i]);
+        if (cand && (i == 0 || nd_count[nd_parent[i]] > (uint32_t)n_grp)) head[nd_first[i]] = (uint32_t)i;
+    }
+}
+
+__global__ void __launch_bounds__(kB) k_group_count(int64_t n, const uint32_t* __restrict__ head,
+                                                    uint32_t* __restrict__ part) {
+    int64_t t0, t1;
+    block_tiles(n, &t0, &t1);
+    uint32_t c = 0;
+    for (int64_t t = t0; t < t1; ++t) {
+        const int64_t i = t * kB + threadIdx.x;
+        if (i < n && head[i] != 0xFFFFFFFFu) ++c;
+    }
+    uint32_t tot = block_sum(c);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_group_scan(DevState* st, uint32_t* part, int np,
+                                                     int64_t cap_groups) {
+    uint32_t tot;
+    scan_partials(part, np, &tot);
+    if (threadIdx.x == 0) {
+        if ((int64_t)tot > cap_groups) st->overflow |= kOvfGroups;
+        st->n_groups = (int32_t)((int64_t)tot > cap_groups ? cap_groups : tot);
+    }
+}
+
+__global__ void __launch_bounds__(kB) k_group_write(int64_t n, int64_t cap_groups,
+                                                    const uint32_t* __restrict__ head,
+                                                    const uint32_t* __restrict__ part,
+                                                    const uint32_t* __restrict__ nd_count,
+                                                    uint32_t* __restrict__ g_node,
+                                                    uint32_t* __restrict__ g_first,
+                                                    uint32_t* __restrict__ g_count) {
+    int64_t t0, t1;
+    block_tiles(n, &t0, &t1);
+    uint32_t running = part[blockIdx.x];
+    for (int64_t t = t0; t < t1; ++t) {
+        const int64_t i = t * kB + threadIdx.x;
+        const uint32_t h = i < n ? head[i] : 0xFFFFFFFFu;
+        const uint32_t flag = h != 0xFFFFFFFFu ? 1u : 0u;
+        uint32_t tot;
+        const uint32_t rank = block_excl(flag, &tot);
+        if (flag) {
+            const int64_t g = (int64_t)running + rank;
+            if (g < cap_groups) {
+                g_node[g] = h;
+                g_first[g] = (uint32_t)i;
+                g_count[g] = nd_count[h];
+            }
+        }
+        running += tot;
+    }
+}
+
+__device__ __forceinline__ unsigned long long ord64(double v) {
+    unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double unord64(unsigned long long o) {
+    unsigned long long u = (o >> 63) ? (o & 0x7FFFFFFFFFFFFFFFull) : ~o;
+    return __longlong_as_double((long long)u);
+}
+__device__ __forceinline__ uint32_t quantise(double x, double lo, double s) {
+    double t = __dsub_rn(x, lo);
+    double u = __dmul_rn(t, s);
+    double f = floor(u);
+    f = f > (double)kQMax ? (double)kQMax : f;
+    f = f < 0.0 ? 0.0 : f;
+    return (uint32_t)f;
+}
+
+// One warp per group: FP64 box (min / max over the particles), its grid
+// box (the quantised corners: quantisation is monotone, so these are the
+// minimum and maximum grid coordinates of the particles), FP64 centre and
+// the FP32 copies the walk's filter and the force kernel use.
+__global__ void __launch_bounds__(256) k_group_data(
+    const DevState* __restrict__ st, const uint32_t* __restrict__ g_first,
+    const uint32_t* __restrict__ g_count, const double* __restrict__ px,
+    const double* __restrict__ py, const double* __restrict__ pz, double* __restrict__ g_box,
+    uint32_t* __restrict__ g_qbox, dvec4* __restrict__ g_c64, float4* __restrict__ g_ch,
+    float4* __restrict__ g_cl, float4* __restrict__ g_blo, float4* __restrict__ g_bhi) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t ng = st->n_groups;
+    const double lo0 = st->lo[0], lo1 = st->lo[1], lo2 = st->lo[2], s = st->s;
+    const double c0x = st->c0[0], c0y = st->c0[1], c0z = st->c0[2];
+    for (int64_t g = warp; g < ng; g += nwarps) {
+        const uint32_t f = g_first[g], c = g_count[g];
+        unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
+        for (uint32_t p = f + lane; p < f + c; p += 32) {
+            unsigned long long v[3] = {ord64(px[p]), ord64(py[p]), ord64(pz[p])};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = v[a] < lo[a] ? v[a] : lo[a];
+                hi[a] = v[a] > hi[a] ? v[a] : hi[a];
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                unsigned long long l2 = __shfl_xor_sync(0xFFFFFFFFu, lo[a], off);
+                unsigned long long h2 = __shfl_xor_sync(0xFFFFFFFFu, hi[a], off);
+                lo[a] = l2 < lo[a] ? l2 : lo[a];
+                hi[a] = h2 > hi[a] ? h2 : hi[a];
+            }
+        if (lane == 0) {
+            double bl[3], bh[3], cc[3];
+            const double lo_r[3] = {lo0, lo1, lo2};
+            const double c0r[3] = {c0x, c0y, c0z};
+            float ch[3], cl[3], fl[3], fh[3];
+            for (int a = 0; a < 3; ++a) {
+                bl[a] = unord64(lo[a]);
+                bh[a] = unord64(hi[a]);
+                g_box[6 * g + a] = bl[a];
+                g_box[6 * g + 3 + a] = bh[a];
+                g_qbox[6 * g + a] = quantise(bl[a], lo_r[a], s);
+                g_qbox[6 * g + 3 + a] = quantise(bh[a], lo_r[a], s);
+                cc[a] = __dmul_rn(__dadd_rn(bl[a], bh[a]), 0.5);
+                split_hilo(cc[a] - c0r[a], &ch[a], &cl[a]);
+                fl[a] = __double2float_rd(bl[a] - cc[a]);
+                fh[a] = __double2float_ru(bh[a] - cc[a]);
+            }
+            g_c64[g] = make_dvec4(cc[0], cc[1], cc[2], 0.0);
+            g_ch[g] = make_float4(ch[0], ch[1], ch[2], 0.0f);
+            g_cl[g] = make_float4(cl[0], cl[1], cl[2], 0.0f);
+            g_blo[g] = make_float4(fl[0], fl[1], fl[2], 0.0f);
+            g_bhi[g] = make_float4(fh[0], fh[1], fh[2], 0.0f);
+        }
+    }
+}
+
+}  // namespace
+
+int build_tree(fdps_tree* t, fdps_psys* ps) {
+    fdps_ctx* ctx = t->ctx;
+    cudaStream_t s = ctx->stream;
+    const int G = t->box_blocks;  // partition width of the level kernels
+    k_root<<<1, 32, 0, s>>>(t->st, ps->n, t->p.n_leaf, t->nd_first, t->nd_count, t->nd_child,
+                            t->nd_meta, t->nd_parent, t->nd_qlo, t->nd_prefix);
+    FDPS_LAUNCH_CHECK(ctx);
+    uint32_t* slot_lb = t->lvl_scratch;
+    uint32_t* slot_cnt = t->lvl_scratch + 8 * t->cap_nodes;
+    for (int l = 1; l <= kMaxLevel; ++l) {
+        k_level_count<<<G, kB, 0, s>>>(l, t->st, t->keys_sorted, t->nd_first, t->nd_count,
+                                       t->nd_meta, slot_lb, slot_cnt, t->lvl_scan);
+        FDPS_LAUNCH_CHECK(ctx);
+        k_level_scan<<<1, 1024, 0, s>>>(l, t->st, t->lvl_scan, G, t->cap_nodes);
+        FDPS_LAUNCH_CHECK(ctx);
+        k_level_write<<<G, kB, 0, s>>>(l, t->p.n_leaf, t->st, slot_lb, slot_cnt, t->lvl_scan,
+                                       t->nd_first, t->nd_count, t->nd_child, t->nd_meta,
+                                       t->nd_parent, t->nd_qlo, t->nd_prefix);
+        FDPS_LAUNCH_CHECK(ctx);
+    }
+    return FDPS_OK;
+}
+
+int compute_moments(fdps_tree* t, fdps_psys* ps) {
+    fdps_ctx* ctx = t->ctx;
+    cudaStream_t s = ctx->stream;
+    const int c = ps->cur;
+    const int grid = ctx->sm_count * 8;
+    for (int l = kMaxLevel; l >= 0; --l) {
+        if (t->p.moment == FDPS_QUADRUPOLE)
+            k_moments_level<true><<<grid, 256, 0, s>>>(
+                l, t->st, ps->x[c], ps->y[c], ps->z[c], ps->m[c], t->nd_first, t->nd_count,
+                t->nd_child, t->nd_meta, t->nd_sx, t->nd_sy, t->nd_sz, t->nd_com, t->nd_quad,
+                t->nd_fh, t->nd_fl, t->nd_fq0, t->nd_fq1);
+        else
+            k_moments_level<false><<<grid, 256, 0, s>>>(
+                l, t->st, ps->x[c], ps->y[c], ps->z[c], ps->m[c], t->nd_first, t->nd_count,
+                t->nd_child, t->nd_meta, t->nd_sx, t->nd_sy, t->nd_sz, t->nd_com, t->nd_quad,
+                t->nd_fh, t->nd_fl, t->nd_fq0, t->nd_fq1);
+        FDPS_LAUNCH_CHECK(ctx);
+    }
+    return FDPS_OK;
+}
+
+int select_groups(fdps_tree* t, fdps_psys* ps) {
+    fdps_ctx* ctx = t->ctx;
+    cudaStream_t s = ctx->stream;
+    const int64_t n = ps->n;
+    const int c = ps->cur;
+    const int G = t->box_blocks;
+    FDPS_CUDA_TRY(ctx, cudaMemsetAsync(t->head, 0xFF, sizeof(uint32_t) * (size_t)n, s));
+    k_group_mark<<<ctx->sm_count * 8, 256, 0, s>>>(t->st, t->p.n_grp, t->nd_first, t->nd_count,
+                                                   t->nd_meta, t->nd_parent, t->head);
+    FDPS_LAUNCH_CHECK(ctx);
+    k_group_count<<<G, kB, 0, s>>>(n, t->head, t->grp_scan);
+    FDPS_LAUNCH_CHECK(ctx);
+    k_group_scan<<<1, 1024, 0, s>>>(t->st, t->grp_scan, G, t->cap_groups);
+    FDPS_LAUNCH_CHECK(ctx);
+    k_group_write<<<G, kB, 0, s>>>(n, t->cap_groups, t->head, t->grp_scan, t->nd_count, t->g_node,
+                                   t->g_first, t->g_count);
+    FDPS_LAUNCH_CHECK(ctx);
+    k_group_data<<<ctx->sm_count * 8, 256, 0, s>>>(t->st, t->g_first, t->g_count, ps->x[c],
+                                                   ps->y[c], ps->z[c], t->g_box, t->g_qbox,
+                                                   t->g_c64, t->g_ch, t->g_cl, t->g_blo, t->g_bhi);
+    FDPS_LAUNCH_CHECK(ctx);
+    return FDPS_OK;
+}
+
+}  // namespace fdps

@@ -1,0 +1,257 @@
+// fdps_internal.cuh -- internal data layout of the CUDA Barnes-Hut library.
+//
+// Device memory is SoA.  Particles of a psys live in the order of the last
+// force calculation (Morton order after the first call); `id` maps that
+// order back to the caller's rows.  The tree keeps its own per-particle
+// scratch (keys, sort buffers, FP32 hi/lo copies of the positions) and the
+// node / group / list tables, all sized for the largest system seen and
+// grown on demand.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <string>
+
+#include "../../include/fdps_gpu.h"
+
+namespace fdps {
+
+// Four doubles on a 32-byte boundary (one 256-bit load).
+struct __align__(32) dvec4 {
+    double x, y, z, w;
+};
+__host__ __device__ __forceinline__ dvec4 make_dvec4(double x, double y, double z, double w) {
+    dvec4 v;
+    v.x = x;
+    v.y = y;
+    v.z = z;
+    v.w = w;
+    return v;
+}
+
+constexpr int kMaxLevel = 21;           // 21 bits per axis, 63-bit keys
+constexpr uint32_t kQMax = (1u << 21) - 1u;
+constexpr uint32_t kLeafTag = 0x80000000u;  // list entry: opened leaf (EPJ)
+constexpr int kMaxLeaf = 16;
+constexpr int kMaxGrp = 4096;
+
+// overflow bits of DevState::overflow
+constexpr uint32_t kOvfNodes = 1u;
+constexpr uint32_t kOvfPool = 2u;
+constexpr uint32_t kOvfFrontier = 4u;
+constexpr uint32_t kOvfGroups = 8u;
+constexpr uint32_t kBadInput = 16u;
+constexpr uint32_t kOvfChunk = 32u;
+
+// Per-tree device-resident state written by the kernels of one force call.
+struct DevState {
+    double lo[3];        // root box minimum
+    double L;            // largest extent (1 if 0)
+    double s;            // 2^21 / L
+    double c0[3];        // root centre lo + L/2: origin of the FP32 hi/lo copies
+    int32_t lvl_start[kMaxLevel + 3];  // node id range of each level
+    int32_t n_nodes;
+    int32_t n_groups;
+    uint32_t overflow;
+    uint32_t walk_counter;   // dynamic group scheduler of the walk
+    uint32_t force_counter;  // dynamic group scheduler of the force kernel
+    uint32_t pad0;
+    unsigned long long pool_cursor;  // list pool allocation cursor (entries)
+    unsigned long long pool_needed;  // what the walk asked for, incl. overflow
+    unsigned long long list_entries;
+    unsigned long long n_epj;
+    unsigned long long n_spj;
+    unsigned long long int_epj;
+    unsigned long long int_spj;
+    unsigned long long fallbacks;
+    uint32_t max_frontier;
+    int32_t max_level;
+};
+
+// Root-box reduction partials (one per block).
+struct BoxPartial {
+    double lo[3];
+    double hi[3];
+};
+
+}  // namespace fdps
+
+struct fdps_ctx {
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    bool profiling = false;
+    std::string last_error;
+};
+
+struct fdps_psys {
+    fdps_ctx* ctx = nullptr;
+    int64_t n = 0;
+    // current particle order (double-buffered for reordering)
+    double* x[2] = {nullptr, nullptr};
+    double* y[2] = {nullptr, nullptr};
+    double* z[2] = {nullptr, nullptr};
+    double* vx[2] = {nullptr, nullptr};
+    double* vy[2] = {nullptr, nullptr};
+    double* vz[2] = {nullptr, nullptr};
+    double* m[2] = {nullptr, nullptr};
+    double* eps[2] = {nullptr, nullptr};
+    uint32_t* id[2] = {nullptr, nullptr};
+    int cur = 0;
+    // results of the last force calculation, in the current order
+    double* ax = nullptr;
+    double* ay = nullptr;
+    double* az = nullptr;
+    double* pot = nullptr;
+    bool has_data = false;
+    bool has_forces = false;
+    uint32_t* d_flag = nullptr;  // validation flag
+    double* d_red = nullptr;     // reduction scratch (energy)
+    double* stage = nullptr;     // host-transfer staging (10 n doubles, on first use)
+};
+
+struct fdps_tree {
+    fdps_ctx* ctx = nullptr;
+    fdps_tree_params p{};
+    // per-particle scratch
+    int64_t cap_n = 0;
+    int64_t n = 0;  // particles of the last call
+    uint64_t* keys_in = nullptr;   // keys in the call's starting order
+    uint64_t* keys_a = nullptr;    // sort ping-pong
+    uint64_t* keys_b = nullptr;
+    uint32_t* vals_a = nullptr;
+    uint32_t* vals_b = nullptr;
+    uint32_t* perm = nullptr;      // result of the sort (points into vals_*)
+    uint64_t* keys_sorted = nullptr;
+    uint32_t* sort_hist = nullptr; // [256][tiles]
+    uint32_t* sort_dtot = nullptr; // [256] digit totals
+    int64_t cap_tiles = 0;
+    float4* pf_hi = nullptr;       // (x_hi, y_hi, z_hi, m) relative to c0
+    float4* pf_lo = nullptr;       // (x_lo, y_lo, z_lo, eps^2)
+    uint32_t* head = nullptr;      // per particle: group node starting here
+    // nodes
+    int64_t cap_nodes = 0;
+    uint32_t* nd_first = nullptr;
+    uint32_t* nd_count = nullptr;
+    uint32_t* nd_child = nullptr;   // first child id (0xFFFFFFFF for a leaf)
+    uint32_t* nd_meta = nullptr;    // level | nchild << 8 | leaf << 16
+    uint32_t* nd_parent = nullptr;
+    uint64_t* nd_qlo = nullptr;     // packed grid origin x<<42 | y<<21 | z
+    uint64_t* nd_prefix = nullptr;  // key prefix (debug / tests)
+    double* nd_sx = nullptr;        // FP64 sums of m x (bottom-up)
+    double* nd_sy = nullptr;
+    double* nd_sz = nullptr;
+    fdps::dvec4* nd_com = nullptr;      // FP64 (com_x, com_y, com_z, M)
+    double* nd_quad = nullptr;      // FP64 [n][6]
+    float4* nd_fh = nullptr;        // FP32 (com_hi - c0, M)
+    float4* nd_fl = nullptr;        // FP32 (com_lo, 0)
+    float4* nd_fq0 = nullptr;       // FP32 (Qxx, Qyy, Qzz, Qxy)
+    float2* nd_fq1 = nullptr;       // FP32 (Qxz, Qyz)
+    uint32_t* lvl_scratch = nullptr;  // child-count slots of one level
+    uint32_t* lvl_scan = nullptr;     // per-block partial sums
+    // groups
+    int64_t cap_groups = 0;
+    uint32_t* g_first = nullptr;
+    uint32_t* g_count = nullptr;
+    uint32_t* g_node = nullptr;
+    double* g_box = nullptr;        // FP64 [g][6] lo, hi
+    uint32_t* g_qbox = nullptr;     // [g][6] qmin, qmax
+    float4* g_ch = nullptr;         // FP32 (centre_hi - c0, 0)
+    float4* g_cl = nullptr;         // FP32 (centre_lo, 0)
+    float4* g_blo = nullptr;        // FP32 box minimum relative to centre
+    float4* g_bhi = nullptr;        // FP32 box maximum relative to centre
+    fdps::dvec4* g_c64 = nullptr;       // FP64 centre
+    unsigned long long* g_off = nullptr;  // list offset in the pool
+    uint32_t* g_len = nullptr;      // list length (entries)
+    uint32_t* g_nspj = nullptr;     // SPJ entries
+    uint32_t* g_nepj = nullptr;     // EPJ particles
+    uint32_t* grp_scan = nullptr;   // compaction partials
+    // lists
+    int64_t cap_pool = 0;           // entries
+    uint32_t* pool = nullptr;
+    int64_t n_walk_warps = 0;
+    int64_t cap_frontier = 0;       // entries per buffer per warp
+    uint32_t* frontier = nullptr;
+    // state
+    fdps::DevState* st = nullptr;   // device
+    fdps::DevState h_st{};          // host copy after a call
+    fdps::BoxPartial* box_part = nullptr;
+    int box_blocks = 0;
+    int64_t retries = 0;
+    bool valid = false;
+    // profiling
+    cudaEvent_t ev[12] = {};
+    bool ev_ok = false;
+    float ms[10] = {};
+};
+
+namespace fdps {
+
+// ---------------------------------------------------------------- errors
+
+inline int set_error(fdps_ctx* ctx, int code, const char* fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        ctx->last_error = buf;
+    }
+    return code;
+}
+
+#define FDPS_CUDA_TRY(ctx, call)                                                  \
+    do {                                                                          \
+        cudaError_t e_ = (call);                                                  \
+        if (e_ != cudaSuccess) {                                                  \
+            return ::fdps::set_error((ctx), FDPS_ECUDA, "%s:%d %s: %s", __FILE__,  \
+                                     __LINE__, #call, cudaGetErrorString(e_));    \
+        }                                                                         \
+    } while (0)
+
+#define FDPS_LAUNCH_CHECK(ctx) FDPS_CUDA_TRY(ctx, cudaGetLastError())
+
+template <class T>
+inline cudaError_t dev_alloc(T** p, int64_t count) {
+    *p = nullptr;
+    if (count <= 0) count = 1;
+    return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (size_t)count);
+}
+
+template <class T>
+inline void dev_free(T*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+inline int grid_for(int64_t n, int block, int max_blocks) {
+    int64_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > max_blocks) g = max_blocks;
+    return (int)g;
+}
+
+// --------------------------------------------------------- stage entry points
+// (host functions, one per .cu file; all issue work on ctx->stream)
+
+int keys_and_sort(fdps_tree* t, fdps_psys* ps);        // keys_sort.cu
+int reorder_particles(fdps_tree* t, fdps_psys* ps);    // keys_sort.cu
+int build_tree(fdps_tree* t, fdps_psys* ps);           // build.cu
+int compute_moments(fdps_tree* t, fdps_psys* ps);      // build.cu
+int select_groups(fdps_tree* t, fdps_psys* ps);        // build.cu
+int compute_forces(fdps_tree* t, fdps_psys* ps, int spj_kind);  // force.cu
+int launch_kick(fdps_psys* ps, double dt_half);        // integrate.cu
+int launch_drift(fdps_psys* ps, double dt);            // integrate.cu
+int launch_energy(fdps_psys* ps, double* kin, double* pot);  // integrate.cu
+int launch_validate(fdps_psys* ps, uint32_t* bad);     // integrate.cu
+int launch_scatter_in(fdps_psys* ps, const double* pos, const double* vel,
+                      const double* mass, const double* eps);  // integrate.cu
+int launch_gather_out(const fdps_psys* ps, double* pos, double* vel,
+                      double* acc, double* pot);       // integrate.cu
+
+}  // namespace fdps

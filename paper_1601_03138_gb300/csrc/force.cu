@@ -1,0 +1,463 @@
+// force.cu -- particle-particle (EPJ) and particle-superparticle (SPJ)
+// forces from the interaction lists, one warp per i-group.
+//
+// Per i-particle (Sect. 2.2, Eqs. ParticleParticleNbody and
+// ParticleSuperparticleNbody, G = 1, softening eps_i of the receiving
+// particle):
+//   a_i   = sum_EPJ m_j (x_j - x_i) / (r^2 + eps_i^2)^{3/2} + sum_SPJ f'
+//   phi_i = -sum_EPJ m_j / (r^2 + eps_i^2)^{1/2} - ... + m_i / eps_i
+// the last term removing the i-particle's own entry (its force term is zero).
+// A quadrupole superparticle (mass M, traceless Q, r = x_i - com,
+// R^2 = r^2 + eps_i^2) contributes phi = -M/R - (r.Q.r) / (2 R^5) and
+// a = -M r / R^3 + Q r / R^5 - (5/2) (r.Q.r) r / R^7.
+//
+// FP32-relative kernel: list entries are gathered into a per-warp shared
+// tile as FP32 coordinates relative to the group centre, formed from FP32
+// hi/lo pairs so that near pairs keep full FP32 precision; the pair loop is
+// FFMA + MUFU rsqrt; each lane accumulates one tile in plain FP32 and adds
+// the tile's sum to its running total with Kahan compensation.  Small groups
+// split their list over several lanes per i-particle ("slices"), reduced in
+// FP64 at the end.  The FP64 kernel is the same walk of the list on FP64
+// absolute coordinates with FP64 sums.
+#include "fdps_internal.cuh"
+
+namespace fdps {
+
+struct ForceArgs {
+    DevState* st;
+    const uint32_t* g_first;
+    const uint32_t* g_count;
+    const unsigned long long* g_off;
+    const uint32_t* g_len;
+    const float4* g_ch;
+    const float4* g_cl;
+    const uint32_t* pool;
+    const uint32_t* nd_first;
+    const uint32_t* nd_count;
+    const float4* nd_fh;
+    const float4* nd_fl;
+    const float4* nd_fq0;
+    const float2* nd_fq1;
+    const dvec4* nd_com;
+    const double* nd_quad;
+    const float4* pf_hi;
+    const float4* pf_lo;
+    const double* px;
+    const double* py;
+    const double* pz;
+    const double* pm;
+    const double* peps;
+    double* ax;
+    double* ay;
+    double* az;
+    double* pot;
+};
+
+namespace {
+
+constexpr int kFBlock = 128;
+constexpr int kFWarps = kFBlock / 32;
+constexpr int kJCap = 256;    // EPJ particles per FP32 tile
+constexpr int kJCap64 = 128;  // EPJ particles per FP64 tile
+
+struct Kahan4 {
+    float s[4];
+    float c[4];
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) s[k] = c[k] = 0.0f;
+    }
+    __device__ __forceinline__ void add(int k, float v) {
+        const float y = v - c[k];
+        const float t = s[k] + y;
+        c[k] = (t - s[k]) - y;
+        s[k] = t;
+    }
+    __device__ __forceinline__ double value(int k) const { return (double)s[k] - (double)c[k]; }
+};
+
+// Lane -> (i offset, slice) split of a group of n_i particles.
+struct Split {
+    int P, nsl;
+    __device__ __forceinline__ Split(uint32_t ni) {
+        if (ni <= 16u) {
+            P = (int)ni;
+            nsl = 32 / P;
+        } else {
+            P = 32;
+            nsl = 1;
+        }
+    }
+};
+
+// Find the entry owning expanded item `item`: largest e with scan[e] <= item.
+__device__ __forceinline__ int owner(const uint32_t* scan, uint32_t item) {
+    int lo = 0, hi = 32;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (scan[mid] <= item)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+template <bool QUAD>
+__global__ void __launch_bounds__(kFBlock) k_force_f32(ForceArgs A) {
+    __shared__ float4 s_j[kFWarps][kJCap];
+    __shared__ float4 s_s0[kFWarps][32];
+    __shared__ float4 s_s1[kFWarps][32];
+    __shared__ float2 s_s2[kFWarps][32];
+    __shared__ uint32_t s_ef[kFWarps][32];
+    __shared__ uint32_t s_es[kFWarps][33];
+    __shared__ double s_red[kFWarps][4][32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    DevState* st = A.st;
+    const uint32_t ngroups = (uint32_t)st->n_groups;
+    for (;;) {
+        uint32_t g = 0;
+        if (lane == 0) g = atomicAdd(&st->force_counter, 1u);
+        g = __shfl_sync(0xFFFFFFFFu, g, 0);
+        if (g >= ngroups) break;
+        const uint32_t ni = A.g_count[g], gf = A.g_first[g];
+        const unsigned long long off = A.g_off[g];
+        const uint32_t len = A.g_len[g];
+        const float4 gch = A.g_ch[g], gcl = A.g_cl[g];
+        const Split sp(ni);
+        const int ioff = lane % sp.P;
+        const int sl = lane / sp.P;
+        const bool lane_on = sl < sp.nsl;
+        for (uint32_t ib = 0; ib < ni; ib += (uint32_t)sp.P) {
+            const uint32_t i = ib + (uint32_t)ioff;
+            const bool iv = lane_on && i < ni;
+            float xi = 0.f, yi = 0.f, zi = 0.f, e2 = 1.f;
+            if (iv) {
+                const float4 h = A.pf_hi[gf + i], l = A.pf_lo[gf + i];
+                xi = (h.x - gch.x) + (l.x - gcl.x);
+                yi = (h.y - gch.y) + (l.y - gcl.y);
+                zi = (h.z - gch.z) + (l.z - gcl.z);
+                e2 = l.w;
+            }
+            const int kbeg = iv ? sl : 0x7FFFFFFF;
+            Kahan4 acc;
+            acc.init();
+            for (uint32_t t = 0; t < len; t += 32) {
+                const bool ve = t + lane < len;
+                const uint32_t e = ve ? A.pool[off + t + lane] : 0u;
+                const bool isleaf = ve && (e & kLeafTag);
+                const bool isspj = ve && !(e & kLeafTag);
+                const uint32_t node = e & ~kLeafTag;
+                const uint32_t smask = __ballot_sync(0xFFFFFFFFu, isspj);
+                const int ns = __popc(smask);
+                if (isspj) {
+                    const int r = __popc(smask & lt);
+                    const float4 fh = A.nd_fh[node], fl = A.nd_fl[node];
+                    s_s0[w][r] = make_float4((fh.x - gch.x) + (fl.x - gcl.x),
+                                             (fh.y - gch.y) + (fl.y - gcl.y),
+                                             (fh.z - gch.z) + (fl.z - gcl.z), fh.w);
+                    if (QUAD) {
+                        s_s1[w][r] = A.nd_fq0[node];
+                        s_s2[w][r] = A.nd_fq1[node];
+                    }
+                }
+                uint32_t cnt = 0, first = 0;
+                if (isleaf) {
+                    cnt = A.nd_count[node];
+                    first = A.nd_first[node];
+                }
+                uint32_t inc = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+                    if (lane >= o) inc += v;
+                }
+                const uint32_t total = __shfl_sync(0xFFFFFFFFu, inc, 31);
+                s_ef[w][lane] = first;
+                s_es[w][lane] = inc - cnt;
+                __syncwarp();
+                // ---- superparticles of this tile
+                if (ns > 0) {
+                    float pax = 0.f, pay = 0.f, paz = 0.f, pp = 0.f;
+                    for (int k = kbeg; k < ns; k += sp.nsl) {
+                        const float4 a = s_s0[w][k];
+                        const float rx = xi - a.x, ry = yi - a.y, rz = zi - a.z;
+                        const float R2 = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, e2)));
+                        const float Ri = rsqrtf(R2);
+                        const float Ri2 = Ri * Ri;
+                        const float MRi = a.w * Ri;
+                        const float MRi3 = MRi * Ri2;
+                        if (QUAD) {
+                            const float4 q0 = s_s1[w][k];
+                            const float2 q1 = s_s2[w][k];
+                            const float Qrx = fmaf(q0.x, rx, fmaf(q0.w, ry, q1.x * rz));
+                            const float Qry = fmaf(q0.w, rx, fmaf(q0.y, ry, q1.y * rz));
+                            const float Qrz = fmaf(q1.x, rx, fmaf(q1.y, ry, q0.z * rz));
+                            const float rQr = fmaf(rx, Qrx, fmaf(ry, Qry, rz * Qrz));
+                            const float Ri5 = Ri2 * Ri2 * Ri;
+                            const float c = fmaf(2.5f * rQr, Ri5 * Ri2, MRi3);
+                            pax = fmaf(Qrx, Ri5, fmaf(-c, rx, pax));
+                            pay = fmaf(Qry, Ri5, fmaf(-c, ry, pay));
+                            paz = fmaf(Qrz, Ri5, fmaf(-c, rz, paz));
+                            pp -= fmaf(0.5f * rQr, Ri5, MRi);
+                        } else {
+                            pax = fmaf(-MRi3, rx, pax);
+                            pay = fmaf(-MRi3, ry, pay);
+                            paz = fmaf(-MRi3, rz, paz);
+                            pp -= MRi;
+                        }
+                    }
+                    acc.add(0, pax);
+                    acc.add(1, pay);
+                    acc.add(2, paz);
+                    acc.add(3, pp);
+                }
+                // ---- particles of the opened leaves, in chunks of kJCap
+                for (uint32_t c0 = 0; c0 < total; c0 += kJCap) {
+                    const uint32_t m = total - c0 < (uint32_t)kJCap ? total - c0 : (uint32_t)kJCap;
+                    for (uint32_t k = lane; k < m; k += 32) {
+                        const uint32_t item = c0 + k;
+                        const int src = owner(s_es[w], item);
+                        const uint32_t p = s_ef[w][src] + (item - s_es[w][src]);
+                        const float4 h = A.pf_hi[p], l = A.pf_lo[p];
+                        s_j[w][k] = make_float4((h.x - gch.x) + (l.x - gcl.x),
+                                                (h.y - gch.y) + (l.y - gcl.y),
+                                                (h.z - gch.z) + (l.z - gcl.z), h.w);
+                    }
+                    __syncwarp();
+                    float pax = 0.f, pay = 0.f, paz = 0.f, pp = 0.f;
+                    for (int k = kbeg; k < (int)m; k += sp.nsl) {
+                        const float4 j = s_j[w][k];
+                        const float dx = j.x - xi, dy = j.y - yi, dz = j.z - zi;
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, e2)));
+                        const float ri = rsqrtf(r2);
+                        const float mri = j.w * ri;
+                        const float mri3 = mri * (ri * ri);
+                        pax = fmaf(mri3, dx, pax);
+                        pay = fmaf(mri3, dy, pay);
+                        paz = fmaf(mri3, dz, paz);
+                        pp -= mri;
+                    }
+                    acc.add(0, pax);
+                    acc.add(1, pay);
+                    acc.add(2, paz);
+                    acc.add(3, pp);
+                    __syncwarp();
+                }
+                __syncwarp();
+            }
+            // ---- combine slices in FP64 and write back
+#pragma unroll
+            for (int k = 0; k < 4; ++k) s_red[w][k][lane] = iv ? acc.value(k) : 0.0;
+            __syncwarp();
+            if (iv && sl == 0) {
+                double r[4] = {0.0, 0.0, 0.0, 0.0};
+                for (int s2 = 0; s2 < sp.nsl; ++s2)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) r[k] += s_red[w][k][s2 * sp.P + ioff];
+                const uint32_t p = gf + i;
+                A.ax[p] = r[0];
+                A.ay[p] = r[1];
+                A.az[p] = r[2];
+                A.pot[p] = r[3] + A.pm[p] / A.peps[p];
+            }
+            __syncwarp();
+        }
+    }
+}
+
+template <bool QUAD>
+__global__ void __launch_bounds__(kFBlock) k_force_f64(ForceArgs A) {
+    __shared__ dvec4 s_j[kFWarps][kJCap64];
+    __shared__ uint32_t s_ef[kFWarps][32];
+    __shared__ uint32_t s_es[kFWarps][33];
+    __shared__ double s_red[kFWarps][4][32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    DevState* st = A.st;
+    const uint32_t ngroups = (uint32_t)st->n_groups;
+    for (;;) {
+        uint32_t g = 0;
+        if (lane == 0) g = atomicAdd(&st->force_counter, 1u);
+        g = __shfl_sync(0xFFFFFFFFu, g, 0);
+        if (g >= ngroups) break;
+        const uint32_t ni = A.g_count[g], gf = A.g_first[g];
+        const unsigned long long off = A.g_off[g];
+        const uint32_t len = A.g_len[g];
+        const Split sp(ni);
+        const int ioff = lane % sp.P;
+        const int sl = lane / sp.P;
+        const bool lane_on = sl < sp.nsl;
+        for (uint32_t ib = 0; ib < ni; ib += (uint32_t)sp.P) {
+            const uint32_t i = ib + (uint32_t)ioff;
+            const bool iv = lane_on && i < ni;
+            double xi = 0.0, yi = 0.0, zi = 0.0, e2 = 1.0;
+            if (iv) {
+                xi = A.px[gf + i];
+                yi = A.py[gf + i];
+                zi = A.pz[gf + i];
+                e2 = A.peps[gf + i] * A.peps[gf + i];
+            }
+            const int kbeg = iv ? sl : 0x7FFFFFFF;
+            double ax = 0.0, ay = 0.0, az = 0.0, pp = 0.0;
+            for (uint32_t t = 0; t < len; t += 32) {
+                const bool ve = t + lane < len;
+                const uint32_t e = ve ? A.pool[off + t + lane] : 0u;
+                const bool isleaf = ve && (e & kLeafTag);
+                const uint32_t node = e & ~kLeafTag;
+                uint32_t cnt = 0, first = 0;
+                if (isleaf) {
+                    cnt = A.nd_count[node];
+                    first = A.nd_first[node];
+                }
+                uint32_t inc = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+                    if (lane >= o) inc += v;
+                }
+                const uint32_t total = __shfl_sync(0xFFFFFFFFu, inc, 31);
+                s_ef[w][lane] = first;
+                s_es[w][lane] = inc - cnt;
+                // superparticles: every lane of a slice reads the entry from the pool
+                const uint32_t nent = len - t < 32u ? len - t : 32u;
+                for (int k = kbeg; k < (int)nent; k += sp.nsl) {
+                    const uint32_t ek = A.pool[off + t + k];
+                    if (ek & kLeafTag) continue;
+                    const dvec4 c = A.nd_com[ek];
+                    const double rx = xi - c.x, ry = yi - c.y, rz = zi - c.z;
+                    const double R2 = rx * rx + ry * ry + rz * rz + e2;
+                    const double Ri = rsqrt(R2);
+                    const double Ri2 = Ri * Ri;
+                    const double MRi = c.w * Ri;
+                    const double MRi3 = MRi * Ri2;
+                    ax -= MRi3 * rx;
+                    ay -= MRi3 * ry;
+                    az -= MRi3 * rz;
+                    pp -= MRi;
+                    if (QUAD) {
+                        const double* Q = A.nd_quad + 6 * (int64_t)ek;
+                        const double Qrx = Q[0] * rx + Q[3] * ry + Q[4] * rz;
+                        const double Qry = Q[3] * rx + Q[1] * ry + Q[5] * rz;
+                        const double Qrz = Q[4] * rx + Q[5] * ry + Q[2] * rz;
+                        const double rQr = rx * Qrx + ry * Qry + rz * Qrz;
+                        const double Ri5 = Ri2 * Ri2 * Ri;
+                        const double c7 = 2.5 * rQr * Ri5 * Ri2;
+                        ax += Qrx * Ri5 - c7 * rx;
+                        ay += Qry * Ri5 - c7 * ry;
+                        az += Qrz * Ri5 - c7 * rz;
+                        pp -= 0.5 * rQr * Ri5;
+                    }
+                }
+                __syncwarp();
+                for (uint32_t c0 = 0; c0 < total; c0 += kJCap64) {
+                    const uint32_t m = total - c0 < (uint32_t)kJCap64 ? total - c0 : (uint32_t)kJCap64;
+                    for (uint32_t k = lane; k < m; k += 32) {
+                        const uint32_t item = c0 + k;
+                        const int src = owner(s_es[w], item);
+                        const uint32_t p = s_ef[w][src] + (item - s_es[w][src]);
+                        s_j[w][k] = make_dvec4(A.px[p], A.py[p], A.pz[p], A.pm[p]);
+                    }
+                    __syncwarp();
+                    for (int k = kbeg; k < (int)m; k += sp.nsl) {
+                        const dvec4 j = s_j[w][k];
+                        const double dx = j.x - xi, dy = j.y - yi, dz = j.z - zi;
+                        const double r2 = dx * dx + dy * dy + dz * dz + e2;
+                        const double ri = rsqrt(r2);
+                        const double mri = j.w * ri;
+                        const double mri3 = mri * ri * ri;
+                        ax += mri3 * dx;
+                        ay += mri3 * dy;
+                        az += mri3 * dz;
+                        pp -= mri;
+                    }
+                    __syncwarp();
+                }
+                __syncwarp();
+            }
+            s_red[w][0][lane] = iv ? ax : 0.0;
+            s_red[w][1][lane] = iv ? ay : 0.0;
+            s_red[w][2][lane] = iv ? az : 0.0;
+            s_red[w][3][lane] = iv ? pp : 0.0;
+            __syncwarp();
+            if (iv && sl == 0) {
+                double r[4] = {0.0, 0.0, 0.0, 0.0};
+                for (int s2 = 0; s2 < sp.nsl; ++s2)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) r[k] += s_red[w][k][s2 * sp.P + ioff];
+                const uint32_t p = gf + i;
+                A.ax[p] = r[0];
+                A.ay[p] = r[1];
+                A.az[p] = r[2];
+                A.pot[p] = r[3] + A.pm[p] / A.peps[p];
+            }
+            __syncwarp();
+        }
+    }
+}
+
+}  // namespace
+
+int force_blocks(fdps_ctx* ctx, int precision, int quad) {
+    int per_sm = 0;
+    cudaError_t e;
+    if (precision == FDPS_FP64)
+        e = quad ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_f64<true>, kFBlock, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_f64<false>, kFBlock, 0);
+    else
+        e = quad ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_f32<true>, kFBlock, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_f32<false>, kFBlock, 0);
+    if (e != cudaSuccess || per_sm < 1) per_sm = 4;
+    return per_sm * ctx->sm_count;
+}
+
+int compute_forces(fdps_tree* t, fdps_psys* ps, int spj_kind) {
+    fdps_ctx* ctx = t->ctx;
+    const int c = ps->cur;
+    ForceArgs A;
+    A.st = t->st;
+    A.g_first = t->g_first;
+    A.g_count = t->g_count;
+    A.g_off = t->g_off;
+    A.g_len = t->g_len;
+    A.g_ch = t->g_ch;
+    A.g_cl = t->g_cl;
+    A.pool = t->pool;
+    A.nd_first = t->nd_first;
+    A.nd_count = t->nd_count;
+    A.nd_fh = t->nd_fh;
+    A.nd_fl = t->nd_fl;
+    A.nd_fq0 = t->nd_fq0;
+    A.nd_fq1 = t->nd_fq1;
+    A.nd_com = t->nd_com;
+    A.nd_quad = t->nd_quad;
+    A.pf_hi = t->pf_hi;
+    A.pf_lo = t->pf_lo;
+    A.px = ps->x[c];
+    A.py = ps->y[c];
+    A.pz = ps->z[c];
+    A.pm = ps->m[c];
+    A.peps = ps->eps[c];
+    A.ax = ps->ax;
+    A.ay = ps->ay;
+    A.az = ps->az;
+    A.pot = ps->pot;
+    const bool quad = spj_kind == FDPS_GRAV_SPJ_QUAD;
+    const int blocks = force_blocks(ctx, t->p.precision, quad);
+    cudaStream_t s = ctx->stream;
+    if (t->p.precision == FDPS_FP64) {
+        if (quad)
+            k_force_f64<true><<<blocks, kFBlock, 0, s>>>(A);
+        else
+            k_force_f64<false><<<blocks, kFBlock, 0, s>>>(A);
+    } else {
+        if (quad)
+            k_force_f32<true><<<blocks, kFBlock, 0, s>>>(A);
+        else
+            k_force_f32<false><<<blocks, kFBlock, 0, s>>>(A);
+    }
+    FDPS_LAUNCH_CHECK(ctx);
+    return FDPS_OK;
+}
+
+}  // namespace fdps

@@ -1,0 +1,401 @@
+// keys_sort.cu -- root box, Morton keys, LSD radix sort and reorder.
+//
+// Tree construction of Sect. 3.2 starts from the particles' positions; the
+// paper does not fix the key scheme.  This file implements the reading:
+//   box   lo_a = min x_a, L = max_a (max x_a - lo_a) (1 if 0), s = 2^21 / L
+//   key   q_a = min(2^21 - 1, floor((x_a - lo_a) * s)) with the subtraction
+//         and the product each rounded to nearest in FP64 (no FMA), then
+//         bits of q_x / q_y / q_z interleaved to key bits 3b+2 / 3b+1 / 3b
+//   sort  stable by key: 8 LSD passes of 8-bit digits, each pass
+//         reduce-then-scan (tile histograms, a scan, a stable scatter).
+// The first pass's tile histograms are produced by the key kernel itself.
+#include "fdps_internal.cuh"
+
+namespace fdps {
+namespace {
+
+constexpr int kSortBlock = 256;
+constexpr int kSortWarps = kSortBlock / 32;
+constexpr int kSortKPT = 8;
+constexpr int kSortTile = kSortBlock * kSortKPT;  // 2048 keys
+constexpr int kRadix = 256;
+
+// Order-preserving map of an FP64 value to an unsigned integer, so the
+// box reduction runs on the integer pipes.  Min and max of the mapped
+// values are the FP64 min and max (inputs are finite).
+__device__ __forceinline__ unsigned long long ord64(double v) {
+    unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double unord64(unsigned long long o) {
+    unsigned long long u = (o >> 63) ? (o & 0x7FFFFFFFFFFFFFFFull) : ~o;
+    return __longlong_as_double((long long)u);
+}
+
+__global__ void __launch_bounds__(256) k_box_partial(int64_t n, const double* __restrict__ x,
+                                                     const double* __restrict__ y,
+                                                     const double* __restrict__ z,
+                                                     BoxPartial* __restrict__ part) {
+    unsigned long long lo[3] = {~0ull, ~0ull, ~0ull};
+    unsigned long long hi[3] = {0ull, 0ull, 0ull};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long v[3] = {ord64(x[i]), ord64(y[i]), ord64(z[i])};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = v[a] < lo[a] ? v[a] : lo[a];
+            hi[a] = v[a] > hi[a] ? v[a] : hi[a];
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            unsigned long long l = __shfl_xor_sync(0xFFFFFFFFu, lo[a], off);
+            unsigned long long h = __shfl_xor_sync(0xFFFFFFFFu, hi[a], off);
+            lo[a] = l < lo[a] ? l : lo[a];
+            hi[a] = h > hi[a] ? h : hi[a];
+        }
+    }
+    __shared__ unsigned long long s_lo[8][3], s_hi[8][3];
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+        for (int a = 0; a < 3; ++a) {
+            s_lo[w][a] = lo[a];
+            s_hi[w][a] = hi[a];
+        }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        int a = threadIdx.x;
+        unsigned long long l = s_lo[0][a], h = s_hi[0][a];
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+            l = s_lo[k][a] < l ? s_lo[k][a] : l;
+            h = s_hi[k][a] > h ? s_hi[k][a] : h;
+        }
+        // blocks that saw no particle keep the neutral sentinels
+        part[blockIdx.x].lo[a] = __longlong_as_double((long long)l);
+        part[blockIdx.x].hi[a] = __longlong_as_double((long long)h);
+    }
+}
+
+__global__ void k_box_final(int nparts, const BoxPartial* __restrict__ part, DevState* st) {
+    if (threadIdx.x != 0) return;
+    unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
+    for (int b = 0; b < nparts; ++b)
+        for (int a = 0; a < 3; ++a) {
+            unsigned long long l = (unsigned long long)__double_as_longlong(part[b].lo[a]);
+            unsigned long long h = (unsigned long long)__double_as_longlong(part[b].hi[a]);
+            lo[a] = l < lo[a] ? l : lo[a];
+            hi[a] = h > hi[a] ? h : hi[a];
+        }
+    double L = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double l = unord64(lo[a]), h = unord64(hi[a]);
+        st->lo[a] = l;
+        double e = __dsub_rn(h, l);
+        L = e > L ? e : L;
+    }
+    if (L == 0.0) L = 1.0;
+    st->L = L;
+    st->s = __ddiv_rn(2097152.0, L);
+    for (int a = 0; a < 3; ++a) st->c0[a] = __dadd_rn(st->lo[a], __dmul_rn(0.5, L));
+}
+
+__device__ __forceinline__ uint32_t quantise(double x, double lo, double s) {
+    double t = __dsub_rn(x, lo);
+    double u = __dmul_rn(t, s);
+    double f = floor(u);
+    f = f > (double)kQMax ? (double)kQMax : f;
+    f = f < 0.0 ? 0.0 : f;
+    return (uint32_t)f;
+}
+
+// Spread the low 21 bits of v to every third bit (bit b -> bit 3b).
+__device__ __forceinline__ uint64_t spread3(uint32_t v) {
+    uint64_t x = v & 0x1FFFFFu;
+    x = (x | (x << 32)) & 0x001F00000000FFFFull;
+    x = (x | (x << 16)) & 0x001F0000FF0000FFull;
+    x = (x | (x << 8)) & 0x100F00F00F00F00Full;
+    x = (x | (x << 4)) & 0x10C30C30C30C30C3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+// Keys of one 2048-key tile per block, plus that tile's histogram of the
+// lowest digit (the first sort pass).
+__global__ void __launch_bounds__(kSortBlock) k_keys(int64_t n, const double* __restrict__ x,
+                                                     const double* __restrict__ y,
+                                                     const double* __restrict__ z,
+                                                     const DevState* __restrict__ st,
+                                                     uint64_t* __restrict__ keys,
+                                                     uint32_t* __restrict__ hist, int ntiles) {
+    __shared__ uint32_t h[kSortWarps][kRadix];
+    for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortBlock) (&h[0][0])[i] = 0;
+    __syncthreads();
+    const double lo0 = st->lo[0], lo1 = st->lo[1], lo2 = st->lo[2], s = st->s;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t base = (int64_t)blockIdx.x * kSortTile + w * (32 * kSortKPT);
+#pragma unroll
+    for (int r = 0; r < kSortKPT; ++r) {
+        int64_t i = base + r * 32 + lane;
+        if (i < n) {
+            uint32_t qx = quantise(x[i], lo0, s), qy = quantise(y[i], lo1, s),
+                     qz = quantise(z[i], lo2, s);
+            uint64_t k = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+            keys[i] = k;
+            atomicAdd(&h[w][k & 0xFF], 1u);
+        }
+    }
+    __syncthreads();
+    uint32_t c = 0;
+#pragma unroll
+    for (int k = 0; k < kSortWarps; ++k) c += h[k][threadIdx.x];
+    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = c;
+}
+
+__global__ void __launch_bounds__(kSortBlock) k_radix_hist(int64_t n, const uint64_t* __restrict__ keys,
+                                                           int shift, uint32_t* __restrict__ hist,
+                                                           int ntiles) {
+    __shared__ uint32_t h[kSortWarps][kRadix];
+    for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortBlock) (&h[0][0])[i] = 0;
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t base = (int64_t)blockIdx.x * kSortTile + w * (32 * kSortKPT);
+#pragma unroll
+    for (int r = 0; r < kSortKPT; ++r) {
+        int64_t i = base + r * 32 + lane;
+        if (i < n) atomicAdd(&h[w][(keys[i] >> shift) & 0xFF], 1u);
+    }
+    __syncthreads();
+    uint32_t c = 0;
+#pragma unroll
+    for (int k = 0; k < kSortWarps; ++k) c += h[k][threadIdx.x];
+    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = c;
+}
+
+// Exclusive block scan of one value per thread (blockDim.x <= 1024).
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total) {
+    __shared__ uint32_t s_w[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        uint32_t t = __shfl_up_sync(0xFFFFFFFFu, inc, off);
+        if (lane >= off) inc += t;
+    }
+    if (lane == 31) s_w[w] = inc;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    if (w == 0) {
+        uint32_t t = lane < nw ? s_w[lane] : 0u;
+        uint32_t ti = t;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            uint32_t u = __shfl_up_sync(0xFFFFFFFFu, ti, off);
+            if (lane >= off) ti += u;
+        }
+        if (lane < nw) s_w[lane] = ti - t;
+        if (lane == nw - 1) s_w[31] = ti;
+    }
+    __syncthreads();
+    uint32_t res = s_w[w] + inc - v;
+    if (total) *total = s_w[31];
+    __syncthreads();
+    return res;
+}
+
+// One block per digit: exclusive scan of that digit's row of tile counts.
+__global__ void __launch_bounds__(1024) k_radix_scan_rows(uint32_t* __restrict__ hist, int ntiles,
+                                                          uint32_t* __restrict__ dtot) {
+    uint32_t* row = hist + (int64_t)blockIdx.x * ntiles;
+    const int per = (ntiles + blockDim.x - 1) / blockDim.x;
+    const int b = threadIdx.x * per;
+    uint32_t sum = 0;
+    for (int k = 0; k < per; ++k)
+        if (b + k < ntiles) sum += row[b + k];
+    uint32_t total;
+    uint32_t off = block_excl_scan(sum, &total);
+    for (int k = 0; k < per; ++k)
+        if (b + k < ntiles) {
+            uint32_t c = row[b + k];
+            row[b + k] = off;
+            off += c;
+        }
+    if (threadIdx.x == 0) dtot[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kRadix) k_radix_scan_digits(uint32_t* __restrict__ dtot) {
+    uint32_t v = dtot[threadIdx.x];
+    uint32_t off = block_excl_scan(v, nullptr);
+    dtot[threadIdx.x] = off;
+}
+
+// Stable scatter of one tile: warp-level ranking with match_any, tile-local
+// reordering in shared memory, then coalesced runs per digit.
+__global__ void __launch_bounds__(kSortBlock) k_radix_scatter(
+    int64_t n, const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+    uint64_t* __restrict__ kout, uint32_t* __restrict__ vout, int shift,
+    const uint32_t* __restrict__ hist, const uint32_t* __restrict__ dbase, int ntiles) {
+    __shared__ uint64_t sk[kSortTile];
+    __shared__ uint32_t sv[kSortTile];
+    __shared__ uint32_t wcnt[kSortWarps][kRadix];
+    __shared__ uint32_t tstart[kRadix];
+    __shared__ uint32_t gbase[kRadix];
+    for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortBlock) (&wcnt[0][0])[i] = 0;
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const int64_t tile0 = (int64_t)blockIdx.x * kSortTile;
+    const int64_t base = tile0 + w * (32 * kSortKPT);
+    uint64_t mk[kSortKPT];
+    uint32_t mv[kSortKPT], mr[kSortKPT];
+#pragma unroll
+    for (int r = 0; r < kSortKPT; ++r) {
+        int64_t i = base + r * 32 + lane;
+        bool valid = i < n;
+        uint64_t k = valid ? kin[i] : 0ull;
+        uint32_t v = valid ? (vin ? vin[i] : (uint32_t)i) : 0u;
+        uint32_t d = (uint32_t)(k >> shift) & 0xFFu;
+        uint32_t vmask = __ballot_sync(0xFFFFFFFFu, valid);
+        uint32_t rank = 0, before = 0, peers = 0;
+        if (valid) {
+            peers = __match_any_sync(vmask, d);
+            rank = __popc(peers & lt_mask);
+            before = wcnt[w][d];
+        }
+        __syncwarp();
+        if (valid && rank == 0) wcnt[w][d] = before + __popc(peers);
+        __syncwarp();
+        mk[r] = k;
+        mv[r] = v;
+        mr[r] = before + rank;
+    }
+    __syncthreads();
+    {
+        const int d = threadIdx.x;  // one thread per digit
+        uint32_t run = 0;
+#pragma unroll
+        for (int k = 0; k < kSortWarps; ++k) {
+            uint32_t c = wcnt[k][d];
+            wcnt[k][d] = run;
+            run += c;
+        }
+        uint32_t st0 = block_excl_scan(run, nullptr);
+        tstart[d] = st0;
+        gbase[d] = dbase[d] + hist[(int64_t)d * ntiles + blockIdx.x];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortKPT; ++r) {
+        int64_t i = base + r * 32 + lane;
+        if (i < n) {
+            uint32_t d = (uint32_t)(mk[r] >> shift) & 0xFFu;
+            uint32_t p = tstart[d] + wcnt[w][d] + mr[r];
+            sk[p] = mk[r];
+            sv[p] = mv[r];
+        }
+    }
+    __syncthreads();
+    int64_t rem = n - tile0;
+    const int cnt = rem < kSortTile ? (int)rem : kSortTile;
+    for (int p = threadIdx.x; p < cnt; p += kSortBlock) {
+        uint64_t k = sk[p];
+        uint32_t d = (uint32_t)(k >> shift) & 0xFFu;
+        uint32_t dst = gbase[d] + (uint32_t)p - tstart[d];
+        kout[dst] = k;
+        vout[dst] = sv[p];
+    }
+}
+
+// Reorder the particle system into key order and write the FP32 hi/lo
+// copies relative to the root centre used by the walk and force kernels.
+__global__ void __launch_bounds__(256) k_reorder(
+    int64_t n, const uint32_t* __restrict__ perm, const DevState* __restrict__ st,
+    const double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ z,
+    const double* __restrict__ vx, const double* __restrict__ vy, const double* __restrict__ vz,
+    const double* __restrict__ m, const double* __restrict__ eps, const uint32_t* __restrict__ id,
+    double* __restrict__ x2, double* __restrict__ y2, double* __restrict__ z2,
+    double* __restrict__ vx2, double* __restrict__ vy2, double* __restrict__ vz2,
+    double* __restrict__ m2, double* __restrict__ eps2, uint32_t* __restrict__ id2,
+    float4* __restrict__ pf_hi, float4* __restrict__ pf_lo) {
+    const double c0 = st->c0[0], c1 = st->c0[1], c2 = st->c0[2];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t s = perm[i];
+        double px = x[s], py = y[s], pz = z[s], pm = m[s], pe = eps[s];
+        x2[i] = px;
+        y2[i] = py;
+        z2[i] = pz;
+        vx2[i] = vx[s];
+        vy2[i] = vy[s];
+        vz2[i] = vz[s];
+        m2[i] = pm;
+        eps2[i] = pe;
+        id2[i] = id[s];
+        double rx = px - c0, ry = py - c1, rz = pz - c2;
+        float hx = __double2float_rn(rx), hy = __double2float_rn(ry), hz = __double2float_rn(rz);
+        float lx = __double2float_rn(rx - (double)hx), ly = __double2float_rn(ry - (double)hy),
+              lz = __double2float_rn(rz - (double)hz);
+        pf_hi[i] = make_float4(hx, hy, hz, __double2float_rn(pm));
+        pf_lo[i] = make_float4(lx, ly, lz, __double2float_rn(pe * pe));
+    }
+}
+
+}  // namespace
+
+int keys_and_sort(fdps_tree* t, fdps_psys* ps) {
+    fdps_ctx* ctx = t->ctx;
+    cudaStream_t s = ctx->stream;
+    const int64_t n = ps->n;
+    const int c = ps->cur;
+    const int ntiles = (int)((n + kSortTile - 1) / kSortTile);
+    k_box_partial<<<t->box_blocks, 256, 0, s>>>(n, ps->x[c], ps->y[c], ps->z[c], t->box_part);
+    FDPS_LAUNCH_CHECK(ctx);
+    k_box_final<<<1, 32, 0, s>>>(t->box_blocks, t->box_part, t->st);
+    FDPS_LAUNCH_CHECK(ctx);
+    k_keys<<<ntiles, kSortBlock, 0, s>>>(n, ps->x[c], ps->y[c], ps->z[c], t->st, t->keys_in,
+                                         t->sort_hist, ntiles);
+    FDPS_LAUNCH_CHECK(ctx);
+    if (t->ev_ok && ctx->profiling) cudaEventRecord(t->ev[1], s);
+    const uint64_t* kin = t->keys_in;
+    const uint32_t* vin = nullptr;
+    uint64_t* kb[2] = {t->keys_a, t->keys_b};
+    uint32_t* vb[2] = {t->vals_a, t->vals_b};
+    for (int pass = 0; pass < 8; ++pass) {
+        const int shift = 8 * pass;
+        if (pass > 0) {
+            k_radix_hist<<<ntiles, kSortBlock, 0, s>>>(n, kin, shift, t->sort_hist, ntiles);
+            FDPS_LAUNCH_CHECK(ctx);
+        }
+        k_radix_scan_rows<<<kRadix, 1024, 0, s>>>(t->sort_hist, ntiles, t->sort_dtot);
+        FDPS_LAUNCH_CHECK(ctx);
+        k_radix_scan_digits<<<1, kRadix, 0, s>>>(t->sort_dtot);
+        FDPS_LAUNCH_CHECK(ctx);
+        uint64_t* ko = kb[pass & 1];
+        uint32_t* vo = vb[pass & 1];
+        k_radix_scatter<<<ntiles, kSortBlock, 0, s>>>(n, kin, vin, ko, vo, shift, t->sort_hist,
+                                                      t->sort_dtot, ntiles);
+        FDPS_LAUNCH_CHECK(ctx);
+        kin = ko;
+        vin = vo;
+    }
+    t->keys_sorted = kb[1];
+    t->perm = vb[1];
+    return FDPS_OK;
+}
+
+int reorder_particles(fdps_tree* t, fdps_psys* ps) {
+    fdps_ctx* ctx = t->ctx;
+    const int c = ps->cur, o = 1 - ps->cur;
+    const int64_t n = ps->n;
+    int grid = grid_for(n, 256, ctx->sm_count * 16);
+    k_reorder<<<grid, 256, 0, ctx->stream>>>(
+        n, t->perm, t->st, ps->x[c], ps->y[c], ps->z[c], ps->vx[c], ps->vy[c], ps->vz[c],
+        ps->m[c], ps->eps[c], ps->id[c], ps->x[o], ps->y[o], ps->z[o], ps->vx[o], ps->vy[o],
+        ps->vz[o], ps->m[o], ps->eps[o], ps->id[o], t->pf_hi, t->pf_lo);
+    FDPS_LAUNCH_CHECK(ctx);
+    ps->cur = o;
+    return FDPS_OK;
+}
+
+}  // namespace fdps

@@ -1,0 +1,317 @@
+// walk.cu -- interaction lists: one warp walks the tree for one i-group.
+//
+// The "usual tree traversal" with a fixed opening angle (Sect. 3.2), done
+// once per i-group as in the modified tree algorithm of Barnes (1990) that
+// the paper's cost model uses (Sect. 5.5, T_icalc,const).  The paper does
+// not state the criterion; this library opens a cell C for group G iff
+//   (a) C's grid cube meets G's grid box (closed integer intervals of the
+//       quantised coordinates), or
+//   (b) ell_C^2 >= theta^2 d^2, ell_C = L 2^-level, d = distance from C's
+//       centre of mass to G's FP64 bounding box,
+// and evaluates (b) as FP64 with each operation rounded on its own, in a
+// fixed order.  The same FP64 decision is reproduced here at FP32 cost: the
+// test is first evaluated in FP32 on double-float (hi + lo) copies of the
+// positions relative to the group centre, with a rigorous bound on the
+// FP32 error; only tests that land inside that bound are re-evaluated with
+// the exact FP64 operation sequence.
+//
+// Traversal is breadth-first per warp: 32 cells of the current frontier are
+// tested at a time; opened internal cells push their children (contiguous
+// ids) to the next frontier, opened leaves append one EPJ entry (node id
+// with bit 31 set: all of the leaf's particles), unopened cells one SPJ
+// entry.  A group's list is contiguous in a pool handed out in chunks of
+// 2^16 entries; when a chunk fills the group's partial list moves to a
+// fresh chunk.  Overflow of the pool or of the frontier sets a flag; the
+// host then grows the buffer and repeats the walk.
+#include "fdps_internal.cuh"
+
+namespace fdps {
+
+struct WalkArgs {
+    DevState* st;
+    const uint32_t* nd_count;
+    const uint32_t* nd_child;
+    const uint32_t* nd_meta;
+    const uint64_t* nd_qlo;
+    const float4* nd_fh;
+    const float4* nd_fl;
+    const dvec4* nd_com;
+    const uint32_t* g_count;
+    const uint32_t* g_qbox;
+    const double* g_box;
+    const float4* g_ch;
+    const float4* g_cl;
+    const float4* g_blo;
+    const float4* g_bhi;
+    unsigned long long* g_off;
+    uint32_t* g_len;
+    uint32_t* g_nspj;
+    uint32_t* g_nepj;
+    uint32_t* pool;
+    unsigned long long cap_pool;
+    uint32_t* frontier;
+    uint32_t cap_frontier;
+    double theta2;
+    float theta2f;
+};
+
+namespace {
+
+constexpr int kWalkBlock = 128;
+constexpr unsigned long long kChunk = 1ull << 16;
+constexpr float kU32 = 5.9604645e-08f;  // 2^-24, unit roundoff of FP32
+
+__device__ __forceinline__ unsigned long long shfl_u64(unsigned long long v, int src) {
+    return __shfl_sync(0xFFFFFFFFu, v, src);
+}
+
+// Exact FP64 opening test (b): the reference sequence of operations.
+__device__ __noinline__ bool open_fp64(double L, int level, double theta2, const dvec4 com,
+                                       const double* box) {
+    const double ell = ldexp(L, -level);
+    const double c[3] = {com.x, com.y, com.z};
+    double d2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double below = __dsub_rn(box[a], c[a]);
+        const double above = __dsub_rn(c[a], box[3 + a]);
+        const double da = below > 0.0 ? below : (above > 0.0 ? above : 0.0);
+        d2 = __dadd_rn(d2, __dmul_rn(da, da));
+    }
+    return __dmul_rn(ell, ell) >= __dmul_rn(theta2, d2);
+}
+
+__global__ void __launch_bounds__(kWalkBlock) k_walk(WalkArgs A) {
+    __shared__ float s_ell[kMaxLevel + 1];
+    DevState* st = A.st;
+    const double L = st->L;
+    if (threadIdx.x <= kMaxLevel) s_ell[threadIdx.x] = __double2float_rn(ldexp(L, -(int)threadIdx.x));
+    __syncthreads();
+    const float Lf = __double2float_rn(L);
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    uint32_t* fa = A.frontier + wid * 2 * (int64_t)A.cap_frontier;
+    uint32_t* fb = fa + A.cap_frontier;
+    const uint32_t F = A.cap_frontier;
+    const uint32_t ngroups = (uint32_t)st->n_groups;
+
+    unsigned long long cursor = 0, chunk_end = 0;
+    bool ovf = false;
+    unsigned long long acc_entries = 0, acc_epj = 0, acc_spj = 0, acc_iepj = 0, acc_ispj = 0,
+                       acc_fb = 0;
+    uint32_t max_front = 0;
+
+    for (;;) {
+        uint32_t g = 0;
+        if (lane == 0) g = atomicAdd(&st->walk_counter, 1u);
+        g = __shfl_sync(0xFFFFFFFFu, g, 0);
+        if (g >= ngroups) break;
+
+        const uint32_t* qb = A.g_qbox + 6 * (int64_t)g;
+        const uint32_t qmin0 = qb[0], qmin1 = qb[1], qmin2 = qb[2];
+        const uint32_t qmax0 = qb[3], qmax1 = qb[4], qmax2 = qb[5];
+        const float4 gch = A.g_ch[g], gcl = A.g_cl[g];
+        const float4 blo = A.g_blo[g], bhi = A.g_bhi[g];
+        const float hb = fmaxf(fmaxf(fmaxf(-blo.x, -blo.y), fmaxf(-blo.z, bhi.x)), fmaxf(bhi.y, bhi.z));
+        const double* box64 = A.g_box + 6 * (int64_t)g;
+
+        unsigned long long gstart = cursor;
+        uint32_t nspj = 0, nepj = 0;
+        uint32_t fsize = 1;
+        if (lane == 0) fa[0] = 0u;
+        __syncwarp();
+        while (fsize > 0) {
+            uint32_t nsize = 0;
+            max_front = fsize > max_front ? fsize : max_front;
+            for (uint32_t base = 0; base < fsize; base += 32) {
+                const uint32_t idx = base + lane;
+                const bool act = idx < fsize;
+                const uint32_t node = act ? fa[idx] : 0u;
+                int action = 0;  // 1 SPJ, 2 EPJ leaf, 3 open internal
+                uint32_t nch = 0, child = 0, pcount = 0;
+                bool fallback = false;
+                if (act) {
+                    const uint32_t meta = A.nd_meta[node];
+                    const int level = (int)(meta & 0xFFu);
+                    const bool leaf = (meta >> 16) & 1u;
+                    const uint64_t q = A.nd_qlo[node];
+                    const uint32_t w = (1u << (kMaxLevel - level)) - 1u;
+                    const uint32_t qx = (uint32_t)(q >> 42), qy = (uint32_t)(q >> 21) & kQMax,
+                                   qz = (uint32_t)q & kQMax;
+                    const bool meets = qx <= qmax0 && qx + w >= qmin0 && qy <= qmax1 &&
+                                       qy + w >= qmin1 && qz <= qmax2 && qz + w >= qmin2;
+                    bool open = true;
+                    if (!meets) {
+                        const float4 fh = A.nd_fh[node], fl = A.nd_fl[node];
+                        const float dx = (fh.x - gch.x) + (fl.x - gcl.x);
+                        const float dy = (fh.y - gch.y) + (fl.y - gcl.y);
+                        const float dz = (fh.z - gch.z) + (fl.z - gcl.z);
+                        const float tx = fmaxf(fmaxf(blo.x - dx, dx - bhi.x), 0.0f);
+                        const float ty = fmaxf(fmaxf(blo.y - dy, dy - bhi.y), 0.0f);
+                        const float tz = fmaxf(fmaxf(blo.z - dz, dz - bhi.z), 0.0f);
+                        const float d2 = tx * tx + ty * ty + tz * tz;
+                        const float ell = s_ell[level];
+                        const float l2 = ell * ell;
+                        const float r2 = A.theta2f * d2;
+                        const float T = l2 - r2;
+                        // bound on |T - (ell^2 - theta^2 D^2)|, D the exact distance
+                        const float E = 4.0f * kU32 *
+                                            (fmaxf(fmaxf(fabsf(dx), fabsf(dy)), fabsf(dz)) + hb) +
+                                        1e-13f * Lf;
+                        const float S1 = tx + ty + tz;
+                        const float margin =
+                            8.0f * kU32 * (l2 + r2) + A.theta2f * (2.0f * E * S1 + 3.0f * E * E);
+                        if (T > margin) {
+                            open = true;
+                        } else if (T < -margin) {
+                            open = false;
+                        } else {
+                            fallback = true;
+                            open = open_fp64(L, level, A.theta2, A.nd_com[node], box64);
+                        }
+                    }
+                    if (!open) {
+                        action = 1;
+                    } else if (leaf) {
+                        action = 2;
+                        pcount = A.nd_count[node];
+                    } else {
+                        action = 3;
+                        child = A.nd_child[node];
+                        nch = (meta >> 8) & 0xFFu;
+                    }
+                }
+                acc_fb += __popc(__ballot_sync(0xFFFFFFFFu, fallback));
+                // ---- append SPJ / EPJ entries
+                const bool emit = action == 1 || action == 2;
+                const uint32_t emask = __ballot_sync(0xFFFFFFFFu, emit);
+                const uint32_t k = __popc(emask);
+                if (k) {
+                    if (cursor + k > chunk_end) {
+                        const unsigned long long sofar = cursor - gstart;
+                        unsigned long long nb = 0;
+                        if (lane == 0) nb = atomicAdd(&st->pool_cursor, kChunk);
+                        nb = shfl_u64(nb, 0);
+                        if (!ovf && (nb + kChunk > A.cap_pool || sofar + k > kChunk)) {
+                            if (lane == 0)
+                                atomicOr(&st->overflow, nb + kChunk > A.cap_pool ? kOvfPool : kOvfChunk);
+                            ovf = true;
+                        }
+                        if (!ovf) {
+                            for (unsigned long long j = lane; j < sofar; j += 32)
+                                A.pool[nb + j] = A.pool[gstart + j];
+                            __syncwarp();
+                            gstart = nb;
+                            cursor = nb + sofar;
+                            chunk_end = nb + kChunk;
+                        } else {
+                            chunk_end = ~0ull;  // count only from here on
+                        }
+                    }
+                    if (emit && !ovf)
+                        A.pool[cursor + __popc(emask & lt)] = action == 2 ? (node | kLeafTag) : node;
+                    cursor += k;
+                }
+                nspj += __popc(__ballot_sync(0xFFFFFFFFu, action == 1));
+                uint32_t pc = pcount;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) pc += __shfl_xor_sync(0xFFFFFFFFu, pc, off);
+                nepj += pc;
+                // ---- push children of opened internal cells
+                uint32_t inc = nch;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    uint32_t tv = __shfl_up_sync(0xFFFFFFFFu, inc, off);
+                    if (lane >= off) inc += tv;
+                }
+                const uint32_t tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
+                if (nsize + tot > F) {
+                    if (lane == 0) atomicOr(&st->overflow, kOvfFrontier);
+                    ovf = true;
+                } else {
+                    const uint32_t o = nsize + inc - nch;
+                    for (uint32_t c = 0; c < nch; ++c) fb[o + c] = child + c;
+                    nsize += tot;
+                }
+            }
+            __syncwarp();
+            uint32_t* tmp = fa;
+            fa = fb;
+            fb = tmp;
+            fsize = nsize;
+        }
+        const unsigned long long len = cursor - gstart;
+        if (lane == 0) {
+            A.g_off[g] = gstart;
+            A.g_len[g] = (uint32_t)len;
+            A.g_nspj[g] = nspj;
+            A.g_nepj[g] = nepj;
+        }
+        const unsigned long long ni = A.g_count[g];
+        acc_entries += len;
+        acc_epj += nepj;
+        acc_spj += nspj;
+        acc_iepj += ni * nepj;
+        acc_ispj += ni * nspj;
+    }
+    if (lane == 0) {
+        atomicAdd(&st->pool_needed, acc_entries);
+        atomicAdd(&st->list_entries, acc_entries);
+        atomicAdd(&st->n_epj, acc_epj);
+        atomicAdd(&st->n_spj, acc_spj);
+        atomicAdd(&st->int_epj, acc_iepj);
+        atomicAdd(&st->int_spj, acc_ispj);
+        atomicAdd(&st->fallbacks, acc_fb);
+        atomicMax(&st->max_frontier, max_front);
+    }
+}
+
+}  // namespace
+
+int walk_blocks(fdps_ctx* ctx) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk, kWalkBlock, 0) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 4;
+    return per_sm * ctx->sm_count;
+}
+
+int walk_warps_per_block() { return kWalkBlock / 32; }
+
+unsigned long long walk_chunk() { return kChunk; }
+
+int launch_walk(fdps_tree* t, int blocks) {
+    fdps_ctx* ctx = t->ctx;
+    WalkArgs A;
+    A.st = t->st;
+    A.nd_count = t->nd_count;
+    A.nd_child = t->nd_child;
+    A.nd_meta = t->nd_meta;
+    A.nd_qlo = t->nd_qlo;
+    A.nd_fh = t->nd_fh;
+    A.nd_fl = t->nd_fl;
+    A.nd_com = t->nd_com;
+    A.g_count = t->g_count;
+    A.g_qbox = t->g_qbox;
+    A.g_box = t->g_box;
+    A.g_ch = t->g_ch;
+    A.g_cl = t->g_cl;
+    A.g_blo = t->g_blo;
+    A.g_bhi = t->g_bhi;
+    A.g_off = t->g_off;
+    A.g_len = t->g_len;
+    A.g_nspj = t->g_nspj;
+    A.g_nepj = t->g_nepj;
+    A.pool = t->pool;
+    A.cap_pool = (unsigned long long)t->cap_pool;
+    A.frontier = t->frontier;
+    A.cap_frontier = (uint32_t)t->cap_frontier;
+    A.theta2 = t->p.theta * t->p.theta;
+    A.theta2f = (float)A.theta2;
+    k_walk<<<blocks, kWalkBlock, 0, ctx->stream>>>(A);
+    FDPS_LAUNCH_CHECK(ctx);
+    return FDPS_OK;
+}
+
+}  // namespace fdps

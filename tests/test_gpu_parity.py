@@ -1,0 +1,302 @@
+"""CUDA path versus the oracle, through the C ABI.
+
+Bit-exact: root box, Morton keys, sort permutation, node table, i-groups,
+interaction lists (as sets).  Floating point: forces and potentials within
+RMS relative error 1e-5 of the oracle's FP64 evaluation of the identical
+lists (FP32-relative kernel) and 1e-12 (FP64 kernel); tree accuracy against
+the FP64 direct sum at theta = 0.5 within median 2e-3 (monopole) and 5e-4
+(quadrupole).
+"""
+import numpy as np
+import pytest
+
+import ics
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+RMS_FP32 = 1e-5
+RMS_FP64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_1601_03138_gb300 import build as B
+    B.build()
+    import paper_1601_03138_gb300 as G
+    return G
+
+
+@pytest.fixture(scope="module")
+def ctx(G):
+    c = G.Context(0)
+    yield c
+    c.close()
+
+
+def run_gpu(G, ctx, pos, vel, mass, eps, theta, n_leaf, n_grp, quad=False, fp64=False):
+    n = len(pos)
+    ps = G.ParticleSystem(ctx, n)
+    tree = G.Tree(ctx, theta=theta, n_leaf=n_leaf, n_grp=n_grp, quad=quad, fp64=fp64)
+    ps.set(np.ascontiguousarray(pos), np.ascontiguousarray(vel), np.ascontiguousarray(mass),
+           np.ascontiguousarray(eps))
+    tree.calc_force_all_and_write_back(ps)
+    return ps, tree
+
+
+def rms_rel(a, b):
+    if a.ndim == 2:
+        e = np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
+    else:
+        e = np.abs(a - b) / np.abs(b)
+    return float(np.sqrt(np.mean(e ** 2)))
+
+
+def decode_lists(offs, ent, nodes):
+    """[(EPJ particle indices, SPJ node ids)] per group from raw GPU entries."""
+    out = []
+    for k in range(len(offs) - 1):
+        e = ent[offs[k]:offs[k + 1]]
+        leaf = (e & np.uint32(0x80000000)) != 0
+        spj = np.sort(e[~leaf].astype(np.int64))
+        lid = (e[leaf] & np.uint32(0x7FFFFFFF)).astype(np.int64)
+        if len(lid):
+            epj = np.concatenate([np.arange(nodes["first"][c], nodes["first"][c] + nodes["count"][c])
+                                  for c in lid])
+        else:
+            epj = np.zeros(0, np.int64)
+        out.append((np.sort(epj), spj))
+    return out
+
+
+def check_structure(G, tree, ref, n, group_sample=None):
+    keys_g, perm_g = tree.keys(n)
+    keys_r, perm_r = ref.keys()
+    np.testing.assert_array_equal(keys_g, keys_r)
+    np.testing.assert_array_equal(perm_g, perm_r)
+    lo_g, L_g, s_g = tree.box()
+    lo_r, L_r, s_r = ref.box()
+    assert np.all(lo_g == lo_r) and L_g == L_r and s_g == s_r
+    ng, nr = tree.nodes(), ref.nodes()
+    assert len(ng["level"]) == ref.n_nodes
+    for k in ("level", "first", "count", "child_first", "nchild"):
+        np.testing.assert_array_equal(ng[k], nr[k], err_msg=k)
+    np.testing.assert_array_equal(ng["mass"], nr["mass"])
+    np.testing.assert_array_equal(ng["com"], nr["com"])  # bit-exact FP64 COM
+    gg, gr = tree.groups(), ref.groups()
+    for k in ("first", "count", "node"):
+        np.testing.assert_array_equal(gg[k], gr[k], err_msg=k)
+    np.testing.assert_array_equal(gg["box"], gr["box"])
+    groups = range(ref.n_groups) if group_sample is None else group_sample
+    for g in groups:
+        offs, ent = tree.lists(int(g), int(g) + 1)
+        (epj_g, spj_g), = decode_lists(offs, ent, ng)
+        epj_r, spj_r = ref.walk(int(g))
+        np.testing.assert_array_equal(epj_g, np.sort(epj_r), err_msg=f"EPJ of group {g}")
+        np.testing.assert_array_equal(spj_g, np.sort(spj_r), err_msg=f"SPJ of group {g}")
+    return ng, nr
+
+
+CASES = [
+    # name, model, n, theta, n_leaf, n_grp, quad
+    ("plummer16k-mono", "plummer", 16384, 0.5, 8, 64, False),
+    ("plummer-ragged-quad", "plummer", 20001, 0.5, 16, 128, True),
+    ("hernquist-theta0.3", "hernquist", 30000, 0.3, 8, 64, True),
+    ("hernquist-theta0.7-ngrp256", "hernquist", 50001, 0.7, 16, 256, True),
+    ("clumpy-ngrp512", "clumpy", 40000, 0.5, 16, 512, True),
+    ("plummer-nleaf1", "plummer", 3000, 0.6, 1, 4, False),
+]
+
+
+@pytest.mark.parametrize("name,model,n,theta,n_leaf,n_grp,quad", CASES, ids=[c[0] for c in CASES])
+def test_parity_with_oracle(G, ctx, name, model, n, theta, n_leaf, n_grp, quad):
+    pos, vel, mass, eps = ics.make(model, n, ics.SEED_BASE + 11 + n, 0.01)
+    ps, tree = run_gpu(G, ctx, pos, vel, mass, eps, theta, n_leaf, n_grp, quad)
+    try:
+        ref = oracle.Tree(pos, mass, eps, theta=theta, n_leaf=n_leaf, n_grp=n_grp, quad=quad)
+        sample = None if ref.n_groups <= 400 else np.random.default_rng(n).choice(
+            ref.n_groups, 400, replace=False)
+        ng, nr = check_structure(G, tree, ref, n, sample)
+        if quad:
+            np.testing.assert_allclose(ng["quad"], nr["quad"], rtol=1e-9,
+                                       atol=1e-12 * np.abs(nr["quad"]).max())
+        _, _, acc, pot = ps.get()
+        acc_r, pot_r, tot = ref.force()
+        assert rms_rel(acc, acc_r) <= RMS_FP32
+        assert rms_rel(pot, pot_r) <= RMS_FP32
+        st = tree.stats()
+        assert st["interactions_epj"] + st["interactions_spj"] == tot[2]
+        assert st["interactions_spj"] == tot[3]
+    finally:
+        tree.close()
+        ps.close()
+
+
+@pytest.mark.parametrize("quad", [False, True])
+def test_fp64_variant_matches_oracle(G, ctx, quad):
+    n = 12000
+    pos, vel, mass, eps = ics.make("hernquist", n, ics.SEED_BASE + 21, 0.01)
+    ps, tree = run_gpu(G, ctx, pos, vel, mass, eps, 0.5, 8, 64, quad, fp64=True)
+    try:
+        ref = oracle.Tree(pos, mass, eps, theta=0.5, n_leaf=8, n_grp=64, quad=quad)
+        _, _, acc, pot = ps.get()
+        acc_r, pot_r, _ = ref.force()
+        assert rms_rel(acc, acc_r) <= RMS_FP64
+        assert rms_rel(pot, pot_r) <= RMS_FP64
+    finally:
+        tree.close()
+        ps.close()
+
+
+@pytest.mark.parametrize("quad,tol", [(False, 2e-3), (True, 5e-4)])
+def test_accuracy_against_direct_sum(G, ctx, quad, tol):
+    pos, vel, mass, eps = ics.make_config("plummer16k")
+    ps, tree = run_gpu(G, ctx, pos, vel, mass, eps, 0.5, 8, 64, quad)
+    try:
+        _, _, acc, pot = ps.get()
+        ad, pd = oracle.direct(pos, mass, eps)
+        err = np.linalg.norm(acc - ad, axis=1) / np.linalg.norm(ad, axis=1)
+        assert np.median(err) <= tol
+    finally:
+        tree.close()
+        ps.close()
+
+
+def test_theta_zero_is_direct_summation(G, ctx):
+    n = 3000
+    pos, vel, mass, eps = ics.make("plummer", n, 5, 0.02)
+    ps, tree = run_gpu(G, ctx, pos, vel, mass, eps, 0.0, 8, 64, False)
+    try:
+        _, _, acc, pot = ps.get()
+        ad, pd = oracle.direct(pos, mass, eps)
+        assert rms_rel(acc, ad) <= RMS_FP32
+        assert rms_rel(pot, pd) <= RMS_FP32
+        assert tree.stats()["n_spj"] == 0
+    finally:
+        tree.close()
+        ps.close()
+
+
+def test_edge_cases(G, ctx):
+    # one particle: no force, no potential (self term removed)
+    ps, tree = run_gpu(G, ctx, np.array([[0.3, -0.2, 0.1]]), np.zeros((1, 3)), np.ones(1),
+                       np.full(1, 0.1), 0.5, 8, 64)
+    _, _, acc, pot = ps.get()
+    assert np.all(acc == 0) and abs(pot[0]) < 1e-6
+    tree.close()
+    ps.close()
+    # two bodies: closed form
+    r, e, m1, m2 = 0.75, 0.1, 0.3, 1.7
+    pos = np.array([[0.0, 0.0, 0.0], [r, 0.0, 0.0]])
+    ps, tree = run_gpu(G, ctx, pos, np.zeros((2, 3)), np.array([m1, m2]), np.full(2, e), 0.5, 1, 1)
+    _, _, acc, pot = ps.get()
+    f = (r * r + e * e) ** -1.5
+    np.testing.assert_allclose(acc[0], [m2 * r * f, 0, 0], rtol=1e-6, atol=1e-12)
+    np.testing.assert_allclose(acc[1], [-m1 * r * f, 0, 0], rtol=1e-6, atol=1e-12)
+    np.testing.assert_allclose(pot, [-m2 / np.hypot(r, e), -m1 / np.hypot(r, e)], rtol=1e-6)
+    tree.close()
+    ps.close()
+    # many duplicates: level-21 leaves larger than n_leaf, groups larger than n_grp
+    rng = np.random.default_rng(3)
+    pos = rng.normal(size=(2000, 3))
+    pos[:700] = pos[0]
+    pos[700:900] = pos[1]
+    mass = rng.uniform(0, 1, 2000)
+    mass[5] = 0.0  # a massless particle
+    eps = np.full(2000, 0.05)
+    ps, tree = run_gpu(G, ctx, pos, np.zeros((2000, 3)), mass, eps, 0.5, 4, 32, True)
+    ref = oracle.Tree(pos, mass, eps, theta=0.5, n_leaf=4, n_grp=32, quad=True)
+    check_structure(G, tree, ref, 2000)
+    _, _, acc, pot = ps.get()
+    acc_r, pot_r, _ = ref.force()
+    assert rms_rel(acc, acc_r) <= RMS_FP32
+    assert max(ref.groups()["count"]) >= 700
+    tree.close()
+    ps.close()
+    # all particles at one point (L = 1), and n_grp >= N (one group)
+    pos = np.ones((50, 3)) * 2.5
+    ps, tree = run_gpu(G, ctx, pos, np.zeros((50, 3)), np.ones(50), np.full(50, 0.1), 0.5, 2, 64)
+    ref = oracle.Tree(pos, np.ones(50), np.full(50, 0.1), theta=0.5, n_leaf=2, n_grp=64)
+    check_structure(G, tree, ref, 50)
+    _, _, acc, pot = ps.get()
+    assert np.all(acc == 0)
+    tree.close()
+    ps.close()
+
+
+def test_invalid_input_is_rejected(G, ctx):
+    with pytest.raises(G.FdpsError) as e:
+        G.Tree(ctx, theta=-1.0)
+    assert e.value.code == G.FDPS_EINVAL
+    with pytest.raises(G.FdpsError):
+        G.Tree(ctx, n_leaf=8, n_grp=4)
+    ps = G.ParticleSystem(ctx, 4)
+    pos = np.zeros((4, 3))
+    pos[2, 1] = np.nan
+    with pytest.raises(G.FdpsError) as e:
+        ps.set(pos, np.zeros((4, 3)), np.ones(4), np.full(4, 0.1))
+    assert e.value.code == G.FDPS_EINVAL
+    with pytest.raises(G.FdpsError) as e:
+        ps.set(np.zeros((4, 3)), np.zeros((4, 3)), np.ones(4), np.zeros(4))
+    assert e.value.code == G.FDPS_EINVAL
+    ps.set(np.random.default_rng(1).normal(size=(4, 3)), np.zeros((4, 3)), np.ones(4), np.full(4, 0.1))
+    with pytest.raises(G.FdpsError) as e:
+        ps.get()
+    assert e.value.code == G.FDPS_ESTATE
+    tree = G.Tree(ctx)  # monopole tree
+    with pytest.raises(G.FdpsError) as e:
+        G.fdps_tree_calc_force_all_and_write_back(ctx.h, tree.h, ps.h, G.FDPS_GRAV_EPJ,
+                                                  G.FDPS_GRAV_SPJ_QUAD)
+    assert e.value.code == G.FDPS_EINVAL
+    tree.calc_force_all_and_write_back(ps)
+    ps.get()
+    tree.close()
+    ps.close()
+
+
+def test_device_pointer_roundtrip_and_order(G, ctx):
+    torch = pytest.importorskip("torch")
+    n = 5000
+    pos, vel, mass, eps = ics.make("plummer", n, 77, 0.02)
+    dev = [torch.tensor(a, device="cuda", dtype=torch.float64).contiguous() for a in (pos, vel, mass, eps)]
+    torch.cuda.synchronize()
+    ps = G.ParticleSystem(ctx, n)
+    tree = G.Tree(ctx, theta=0.5, n_leaf=8, n_grp=64)
+    ps.set(*dev)
+    tree.calc_force_all_and_write_back(ps)
+    acc_d = torch.zeros((n, 3), device="cuda", dtype=torch.float64)
+    pos_d = torch.zeros((n, 3), device="cuda", dtype=torch.float64)
+    G.fdps_psys_get(ctx.h, ps.h, pos_d, None, acc_d, None)
+    p2, v2, acc, pot = ps.get()
+    np.testing.assert_array_equal(p2, pos)  # caller's order restored
+    np.testing.assert_array_equal(v2, vel)
+    np.testing.assert_array_equal(acc_d.cpu().numpy(), acc)
+    np.testing.assert_array_equal(pos_d.cpu().numpy(), pos)
+    tree.close()
+    ps.close()
+
+
+def test_leapfrog_matches_oracle_integration(G, ctx):
+    """Ten KDK steps of the GPU pipeline against ten oracle steps with the
+    oracle tree (monopole); trajectories agree to the force tolerance."""
+    n = 4096
+    pos, vel, mass, eps = ics.make("plummer", n, 99, 1.0 / 64.0)
+    ps, tree = run_gpu(G, ctx, pos, vel, mass, eps, 0.5, 8, 64)
+    x, v = pos.copy(), vel.copy()
+    a, p, _ = oracle.Tree(x, mass, eps, 0.5, 8, 64).force()
+    dt = 1.0 / 128.0
+    for _ in range(10):
+        tree.step(ps, dt)
+        v = oracle.kick(v, a, 0.5 * dt)
+        x = oracle.drift(x, v, dt)
+        a, p, _ = oracle.Tree(x, mass, eps, 0.5, 8, 64).force()
+        v = oracle.kick(v, a, 0.5 * dt)
+    pg, vg, ag, potg = ps.get()
+    assert np.abs(pg - x).max() < 1e-6
+    assert np.abs(vg - v).max() < 1e-5
+    ek, ep = ps.energy()
+    ek_r, ep_r = oracle.energy(v, mass, p)
+    assert abs(ek - ek_r) < 1e-6 * abs(ek_r)
+    assert abs(ep - ep_r) < 1e-5 * abs(ep_r)
+    tree.close()
+    ps.close()
