@@ -238,19 +238,15 @@ int run_force(fdps_tree* t, fdps_psys* ps, int k_spj) {
         record(t, 7);
         if ((rc = read_state(t))) return rc;
         const uint32_t ov = t->h_st.overflow;
-        if (!(ov & (kOvfPool | kOvfChunk | kOvfFrontier))) break;
+        if (!(ov & (kOvfPool | kOvfFrontier))) break;
         if (attempt > 8)
             return set_error(ctx, FDPS_EOVERFLOW, "interaction lists did not fit after %d resizes",
                              attempt);
         ++t->retries;
-        if (ov & kOvfChunk)
-            return set_error(ctx, FDPS_EOVERFLOW,
-                             "an interaction list exceeds %llu entries; lower theta or n_grp",
-                             walk_chunk());
         if (ov & kOvfFrontier)
             if ((rc = ensure_frontier(t, 2 * t->cap_frontier))) return rc;
         if (ov & kOvfPool) {
-            const int64_t need = (int64_t)(t->h_st.pool_needed * 5 / 4) +
+            const int64_t need = (int64_t)(t->h_st.pool_needed * 3 / 2) +
                                  2 * t->n_walk_warps * (int64_t)walk_chunk();
             if ((rc = ensure_pool(t, std::max<int64_t>(need, 2 * t->cap_pool)))) return rc;
         }

@@ -19,9 +19,9 @@
 // tested at a time; opened internal cells push their children (contiguous
 // ids) to the next frontier, opened leaves append one EPJ entry (node id
 // with bit 31 set: all of the leaf's particles), unopened cells one SPJ
-// entry.  A group's list is contiguous in a pool handed out in chunks of
-// 2^16 entries; when a chunk fills the group's partial list moves to a
-// fresh chunk.  Overflow of the pool or of the frontier sets a flag; the
+// entry.  A group's list is contiguous in a pool handed out in chunks of at
+// least 2^16 entries; when a chunk fills, the group's partial list moves to
+// a fresh chunk twice its length.  Overflow of the pool or of the frontier sets a flag; the
 // host then grows the buffer and repeats the walk.
 #include "fdps_internal.cuh"
 
@@ -189,13 +189,16 @@ __global__ void __launch_bounds__(kWalkBlock) k_walk(WalkArgs A) {
                 const uint32_t k = __popc(emask);
                 if (k) {
                     if (cursor + k > chunk_end) {
+                        // new chunk: at least kChunk entries and twice the
+                        // group's list so far, so long lists move O(log) times
                         const unsigned long long sofar = cursor - gstart;
+                        const unsigned long long want =
+                            2 * (sofar + k) > kChunk ? 2 * (sofar + k) : kChunk;
                         unsigned long long nb = 0;
-                        if (lane == 0) nb = atomicAdd(&st->pool_cursor, kChunk);
+                        if (lane == 0) nb = atomicAdd(&st->pool_cursor, want);
                         nb = shfl_u64(nb, 0);
-                        if (!ovf && (nb + kChunk > A.cap_pool || sofar + k > kChunk)) {
-                            if (lane == 0)
-                                atomicOr(&st->overflow, nb + kChunk > A.cap_pool ? kOvfPool : kOvfChunk);
+                        if (!ovf && nb + want > A.cap_pool) {
+                            if (lane == 0) atomicOr(&st->overflow, kOvfPool);
                             ovf = true;
                         }
                         if (!ovf) {
@@ -204,7 +207,7 @@ __global__ void __launch_bounds__(kWalkBlock) k_walk(WalkArgs A) {
                             __syncwarp();
                             gstart = nb;
                             cursor = nb + sofar;
-                            chunk_end = nb + kChunk;
+                            chunk_end = nb + want;
                         } else {
                             chunk_end = ~0ull;  // count only from here on
                         }

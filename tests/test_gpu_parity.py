@@ -105,6 +105,9 @@ CASES = [
     ("hernquist-theta0.7-ngrp256", "hernquist", 50001, 0.7, 16, 256, True),
     ("clumpy-ngrp512", "clumpy", 40000, 0.5, 16, 512, True),
     ("plummer-nleaf1", "plummer", 3000, 0.6, 1, 4, False),
+    # theta = 0 with one particle per leaf: every list holds ~70000 leaves,
+    # longer than one 2^16-entry pool chunk
+    ("plummer-theta0-long-lists", "plummer", 70000, 0.0, 1, 512, False),
 ]
 
 
@@ -125,6 +128,9 @@ def test_parity_with_oracle(G, ctx, name, model, n, theta, n_leaf, n_grp, quad):
         assert rms_rel(acc, acc_r) <= RMS_FP32
         assert rms_rel(pot, pot_r) <= RMS_FP32
         st = tree.stats()
+        if name.endswith("long-lists"):
+            offs, _ = tree.lists(0, ref.n_groups)
+            assert np.diff(offs).max() > 65536
         assert st["interactions_epj"] + st["interactions_spj"] == tot[2]
         assert st["interactions_spj"] == tot[3]
     finally:
