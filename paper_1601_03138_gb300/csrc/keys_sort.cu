@@ -173,9 +173,10 @@ __global__ void __launch_bounds__(kSortBlock) k_radix_hist(int64_t n, const uint
     hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = c;
 }
 
-// Exclusive block scan of one value per thread (blockDim.x <= 1024).
+// Exclusive block scan of one value per thread (blockDim.x <= 1024); the
+// block total is kept apart from the 32 per-warp offsets.
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total) {
-    __shared__ uint32_t s_w[32];
+    __shared__ uint32_t s_w[33];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint32_t inc = v;
 #pragma unroll
@@ -195,11 +196,11 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total)
             if (lane >= off) ti += u;
         }
         if (lane < nw) s_w[lane] = ti - t;
-        if (lane == nw - 1) s_w[31] = ti;
+        if (lane == nw - 1) s_w[32] = ti;
     }
     __syncthreads();
     uint32_t res = s_w[w] + inc - v;
-    if (total) *total = s_w[31];
+    if (total) *total = s_w[32];
     __syncthreads();
     return res;
 }

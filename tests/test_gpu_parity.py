@@ -306,3 +306,42 @@ def test_leapfrog_matches_oracle_integration(G, ctx):
     assert abs(ep - ep_r) < 1e-5 * abs(ep_r)
     tree.close()
     ps.close()
+
+
+def _sampled_parity(G, ctx, pos, vel, mass, eps, theta, n_leaf, n_grp, quad, n_sample, n_direct,
+                    direct_tol):
+    n = len(pos)
+    ps, tree = run_gpu(G, ctx, pos, vel, mass, eps, theta, n_leaf, n_grp, quad)
+    try:
+        ref = oracle.Tree(pos, mass, eps, theta=theta, n_leaf=n_leaf, n_grp=n_grp, quad=quad)
+        sample = np.random.default_rng(n).choice(ref.n_groups, n_sample, replace=False)
+        check_structure(G, tree, ref, n, sample)
+        _, _, acc, pot = ps.get()
+        acc_r, pot_r, _ = ref.force(sample)
+        rows = ~np.isnan(pot_r)
+        assert rows.sum() > 0
+        assert rms_rel(acc[rows], acc_r[rows]) <= RMS_FP32
+        assert rms_rel(pot[rows], pot_r[rows]) <= RMS_FP32
+        idx = np.random.default_rng(n + 1).choice(n, n_direct, replace=False)
+        ad, pd = oracle.direct(pos, mass, eps, idx)
+        err = np.linalg.norm(acc[idx] - ad, axis=1) / np.linalg.norm(ad, axis=1)
+        assert np.median(err) <= direct_tol
+    finally:
+        tree.close()
+        ps.close()
+
+
+def test_parity_three_million_ragged(G, ctx):
+    """More sort tiles than one block has threads, a ragged last tile."""
+    pos, vel, mass, eps = ics.make("plummer", 3_000_001, ics.SEED_BASE + 31, 1.0 / 64.0)
+    _sampled_parity(G, ctx, pos, vel, mass, eps, 0.5, 16, 128, False, 200, 256, 2e-3)
+
+
+def test_parity_at_full_bench_size(G, ctx):
+    """The benchmark's workload and launch configuration: Hernquist N = 2^24,
+    theta = 0.5, quadrupole, n_leaf = 16, n_grp = 128; every key, the
+    permutation, every node and group bit-exact; lists and forces of 64
+    sampled groups against the oracle; 256 sampled particles against the
+    FP64 direct sum."""
+    pos, vel, mass, eps = ics.make("hernquist", 1 << 24, ics.SEED_BASE + 3, 0.005)
+    _sampled_parity(G, ctx, pos, vel, mass, eps, 0.5, 16, 128, True, 64, 256, 5e-4)
