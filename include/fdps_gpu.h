@@ -132,6 +132,9 @@ void* fdps_get_stream(const fdps_ctx* ctx);
 /* Issue all further work on a caller-owned cudaStream_t (NULL = back to the
    context's own stream).  The caller keeps ownership. */
 int fdps_set_stream(fdps_ctx* ctx, void* stream);
+/* Number of CUDA kernels this library has launched on the context so far
+   (-1 for NULL). */
+int64_t fdps_kernel_launches(const fdps_ctx* ctx);
 /* Enable (1) / disable (0) per-stage CUDA-event timing in fdps_tree_stats. */
 int fdps_set_profiling(fdps_ctx* ctx, int on);
 

@@ -77,6 +77,7 @@ _PROTOS = {
     "fdps_get_stream": (_vp, [_vp]),
     "fdps_set_stream": (C.c_int, [_vp, _vp]),
     "fdps_set_profiling": (C.c_int, [_vp, C.c_int]),
+    "fdps_kernel_launches": (_i64, [_vp]),
     "fdps_psys_create": (C.c_int, [_vp, _i64, C.POINTER(_vp)]),
     "fdps_psys_destroy": (C.c_int, [_vp]),
     "fdps_psys_size": (_i64, [_vp]),
@@ -164,6 +165,10 @@ def fdps_get_stream(ctx) -> int:
 
 def fdps_set_stream(ctx, stream_ptr: int | None):
     _check(lib().fdps_set_stream(ctx, C.c_void_p(stream_ptr) if stream_ptr else None), ctx)
+
+
+def fdps_kernel_launches(ctx) -> int:
+    return int(lib().fdps_kernel_launches(ctx))
 
 
 def fdps_set_profiling(ctx, on: bool):
@@ -323,6 +328,10 @@ class Context:
 
     def set_profiling(self, on=True):
         fdps_set_profiling(self.h, on)
+
+    @property
+    def launches(self) -> int:
+        return fdps_kernel_launches(self.h)
 
 
 class ParticleSystem:

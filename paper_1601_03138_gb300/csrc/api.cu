@@ -316,6 +316,8 @@ int fdps_set_stream(fdps_ctx* ctx, void* stream) {
     return FDPS_OK;
 }
 
+int64_t fdps_kernel_launches(const fdps_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
 int fdps_set_profiling(fdps_ctx* ctx, int on) {
     if (!ctx) return FDPS_EINVAL;
     ctx->profiling = on != 0;

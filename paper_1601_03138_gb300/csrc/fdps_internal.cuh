@@ -85,6 +85,7 @@ struct fdps_ctx {
     cudaStream_t own_stream = nullptr;
     cudaStream_t stream = nullptr;
     bool profiling = false;
+    int64_t launches = 0;  // kernels launched by this library on this context
     std::string last_error;
 };
 
@@ -214,7 +215,11 @@ inline int set_error(fdps_ctx* ctx, int code, const char* fmt, ...) {
         }                                                                         \
     } while (0)
 
-#define FDPS_LAUNCH_CHECK(ctx) FDPS_CUDA_TRY(ctx, cudaGetLastError())
+#define FDPS_LAUNCH_CHECK(ctx)                   \
+    do {                                         \
+        ++(ctx)->launches;                       \
+        FDPS_CUDA_TRY(ctx, cudaGetLastError());  \
+    } while (0)
 
 template <class T>
 inline cudaError_t dev_alloc(T** p, int64_t count) {
