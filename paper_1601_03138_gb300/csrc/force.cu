@@ -103,166 +103,307 @@ __device__ __forceinline__ int owner(const uint32_t* scan, uint32_t item) {
     return lo;
 }
 
+// ---------------------------------------------------------------- FP32
+// One 128-thread CTA per i-group.  Thread t owns K i-particles
+// (i = t % P + k P, k < K) and the list slice j = t / P (mod nsl);
+// (K, P, nsl) is chosen per group to keep the most lanes busy.
+
+constexpr int kCB = 128;           // threads per CTA
+constexpr int kCW = kCB / 32;
+constexpr int kCJ = 512;           // EPJ particles per shared tile
+constexpr int kRed = 4 * kCB;     // slice-reduction slots per component
+
+struct GroupPlan {
+    int K, P, nsl;
+};
+
+__device__ __forceinline__ GroupPlan plan_group(uint32_t ni) {
+    // maximise ni * nsl / (kCB * K) over K in {1, 2, 4}; larger K on ties
+    GroupPlan best{1, 1, 1};
+    float bu = -1.f;
+#pragma unroll
+    for (int K = 4; K >= 1; K >>= 1) {
+        const int P = (int)((ni + K - 1) / K);
+        if (P > kCB) continue;
+        const int nsl = kCB / P;
+        const float u = (float)ni * nsl / (float)(kCB * K);
+        if (u > bu + 1e-6f) {
+            bu = u;
+            best = GroupPlan{K, P, nsl};
+        }
+    }
+    if (bu < 0.f) best = GroupPlan{4, kCB, 1};  // more than 4 kCB particles: rounds
+    return best;
+}
+
+// Block-wide exclusive scans of two values at once (kCB threads).
+__device__ __forceinline__ void block_scan2(uint32_t a, uint32_t b, uint32_t* ea, uint32_t* eb,
+                                            uint32_t* ta, uint32_t* tb, uint32_t* s_w) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t ia = a, ib = b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t va = __shfl_up_sync(0xFFFFFFFFu, ia, o);
+        const uint32_t vb = __shfl_up_sync(0xFFFFFFFFu, ib, o);
+        if (lane >= o) {
+            ia += va;
+            ib += vb;
+        }
+    }
+    if (lane == 31) {
+        s_w[w] = ia;
+        s_w[kCW + w] = ib;
+    }
+    __syncthreads();
+    uint32_t oa = 0, ob = 0, sa = 0, sb = 0;
+#pragma unroll
+    for (int k = 0; k < kCW; ++k) {
+        const uint32_t xa = s_w[k], xb = s_w[kCW + k];
+        if (k < w) {
+            oa += xa;
+            ob += xb;
+        }
+        sa += xa;
+        sb += xb;
+    }
+    *ea = oa + ia - a;
+    *eb = ob + ib - b;
+    *ta = sa;
+    *tb = sb;
+}
+
+__device__ __forceinline__ int owner128(const uint32_t* scan, uint32_t item) {
+    int lo = 0, hi = kCB;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (scan[mid] <= item)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Kahan running sums of one thread live in shared memory, touched once per
+// tile: sum of (q, c) at s_k[((q * 4 + c) * 2) * kCB + t], its compensation
+// kCB further on.
+__device__ __forceinline__ void kahan_smem_add(float* s_k, int q, int c, float v) {
+    float* s = s_k + ((q * 4 + c) * 2) * kCB + threadIdx.x;
+    float* cp = s + kCB;
+    const float y = v - *cp;
+    const float t = *s + y;
+    *cp = (t - *s) - y;
+    *s = t;
+}
+
+template <bool QUAD, int K>
+__device__ __forceinline__ void force_group_f32(const ForceArgs& A, uint32_t gf, uint32_t ni,
+                                                unsigned long long off, uint32_t len, float4 gch,
+                                                float4 gcl, int P, int nsl, uint32_t ib,
+                                                float4* s_j, float4* s_s0, float4* s_s1,
+                                                float2* s_s2, uint32_t* s_ef, uint32_t* s_es,
+                                                uint32_t* s_w, double* s_red, float* s_k) {
+    const int t = threadIdx.x;
+    const int ip = t % P, sl = t / P;
+    const bool on = sl < nsl;
+    float xi[K], yi[K], zi[K], e2[K];
+    bool iv[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        const uint32_t i = ib + (uint32_t)(ip + q * P);
+        iv[q] = on && i < ni;
+        xi[q] = yi[q] = zi[q] = 0.f;
+        e2[q] = 1.f;
+        if (iv[q]) {
+            const float4 h = A.pf_hi[gf + i], l = A.pf_lo[gf + i];
+            xi[q] = (h.x - gch.x) + (l.x - gcl.x);
+            yi[q] = (h.y - gch.y) + (l.y - gcl.y);
+            zi[q] = (h.z - gch.z) + (l.z - gcl.z);
+            e2[q] = l.w;
+        }
+    }
+    const int kbeg = on ? sl : 0x3FFFFFFF;
+#pragma unroll
+    for (int k = 0; k < 8 * K; ++k) s_k[k * kCB + t] = 0.0f;
+
+    for (uint32_t base = 0; base < len; base += kCB) {
+        const bool ve = base + t < len;
+        const uint32_t e = ve ? A.pool[off + base + t] : 0u;
+        const bool isleaf = ve && (e & kLeafTag);
+        const bool isspj = ve && !(e & kLeafTag);
+        const uint32_t node = e & ~kLeafTag;
+        uint32_t cnt = 0, first = 0;
+        if (isleaf) {
+            cnt = A.nd_count[node];
+            first = A.nd_first[node];
+        }
+        uint32_t rs, es, ns, total;
+        block_scan2(isspj ? 1u : 0u, cnt, &rs, &es, &ns, &total, s_w);
+        if (isspj) {
+            const float4 fh = A.nd_fh[node], fl = A.nd_fl[node];
+            s_s0[rs] = make_float4((fh.x - gch.x) + (fl.x - gcl.x), (fh.y - gch.y) + (fl.y - gcl.y),
+                                   (fh.z - gch.z) + (fl.z - gcl.z), fh.w);
+            if (QUAD) {
+                s_s1[rs] = A.nd_fq0[node];
+                s_s2[rs] = A.nd_fq1[node];
+            }
+        }
+        s_ef[t] = first;
+        s_es[t] = es;
+        __syncthreads();
+        // ---- superparticles of this chunk
+        if (ns > 0) {
+            float pax[K], pay[K], paz[K], pp[K];
+#pragma unroll
+            for (int q = 0; q < K; ++q) pax[q] = pay[q] = paz[q] = pp[q] = 0.f;
+            for (int k = kbeg; k < (int)ns; k += nsl) {
+                const float4 a = s_s0[k];
+                float4 q0;
+                float2 q1;
+                if (QUAD) {
+                    q0 = s_s1[k];
+                    q1 = s_s2[k];
+                }
+#pragma unroll
+                for (int q = 0; q < K; ++q) {
+                    const float rx = xi[q] - a.x, ry = yi[q] - a.y, rz = zi[q] - a.z;
+                    const float R2 = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, e2[q])));
+                    const float Ri = rsqrtf(R2);
+                    const float Ri2 = Ri * Ri;
+                    const float MRi = a.w * Ri;
+                    const float MRi3 = MRi * Ri2;
+                    if (QUAD) {
+                        const float Qrx = fmaf(q0.x, rx, fmaf(q0.w, ry, q1.x * rz));
+                        const float Qry = fmaf(q0.w, rx, fmaf(q0.y, ry, q1.y * rz));
+                        const float Qrz = fmaf(q1.x, rx, fmaf(q1.y, ry, q0.z * rz));
+                        const float rQr = fmaf(rx, Qrx, fmaf(ry, Qry, rz * Qrz));
+                        const float Ri5 = Ri2 * Ri2 * Ri;
+                        const float c = fmaf(2.5f * rQr, Ri5 * Ri2, MRi3);
+                        pax[q] = fmaf(Qrx, Ri5, fmaf(-c, rx, pax[q]));
+                        pay[q] = fmaf(Qry, Ri5, fmaf(-c, ry, pay[q]));
+                        paz[q] = fmaf(Qrz, Ri5, fmaf(-c, rz, paz[q]));
+                        pp[q] -= fmaf(0.5f * rQr, Ri5, MRi);
+                    } else {
+                        pax[q] = fmaf(-MRi3, rx, pax[q]);
+                        pay[q] = fmaf(-MRi3, ry, pay[q]);
+                        paz[q] = fmaf(-MRi3, rz, paz[q]);
+                        pp[q] -= MRi;
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < K; ++q) {
+                kahan_smem_add(s_k, q, 0, pax[q]);
+                kahan_smem_add(s_k, q, 1, pay[q]);
+                kahan_smem_add(s_k, q, 2, paz[q]);
+                kahan_smem_add(s_k, q, 3, pp[q]);
+            }
+        }
+        // ---- particles of the opened leaves, in shared tiles of kCJ
+        for (uint32_t c0 = 0; c0 < total; c0 += kCJ) {
+            const uint32_t m = total - c0 < (uint32_t)kCJ ? total - c0 : (uint32_t)kCJ;
+            if (c0 > 0) __syncthreads();  // previous tile fully consumed
+            for (uint32_t k = t; k < m; k += kCB) {
+                const uint32_t item = c0 + k;
+                const int src = owner128(s_es, item);
+                const uint32_t p = s_ef[src] + (item - s_es[src]);
+                const float4 h = A.pf_hi[p], l = A.pf_lo[p];
+                s_j[k] = make_float4((h.x - gch.x) + (l.x - gcl.x), (h.y - gch.y) + (l.y - gcl.y),
+                                     (h.z - gch.z) + (l.z - gcl.z), h.w);
+            }
+            __syncthreads();
+            float pax[K], pay[K], paz[K], pp[K];
+#pragma unroll
+            for (int q = 0; q < K; ++q) pax[q] = pay[q] = paz[q] = pp[q] = 0.f;
+            for (int k = kbeg; k < (int)m; k += nsl) {
+                const float4 j = s_j[k];
+#pragma unroll
+                for (int q = 0; q < K; ++q) {
+                    const float dx = j.x - xi[q], dy = j.y - yi[q], dz = j.z - zi[q];
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, e2[q])));
+                    const float ri = rsqrtf(r2);
+                    const float mri = j.w * ri;
+                    const float mri3 = mri * (ri * ri);
+                    pax[q] = fmaf(mri3, dx, pax[q]);
+                    pay[q] = fmaf(mri3, dy, pay[q]);
+                    paz[q] = fmaf(mri3, dz, paz[q]);
+                    pp[q] -= mri;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < K; ++q) {
+                kahan_smem_add(s_k, q, 0, pax[q]);
+                kahan_smem_add(s_k, q, 1, pay[q]);
+                kahan_smem_add(s_k, q, 2, paz[q]);
+                kahan_smem_add(s_k, q, 3, pp[q]);
+            }
+        }
+        __syncthreads();  // chunk buffers are rewritten next
+    }
+    // ---- combine slices (FP64) and write back
+    const int rows = P * K;  // i-slots of this round; nsl * rows <= 4 kCB
+#pragma unroll
+    for (int q = 0; q < K; ++q)
+        if (on)
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                s_red[c * kRed + sl * rows + ip + q * P] =
+                    iv[q] ? (double)s_k[((q * 4 + c) * 2) * kCB + t] - (double)s_k[((q * 4 + c) * 2 + 1) * kCB + t]
+                          : 0.0;
+    __syncthreads();
+    for (int r = t; r < rows; r += kCB) {
+        const uint32_t i = ib + (uint32_t)r;
+        if (i >= ni) continue;
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int s2 = 0; s2 < nsl; ++s2)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) v[c] += s_red[c * kRed + s2 * rows + r];
+        const uint32_t p = gf + i;
+        A.ax[p] = v[0];
+        A.ay[p] = v[1];
+        A.az[p] = v[2];
+        A.pot[p] = v[3] + A.pm[p] / A.peps[p];
+    }
+    __syncthreads();
+}
+
 template <bool QUAD>
-__global__ void __launch_bounds__(kFBlock) k_force_f32(ForceArgs A) {
-    __shared__ float4 s_j[kFWarps][kJCap];
-    __shared__ float4 s_s0[kFWarps][32];
-    __shared__ float4 s_s1[kFWarps][32];
-    __shared__ float2 s_s2[kFWarps][32];
-    __shared__ uint32_t s_ef[kFWarps][32];
-    __shared__ uint32_t s_es[kFWarps][33];
-    __shared__ double s_red[kFWarps][4][32];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t lt = (1u << lane) - 1u;
+__global__ void __launch_bounds__(kCB) k_force_f32(ForceArgs A) {
+    __shared__ __align__(16) float4 s_j[kCJ];
+    __shared__ __align__(16) float4 s_s0[kCB];
+    __shared__ __align__(16) float4 s_s1[QUAD ? kCB : 1];
+    __shared__ __align__(8) float2 s_s2[QUAD ? kCB : 1];
+    __shared__ uint32_t s_ef[kCB];
+    __shared__ uint32_t s_es[kCB];
+    __shared__ uint32_t s_w[2 * kCW];
+    __shared__ uint32_t s_g;
+    __shared__ double s_red[4 * kRed];  // [component][slice * rows + i-slot]
+    __shared__ float s_k[4 * 8 * kCB];  // Kahan sums and compensations
     DevState* st = A.st;
     const uint32_t ngroups = (uint32_t)st->n_groups;
     for (;;) {
-        uint32_t g = 0;
-        if (lane == 0) g = atomicAdd(&st->force_counter, 1u);
-        g = __shfl_sync(0xFFFFFFFFu, g, 0);
+        if (threadIdx.x == 0) s_g = atomicAdd(&st->force_counter, 1u);
+        __syncthreads();
+        const uint32_t g = s_g;
+        __syncthreads();
         if (g >= ngroups) break;
         const uint32_t ni = A.g_count[g], gf = A.g_first[g];
         const unsigned long long off = A.g_off[g];
         const uint32_t len = A.g_len[g];
         const float4 gch = A.g_ch[g], gcl = A.g_cl[g];
-        const Split sp(ni);
-        const int ioff = lane % sp.P;
-        const int sl = lane / sp.P;
-        const bool lane_on = sl < sp.nsl;
-        for (uint32_t ib = 0; ib < ni; ib += (uint32_t)sp.P) {
-            const uint32_t i = ib + (uint32_t)ioff;
-            const bool iv = lane_on && i < ni;
-            float xi = 0.f, yi = 0.f, zi = 0.f, e2 = 1.f;
-            if (iv) {
-                const float4 h = A.pf_hi[gf + i], l = A.pf_lo[gf + i];
-                xi = (h.x - gch.x) + (l.x - gcl.x);
-                yi = (h.y - gch.y) + (l.y - gcl.y);
-                zi = (h.z - gch.z) + (l.z - gcl.z);
-                e2 = l.w;
-            }
-            const int kbeg = iv ? sl : 0x7FFFFFFF;
-            Kahan4 acc;
-            acc.init();
-            for (uint32_t t = 0; t < len; t += 32) {
-                const bool ve = t + lane < len;
-                const uint32_t e = ve ? A.pool[off + t + lane] : 0u;
-                const bool isleaf = ve && (e & kLeafTag);
-                const bool isspj = ve && !(e & kLeafTag);
-                const uint32_t node = e & ~kLeafTag;
-                const uint32_t smask = __ballot_sync(0xFFFFFFFFu, isspj);
-                const int ns = __popc(smask);
-                if (isspj) {
-                    const int r = __popc(smask & lt);
-                    const float4 fh = A.nd_fh[node], fl = A.nd_fl[node];
-                    s_s0[w][r] = make_float4((fh.x - gch.x) + (fl.x - gcl.x),
-                                             (fh.y - gch.y) + (fl.y - gcl.y),
-                                             (fh.z - gch.z) + (fl.z - gcl.z), fh.w);
-                    if (QUAD) {
-                        s_s1[w][r] = A.nd_fq0[node];
-                        s_s2[w][r] = A.nd_fq1[node];
-                    }
-                }
-                uint32_t cnt = 0, first = 0;
-                if (isleaf) {
-                    cnt = A.nd_count[node];
-                    first = A.nd_first[node];
-                }
-                uint32_t inc = cnt;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-                    if (lane >= o) inc += v;
-                }
-                const uint32_t total = __shfl_sync(0xFFFFFFFFu, inc, 31);
-                s_ef[w][lane] = first;
-                s_es[w][lane] = inc - cnt;
-                __syncwarp();
-                // ---- superparticles of this tile
-                if (ns > 0) {
-                    float pax = 0.f, pay = 0.f, paz = 0.f, pp = 0.f;
-                    for (int k = kbeg; k < ns; k += sp.nsl) {
-                        const float4 a = s_s0[w][k];
-                        const float rx = xi - a.x, ry = yi - a.y, rz = zi - a.z;
-                        const float R2 = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, e2)));
-                        const float Ri = rsqrtf(R2);
-                        const float Ri2 = Ri * Ri;
-                        const float MRi = a.w * Ri;
-                        const float MRi3 = MRi * Ri2;
-                        if (QUAD) {
-                            const float4 q0 = s_s1[w][k];
-                            const float2 q1 = s_s2[w][k];
-                            const float Qrx = fmaf(q0.x, rx, fmaf(q0.w, ry, q1.x * rz));
-                            const float Qry = fmaf(q0.w, rx, fmaf(q0.y, ry, q1.y * rz));
-                            const float Qrz = fmaf(q1.x, rx, fmaf(q1.y, ry, q0.z * rz));
-                            const float rQr = fmaf(rx, Qrx, fmaf(ry, Qry, rz * Qrz));
-                            const float Ri5 = Ri2 * Ri2 * Ri;
-                            const float c = fmaf(2.5f * rQr, Ri5 * Ri2, MRi3);
-                            pax = fmaf(Qrx, Ri5, fmaf(-c, rx, pax));
-                            pay = fmaf(Qry, Ri5, fmaf(-c, ry, pay));
-                            paz = fmaf(Qrz, Ri5, fmaf(-c, rz, paz));
-                            pp -= fmaf(0.5f * rQr, Ri5, MRi);
-                        } else {
-                            pax = fmaf(-MRi3, rx, pax);
-                            pay = fmaf(-MRi3, ry, pay);
-                            paz = fmaf(-MRi3, rz, paz);
-                            pp -= MRi;
-                        }
-                    }
-                    acc.add(0, pax);
-                    acc.add(1, pay);
-                    acc.add(2, paz);
-                    acc.add(3, pp);
-                }
-                // ---- particles of the opened leaves, in chunks of kJCap
-                for (uint32_t c0 = 0; c0 < total; c0 += kJCap) {
-                    const uint32_t m = total - c0 < (uint32_t)kJCap ? total - c0 : (uint32_t)kJCap;
-                    for (uint32_t k = lane; k < m; k += 32) {
-                        const uint32_t item = c0 + k;
-                        const int src = owner(s_es[w], item);
-                        const uint32_t p = s_ef[w][src] + (item - s_es[w][src]);
-                        const float4 h = A.pf_hi[p], l = A.pf_lo[p];
-                        s_j[w][k] = make_float4((h.x - gch.x) + (l.x - gcl.x),
-                                                (h.y - gch.y) + (l.y - gcl.y),
-                                                (h.z - gch.z) + (l.z - gcl.z), h.w);
-                    }
-                    __syncwarp();
-                    float pax = 0.f, pay = 0.f, paz = 0.f, pp = 0.f;
-                    for (int k = kbeg; k < (int)m; k += sp.nsl) {
-                        const float4 j = s_j[w][k];
-                        const float dx = j.x - xi, dy = j.y - yi, dz = j.z - zi;
-                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, e2)));
-                        const float ri = rsqrtf(r2);
-                        const float mri = j.w * ri;
-                        const float mri3 = mri * (ri * ri);
-                        pax = fmaf(mri3, dx, pax);
-                        pay = fmaf(mri3, dy, pay);
-                        paz = fmaf(mri3, dz, paz);
-                        pp -= mri;
-                    }
-                    acc.add(0, pax);
-                    acc.add(1, pay);
-                    acc.add(2, paz);
-                    acc.add(3, pp);
-                    __syncwarp();
-                }
-                __syncwarp();
-            }
-            // ---- combine slices in FP64 and write back
-#pragma unroll
-            for (int k = 0; k < 4; ++k) s_red[w][k][lane] = iv ? acc.value(k) : 0.0;
-            __syncwarp();
-            if (iv && sl == 0) {
-                double r[4] = {0.0, 0.0, 0.0, 0.0};
-                for (int s2 = 0; s2 < sp.nsl; ++s2)
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) r[k] += s_red[w][k][s2 * sp.P + ioff];
-                const uint32_t p = gf + i;
-                A.ax[p] = r[0];
-                A.ay[p] = r[1];
-                A.az[p] = r[2];
-                A.pot[p] = r[3] + A.pm[p] / A.peps[p];
-            }
-            __syncwarp();
+        for (uint32_t ib = 0; ib < ni;) {
+            const uint32_t rem = ni - ib;
+            const GroupPlan pl = plan_group(rem);
+            if (pl.K == 1)
+                force_group_f32<QUAD, 1>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, s_j, s_s0,
+                                         s_s1, s_s2, s_ef, s_es, s_w, s_red, s_k);
+            else if (pl.K == 2)
+                force_group_f32<QUAD, 2>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, s_j, s_s0,
+                                         s_s1, s_s2, s_ef, s_es, s_w, s_red, s_k);
+            else
+                force_group_f32<QUAD, 4>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, s_j, s_s0,
+                                         s_s1, s_s2, s_ef, s_es, s_w, s_red, s_k);
+            ib += (uint32_t)(pl.P * pl.K);
         }
     }
 }
@@ -405,8 +546,8 @@ int force_blocks(fdps_ctx* ctx, int precision, int quad) {
         e = quad ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_f64<true>, kFBlock, 0)
                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_f64<false>, kFBlock, 0);
     else
-        e = quad ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_f32<true>, kFBlock, 0)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_f32<false>, kFBlock, 0);
+        e = quad ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_f32<true>, kCB, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_f32<false>, kCB, 0);
     if (e != cudaSuccess || per_sm < 1) per_sm = 4;
     return per_sm * ctx->sm_count;
 }
@@ -452,9 +593,9 @@ int compute_forces(fdps_tree* t, fdps_psys* ps, int spj_kind) {
             k_force_f64<false><<<blocks, kFBlock, 0, s>>>(A);
     } else {
         if (quad)
-            k_force_f32<true><<<blocks, kFBlock, 0, s>>>(A);
+            k_force_f32<true><<<blocks, kCB, 0, s>>>(A);
         else
-            k_force_f32<false><<<blocks, kFBlock, 0, s>>>(A);
+            k_force_f32<false><<<blocks, kCB, 0, s>>>(A);
     }
     FDPS_LAUNCH_CHECK(ctx);
     return FDPS_OK;
