@@ -20,6 +20,9 @@ LIB = os.path.join(BUILD, "libfdpsgpu.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
+# per-file extras: the FP32 force kernel flushes FP32 denormals (its inputs
+# r^2 + eps^2 >= eps^2 are never denormal), so rsqrtf is the bare MUFU op
+FILE_FLAGS = {"force.cu": ["-ftz=true"]}
 
 
 def nvcc() -> str:
@@ -49,7 +52,7 @@ def _compile(src, verbose_regs=False):
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
     if not _stale(obj, [src, *_headers()]) and not verbose_regs:
         return obj, ""
-    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *FILE_FLAGS.get(os.path.basename(src), []), "-c", src, "-o", obj]
     if verbose_regs:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -106,12 +106,18 @@ __device__ __forceinline__ int owner(const uint32_t* scan, uint32_t item) {
 // ---------------------------------------------------------------- FP32
 // One 128-thread CTA per i-group.  Thread t owns K i-particles
 // (i = t % P + k P, k < K) and the list slice j = t / P (mod nsl);
-// (K, P, nsl) is chosen per group to keep the most lanes busy.
+// (K, P, nsl) is chosen per group to keep the most lanes busy.  The list is
+// consumed in chunks of 512 entries (4 per thread); each chunk's
+// superparticles and leaf particles are staged in shared memory, and each
+// thread folds its FP32 partial sums of the chunk into Kahan-compensated
+// running sums once per chunk.
 
-constexpr int kCB = 128;           // threads per CTA
+constexpr int kCB = 128;            // threads per CTA
 constexpr int kCW = kCB / 32;
-constexpr int kCJ = 512;           // EPJ particles per shared tile
-constexpr int kRed = 4 * kCB;     // slice-reduction slots per component
+constexpr int kEPT = 4;             // list entries per thread per chunk
+constexpr int kCE = kCB * kEPT;     // list entries per chunk
+constexpr int kCJ = 256;            // leaf particles per shared tile
+constexpr int kRed = 4 * kCB;       // slice-reduction slots per component
 
 struct GroupPlan {
     int K, P, nsl;
@@ -172,21 +178,17 @@ __device__ __forceinline__ void block_scan2(uint32_t a, uint32_t b, uint32_t* ea
     *tb = sb;
 }
 
-__device__ __forceinline__ int owner128(const uint32_t* scan, uint32_t item) {
-    int lo = 0, hi = kCB;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (scan[mid] <= item)
-            lo = mid;
-        else
-            hi = mid;
-    }
+// Largest e in [0, kCE) with scan[e] <= item.
+__device__ __forceinline__ int owner_chunk(const uint32_t* scan, uint32_t item) {
+    int lo = 0;
+#pragma unroll
+    for (int step = kCE / 2; step > 0; step >>= 1)
+        if (scan[lo + step] <= item) lo += step;
     return lo;
 }
 
-// Kahan running sums of one thread live in shared memory, touched once per
-// tile: sum of (q, c) at s_k[((q * 4 + c) * 2) * kCB + t], its compensation
-// kCB further on.
+// Kahan running sums of one thread in shared memory: sum of (q, c) at
+// s_k[((q * 4 + c) * 2) * kCB + t], its compensation kCB further on.
 __device__ __forceinline__ void kahan_smem_add(float* s_k, int q, int c, float v) {
     float* s = s_k + ((q * 4 + c) * 2) * kCB + threadIdx.x;
     float* cp = s + kCB;
@@ -196,13 +198,20 @@ __device__ __forceinline__ void kahan_smem_add(float* s_k, int q, int c, float v
     *s = t;
 }
 
+template <bool QUAD>
+struct SpjBuf {
+    float4* s0;  // (x, y, z) relative to the group centre, M
+    float4* s1;  // Qxx, Qyy, Qzz, Qxy
+    float2* s2;  // Qxz, Qyz
+};
+
 template <bool QUAD, int K>
-__device__ __forceinline__ void force_group_f32(const ForceArgs& A, uint32_t gf, uint32_t ni,
+__device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf, uint32_t ni,
                                                 unsigned long long off, uint32_t len, float4 gch,
                                                 float4 gcl, int P, int nsl, uint32_t ib,
-                                                float4* s_j, float4* s_s0, float4* s_s1,
-                                                float2* s_s2, uint32_t* s_ef, uint32_t* s_es,
-                                                uint32_t* s_w, double* s_red, float* s_k) {
+                                                float4* s_j, SpjBuf<QUAD> sb, uint32_t* s_ef,
+                                                uint32_t* s_es, uint32_t* s_w, double* s_red,
+                                                float* s_k) {
     const int t = threadIdx.x;
     const int ip = t % P, sl = t / P;
     const bool on = sl < nsl;
@@ -226,77 +235,84 @@ __device__ __forceinline__ void force_group_f32(const ForceArgs& A, uint32_t gf,
 #pragma unroll
     for (int k = 0; k < 8 * K; ++k) s_k[k * kCB + t] = 0.0f;
 
-    for (uint32_t base = 0; base < len; base += kCB) {
-        const bool ve = base + t < len;
-        const uint32_t e = ve ? A.pool[off + base + t] : 0u;
-        const bool isleaf = ve && (e & kLeafTag);
-        const bool isspj = ve && !(e & kLeafTag);
-        const uint32_t node = e & ~kLeafTag;
-        uint32_t cnt = 0, first = 0;
-        if (isleaf) {
-            cnt = A.nd_count[node];
-            first = A.nd_first[node];
+    for (uint32_t base = 0; base < len; base += kCE) {
+        // ---- this thread's kEPT consecutive entries: type, node data, leaf range
+        uint32_t nspj = 0, npart = 0;
+        uint32_t ent[kEPT];
+#pragma unroll
+        for (int r = 0; r < kEPT; ++r) {
+            const uint32_t u = base + (uint32_t)(t * kEPT + r);
+            ent[r] = u < len ? A.pool[off + u] : 0xFFFFFFFFu;
+        }
+        uint32_t lcnt[kEPT], lfirst[kEPT];
+#pragma unroll
+        for (int r = 0; r < kEPT; ++r) {
+            const bool leaf = ent[r] != 0xFFFFFFFFu && (ent[r] & kLeafTag);
+            const bool spj = ent[r] != 0xFFFFFFFFu && !(ent[r] & kLeafTag);
+            lcnt[r] = leaf ? A.nd_count[ent[r] & ~kLeafTag] : 0u;
+            lfirst[r] = leaf ? A.nd_first[ent[r] & ~kLeafTag] : 0u;
+            nspj += spj ? 1u : 0u;
+            npart += lcnt[r];
         }
         uint32_t rs, es, ns, total;
-        block_scan2(isspj ? 1u : 0u, cnt, &rs, &es, &ns, &total, s_w);
-        if (isspj) {
-            const float4 fh = A.nd_fh[node], fl = A.nd_fl[node];
-            s_s0[rs] = make_float4((fh.x - gch.x) + (fl.x - gcl.x), (fh.y - gch.y) + (fl.y - gcl.y),
-                                   (fh.z - gch.z) + (fl.z - gcl.z), fh.w);
-            if (QUAD) {
-                s_s1[rs] = A.nd_fq0[node];
-                s_s2[rs] = A.nd_fq1[node];
-            }
-        }
-        s_ef[t] = first;
-        s_es[t] = es;
-        __syncthreads();
-        // ---- superparticles of this chunk
-        if (ns > 0) {
-            float pax[K], pay[K], paz[K], pp[K];
+        block_scan2(nspj, npart, &rs, &es, &ns, &total, s_w);
 #pragma unroll
-            for (int q = 0; q < K; ++q) pax[q] = pay[q] = paz[q] = pp[q] = 0.f;
-            for (int k = kbeg; k < (int)ns; k += nsl) {
-                const float4 a = s_s0[k];
-                float4 q0;
-                float2 q1;
+        for (int r = 0; r < kEPT; ++r) {
+            const bool spj = ent[r] != 0xFFFFFFFFu && !(ent[r] & kLeafTag);
+            if (spj) {
+                const uint32_t node = ent[r];
+                const float4 fh = A.nd_fh[node], fl = A.nd_fl[node];
+                sb.s0[rs] = make_float4((fh.x - gch.x) + (fl.x - gcl.x),
+                                        (fh.y - gch.y) + (fl.y - gcl.y),
+                                        (fh.z - gch.z) + (fl.z - gcl.z), fh.w);
                 if (QUAD) {
-                    q0 = s_s1[k];
-                    q1 = s_s2[k];
+                    sb.s1[rs] = A.nd_fq0[node];
+                    sb.s2[rs] = A.nd_fq1[node];
                 }
+                ++rs;
+            }
+            s_ef[t * kEPT + r] = lfirst[r];
+            s_es[t * kEPT + r] = es;
+            es += lcnt[r];
+        }
+        __syncthreads();
+        float pax[K], pay[K], paz[K], pp[K];
 #pragma unroll
-                for (int q = 0; q < K; ++q) {
-                    const float rx = xi[q] - a.x, ry = yi[q] - a.y, rz = zi[q] - a.z;
-                    const float R2 = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, e2[q])));
-                    const float Ri = rsqrtf(R2);
-                    const float Ri2 = Ri * Ri;
-                    const float MRi = a.w * Ri;
-                    const float MRi3 = MRi * Ri2;
-                    if (QUAD) {
-                        const float Qrx = fmaf(q0.x, rx, fmaf(q0.w, ry, q1.x * rz));
-                        const float Qry = fmaf(q0.w, rx, fmaf(q0.y, ry, q1.y * rz));
-                        const float Qrz = fmaf(q1.x, rx, fmaf(q1.y, ry, q0.z * rz));
-                        const float rQr = fmaf(rx, Qrx, fmaf(ry, Qry, rz * Qrz));
-                        const float Ri5 = Ri2 * Ri2 * Ri;
-                        const float c = fmaf(2.5f * rQr, Ri5 * Ri2, MRi3);
-                        pax[q] = fmaf(Qrx, Ri5, fmaf(-c, rx, pax[q]));
-                        pay[q] = fmaf(Qry, Ri5, fmaf(-c, ry, pay[q]));
-                        paz[q] = fmaf(Qrz, Ri5, fmaf(-c, rz, paz[q]));
-                        pp[q] -= fmaf(0.5f * rQr, Ri5, MRi);
-                    } else {
-                        pax[q] = fmaf(-MRi3, rx, pax[q]);
-                        pay[q] = fmaf(-MRi3, ry, pay[q]);
-                        paz[q] = fmaf(-MRi3, rz, paz[q]);
-                        pp[q] -= MRi;
-                    }
-                }
+        for (int q = 0; q < K; ++q) pax[q] = pay[q] = paz[q] = pp[q] = 0.f;
+        // ---- superparticles of this chunk
+        for (int k = kbeg; k < (int)ns; k += nsl) {
+            const float4 a = sb.s0[k];
+            float4 q0;
+            float2 q1;
+            if (QUAD) {
+                q0 = sb.s1[k];
+                q1 = sb.s2[k];
             }
 #pragma unroll
             for (int q = 0; q < K; ++q) {
-                kahan_smem_add(s_k, q, 0, pax[q]);
-                kahan_smem_add(s_k, q, 1, pay[q]);
-                kahan_smem_add(s_k, q, 2, paz[q]);
-                kahan_smem_add(s_k, q, 3, pp[q]);
+                const float rx = xi[q] - a.x, ry = yi[q] - a.y, rz = zi[q] - a.z;
+                const float R2 = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, e2[q])));
+                const float Ri = rsqrtf(R2);
+                const float Ri2 = Ri * Ri;
+                const float MRi = a.w * Ri;
+                const float MRi3 = MRi * Ri2;
+                if (QUAD) {
+                    const float Qrx = fmaf(q0.x, rx, fmaf(q0.w, ry, q1.x * rz));
+                    const float Qry = fmaf(q0.w, rx, fmaf(q0.y, ry, q1.y * rz));
+                    const float Qrz = fmaf(q1.x, rx, fmaf(q1.y, ry, q0.z * rz));
+                    const float rQr = fmaf(rx, Qrx, fmaf(ry, Qry, rz * Qrz));
+                    const float Ri5 = Ri2 * Ri2 * Ri;
+                    const float c = fmaf(2.5f * rQr, Ri5 * Ri2, MRi3);
+                    pax[q] = fmaf(Qrx, Ri5, fmaf(-c, rx, pax[q]));
+                    pay[q] = fmaf(Qry, Ri5, fmaf(-c, ry, pay[q]));
+                    paz[q] = fmaf(Qrz, Ri5, fmaf(-c, rz, paz[q]));
+                    pp[q] -= fmaf(0.5f * rQr, Ri5, MRi);
+                } else {
+                    pax[q] = fmaf(-MRi3, rx, pax[q]);
+                    pay[q] = fmaf(-MRi3, ry, pay[q]);
+                    paz[q] = fmaf(-MRi3, rz, paz[q]);
+                    pp[q] -= MRi;
+                }
             }
         }
         // ---- particles of the opened leaves, in shared tiles of kCJ
@@ -305,16 +321,13 @@ __device__ __forceinline__ void force_group_f32(const ForceArgs& A, uint32_t gf,
             if (c0 > 0) __syncthreads();  // previous tile fully consumed
             for (uint32_t k = t; k < m; k += kCB) {
                 const uint32_t item = c0 + k;
-                const int src = owner128(s_es, item);
+                const int src = owner_chunk(s_es, item);
                 const uint32_t p = s_ef[src] + (item - s_es[src]);
                 const float4 h = A.pf_hi[p], l = A.pf_lo[p];
                 s_j[k] = make_float4((h.x - gch.x) + (l.x - gcl.x), (h.y - gch.y) + (l.y - gcl.y),
                                      (h.z - gch.z) + (l.z - gcl.z), h.w);
             }
             __syncthreads();
-            float pax[K], pay[K], paz[K], pp[K];
-#pragma unroll
-            for (int q = 0; q < K; ++q) pax[q] = pay[q] = paz[q] = pp[q] = 0.f;
             for (int k = kbeg; k < (int)m; k += nsl) {
                 const float4 j = s_j[k];
 #pragma unroll
@@ -330,25 +343,27 @@ __device__ __forceinline__ void force_group_f32(const ForceArgs& A, uint32_t gf,
                     pp[q] -= mri;
                 }
             }
+        }
 #pragma unroll
-            for (int q = 0; q < K; ++q) {
-                kahan_smem_add(s_k, q, 0, pax[q]);
-                kahan_smem_add(s_k, q, 1, pay[q]);
-                kahan_smem_add(s_k, q, 2, paz[q]);
-                kahan_smem_add(s_k, q, 3, pp[q]);
-            }
+        for (int q = 0; q < K; ++q) {
+            kahan_smem_add(s_k, q, 0, pax[q]);
+            kahan_smem_add(s_k, q, 1, pay[q]);
+            kahan_smem_add(s_k, q, 2, paz[q]);
+            kahan_smem_add(s_k, q, 3, pp[q]);
         }
         __syncthreads();  // chunk buffers are rewritten next
     }
-    // ---- combine slices (FP64) and write back
-    const int rows = P * K;  // i-slots of this round; nsl * rows <= 4 kCB
+    // ---- combine slices (FP64) and write back; s_red overlays the
+    // superparticle buffer, which is idle until the next chunk
+    const int rows = P * K;  // i-slots of this round; nsl * rows <= kRed
 #pragma unroll
     for (int q = 0; q < K; ++q)
         if (on)
 #pragma unroll
             for (int c = 0; c < 4; ++c)
                 s_red[c * kRed + sl * rows + ip + q * P] =
-                    iv[q] ? (double)s_k[((q * 4 + c) * 2) * kCB + t] - (double)s_k[((q * 4 + c) * 2 + 1) * kCB + t]
+                    iv[q] ? (double)s_k[((q * 4 + c) * 2) * kCB + t] -
+                                (double)s_k[((q * 4 + c) * 2 + 1) * kCB + t]
                           : 0.0;
     __syncthreads();
     for (int r = t; r < rows; r += kCB) {
@@ -369,16 +384,21 @@ __device__ __forceinline__ void force_group_f32(const ForceArgs& A, uint32_t gf,
 
 template <bool QUAD>
 __global__ void __launch_bounds__(kCB) k_force_f32(ForceArgs A) {
+    constexpr int kSpjBytes = kCE * (QUAD ? 40 : 16);
+    constexpr int kRedBytes = 4 * kRed * 8;
+    constexpr int kUnion = kSpjBytes > kRedBytes ? kSpjBytes : kRedBytes;
+    __shared__ __align__(16) unsigned char s_union[kUnion];
     __shared__ __align__(16) float4 s_j[kCJ];
-    __shared__ __align__(16) float4 s_s0[kCB];
-    __shared__ __align__(16) float4 s_s1[QUAD ? kCB : 1];
-    __shared__ __align__(8) float2 s_s2[QUAD ? kCB : 1];
-    __shared__ uint32_t s_ef[kCB];
-    __shared__ uint32_t s_es[kCB];
+    __shared__ uint32_t s_ef[kCE];
+    __shared__ uint32_t s_es[kCE];
     __shared__ uint32_t s_w[2 * kCW];
     __shared__ uint32_t s_g;
-    __shared__ double s_red[4 * kRed];  // [component][slice * rows + i-slot]
     __shared__ float s_k[4 * 8 * kCB];  // Kahan sums and compensations
+    SpjBuf<QUAD> sb;
+    sb.s0 = reinterpret_cast<float4*>(s_union);
+    sb.s1 = reinterpret_cast<float4*>(s_union + kCE * 16);
+    sb.s2 = reinterpret_cast<float2*>(s_union + kCE * 32);
+    double* s_red = reinterpret_cast<double*>(s_union);
     DevState* st = A.st;
     const uint32_t ngroups = (uint32_t)st->n_groups;
     for (;;) {
@@ -392,17 +412,16 @@ __global__ void __launch_bounds__(kCB) k_force_f32(ForceArgs A) {
         const uint32_t len = A.g_len[g];
         const float4 gch = A.g_ch[g], gcl = A.g_cl[g];
         for (uint32_t ib = 0; ib < ni;) {
-            const uint32_t rem = ni - ib;
-            const GroupPlan pl = plan_group(rem);
+            const GroupPlan pl = plan_group(ni - ib);
             if (pl.K == 1)
-                force_group_f32<QUAD, 1>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, s_j, s_s0,
-                                         s_s1, s_s2, s_ef, s_es, s_w, s_red, s_k);
+                force_round_f32<QUAD, 1>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, s_j, sb,
+                                         s_ef, s_es, s_w, s_red, s_k);
             else if (pl.K == 2)
-                force_group_f32<QUAD, 2>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, s_j, s_s0,
-                                         s_s1, s_s2, s_ef, s_es, s_w, s_red, s_k);
+                force_round_f32<QUAD, 2>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, s_j, sb,
+                                         s_ef, s_es, s_w, s_red, s_k);
             else
-                force_group_f32<QUAD, 4>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, s_j, s_s0,
-                                         s_s1, s_s2, s_ef, s_es, s_w, s_red, s_k);
+                force_round_f32<QUAD, 4>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, s_j, sb,
+                                         s_ef, s_es, s_w, s_red, s_k);
             ib += (uint32_t)(pl.P * pl.K);
         }
     }
