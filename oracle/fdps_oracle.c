@@ -8,7 +8,8 @@
  * header or constant with the CUDA library.
  *
  * What it computes, step by step, in the order of the paper's Sect. 3.2
- * ("construct the tree of local particles ... usual tree traversal"):
+ * (build a tree of the particles, then traverse it per group of i-particles
+ * with a fixed opening angle):
  *   root box -> Morton keys -> stable sort -> octree (BFS order) ->
  *   moments (monopole, traceless quadrupole) -> i-groups (Barnes 1990,
  *   Sect. 5.5, eq. wtime_force) -> per-group walk with a fixed opening angle

@@ -15,7 +15,7 @@
 // order; COM = S / M.  These fixed orders make the centres of mass, and
 // thus the opening decisions of the walk, reproducible bit for bit.  The
 // traceless quadrupole Q_ab = sum m (3 d_a d_b - |d|^2 delta_ab) about the
-// COM (Sect. 2.1.2: "up to the quadrupole moment") is summed over particles
+// COM (Sect. 2.1.2: FDPS ships superparticles up to the quadrupole) is summed over particles
 // for leaves and combined from the children with the parallel-axis shift
 // for internal nodes.
 //

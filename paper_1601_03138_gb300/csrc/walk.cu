@@ -1,6 +1,6 @@
 // walk.cu -- interaction lists: one warp walks the tree for one i-group.
 //
-// The "usual tree traversal" with a fixed opening angle (Sect. 3.2), done
+// The Barnes-Hut traversal with a fixed opening angle (Sect. 3.2), done
 // once per i-group as in the modified tree algorithm of Barnes (1990) that
 // the paper's cost model uses (Sect. 5.5, T_icalc,const).  The paper does
 // not state the criterion; this library opens a cell C for group G iff

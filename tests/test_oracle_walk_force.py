@@ -328,8 +328,8 @@ def test_circular_two_body_orbit_energy_bounded():
 @pytest.mark.parametrize("theta,n_grp", [(0.3, 32), (0.5, 64), (0.5, 128), (0.7, 64)])
 def test_list_length_follows_the_paper_model(theta, n_grp):
     """Mean interaction-list length per particle against eq. nlist_long of
-    Sect. 5.5 (with n_p = 1), which the paper fits to its measured lengths
-    "reasonably well"; a factor 1.5 either way is allowed."""
+    Sect. 5.5 (with n_p = 1), which the paper reports as a fair fit to its
+    measured lengths; a factor 1.5 either way is allowed."""
     pos, vel, mass, eps = ics.make_config("plummer16k")
     n = len(pos)
     t = oracle.Tree(pos, mass, eps, theta=theta, n_leaf=8, n_grp=n_grp)
