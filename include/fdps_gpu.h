@@ -71,9 +71,9 @@ typedef enum {
     FDPS_GRAV_SPJ_QUAD = 2  /* monopole + traceless quadrupole term */
 } fdps_kernel_id;
 
-/* Tree-for-force parameters (TreeForForceLong, Sect. 2.2; theta of the
-   "usual tree traversal", Sect. 3.2; n_grp of the modified tree algorithm,
-   Sect. 5.5).
+/* Tree-for-force parameters (TreeForForceLong, Sect. 2.2; theta is the fixed
+   opening angle of the Barnes-Hut traversal, Sect. 3.2; n_grp the group size
+   of the modified tree algorithm, Sect. 5.5).
      theta      >= 0   opening angle; 0 opens every cell (direct summation)
      n_leaf     1..16  a cell with <= n_leaf particles is a leaf
      n_grp      >= n_leaf, <= 4096: a maximal cell with <= n_grp particles
