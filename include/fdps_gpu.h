@@ -225,6 +225,33 @@ int fdps_tree_get_groups(const fdps_tree* tree, int64_t cap, int64_t* n_out,
 int fdps_tree_get_lists(const fdps_tree* tree, int64_t g0, int64_t g1,
                         int64_t* offsets, uint32_t* entries, int64_t cap);
 
+/* ------------------------------------------- allocation-free key sort
+   The paper has no counterpart to this call; it is a service for callers
+   that may not allocate device memory themselves: code running while a
+   stream is captured into a CUDA graph (a cudaMalloc there invalidates the
+   capture) and hosts that hand out all device memory through their own
+   allocator.  It computes what fdps_tree_calc_force_all_and_write_back
+   computes first (root box, 63-bit Morton keys, stable radix sort) for one
+   particle set and allocates nothing: its scratch (about 5.3 MB) is a
+   file-scope device array that every GPU which loads the library holds
+   until the process exits.
+     x, y, z      device arrays of n FP64 positions (SoA), borrowed
+     n            1 .. FDPS_NOALLOC_MAX_N; larger n returns FDPS_EINVAL
+     keys_sorted  device output [n]: the keys in ascending order
+     perm         device output [n]: sorted position -> input index (ties
+                  keep input order)
+     stream       cudaStream_t to run on (NULL = legacy default stream)
+   Returns FDPS_OK, FDPS_EINVAL (NULL pointer, n out of range) or
+   FDPS_ECUDA.  The work is queued on `stream` and not waited for.  The
+   first call on a device looks up the scratch array's device address;
+   make that first call outside any stream capture.  All calls on a device
+   share the one scratch array: calls that may overlap on the GPU (other
+   streams, other host threads) race and must be serialised by the caller. */
+#define FDPS_NOALLOC_MAX_N (1 << 18)
+int fdps_morton_sort_noalloc(const double* x, const double* y, const double* z,
+                             int64_t n, uint64_t* keys_sorted, uint32_t* perm,
+                             void* stream);
+
 #ifdef __cplusplus
 }
 #endif

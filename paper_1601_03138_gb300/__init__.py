@@ -97,7 +97,10 @@ _PROTOS = {
                                       _vp, _vp]),
     "fdps_tree_get_groups": (C.c_int, [_vp, _i64, C.POINTER(_i64), _vp, _vp, _vp, _vp]),
     "fdps_tree_get_lists": (C.c_int, [_vp, _i64, _i64, _vp, _vp, _i64]),
+    "fdps_morton_sort_noalloc": (C.c_int, [_vp, _vp, _vp, _i64, _vp, _vp, _vp]),
 }
+
+FDPS_NOALLOC_MAX_N = 1 << 18
 
 _lib = None
 
@@ -301,6 +304,17 @@ def fdps_tree_get_lists(ctx, tree, g0, g1):
     _check(lib().fdps_tree_get_lists(tree, g0, g1, C.c_void_p(offs.ctypes.data),
                                      C.c_void_p(ent.ctypes.data), len(ent)), ctx)
     return offs, ent[: offs[-1]]
+
+
+def fdps_morton_sort_noalloc(x, y, z, n, keys_sorted, perm, stream=None):
+    """Allocation-free Morton keys + stable sort of n <= FDPS_NOALLOC_MAX_N
+    positions; every argument is a device pointer (int) or has data_ptr()."""
+    def dp(a):
+        return C.c_void_p(a.data_ptr() if hasattr(a, "data_ptr") else int(a))
+    rc = lib().fdps_morton_sort_noalloc(dp(x), dp(y), dp(z), int(n), dp(keys_sorted), dp(perm),
+                                        C.c_void_p(stream) if stream else None)
+    if rc < 0:
+        raise FdpsError(rc, "fdps_morton_sort_noalloc failed")
 
 
 # ------------------------------------------------------------ handle classes

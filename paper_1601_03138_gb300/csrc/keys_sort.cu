@@ -399,4 +399,96 @@ int reorder_particles(fdps_tree* t, fdps_psys* ps) {
     return FDPS_OK;
 }
 
+// ------------------------------------------------- allocation-free variant
+//
+// fdps_morton_sort_noalloc: root box, Morton keys and the stable sort of one
+// particle set with every scratch buffer taken from g_noalloc_scratch, a
+// file-scope device array, so the call itself allocates nothing.  It exists
+// for callers that may not allocate device memory on their own: code that
+// runs while a stream is being captured into a CUDA graph (a cudaMalloc
+// there breaks the capture), and hosts such as frameworks or real-time
+// loops that own every byte of device memory through their own allocator.
+
+namespace {
+
+constexpr int64_t kNoAllocMaxN = int64_t(1) << 18;  // FDPS_NOALLOC_MAX_N
+constexpr int kNoAllocBoxBlocks = 256;
+constexpr int64_t kNoAllocTiles = kNoAllocMaxN / kSortTile;
+
+constexpr size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+constexpr size_t kOffState = 0;
+constexpr size_t kOffBox = align256(kOffState + sizeof(DevState));
+constexpr size_t kOffHist = align256(kOffBox + sizeof(BoxPartial) * kNoAllocBoxBlocks);
+constexpr size_t kOffDtot = align256(kOffHist + sizeof(uint32_t) * kRadix * kNoAllocTiles);
+constexpr size_t kOffKeysIn = align256(kOffDtot + sizeof(uint32_t) * kRadix);
+constexpr size_t kOffKeysA = align256(kOffKeysIn + sizeof(uint64_t) * kNoAllocMaxN);
+constexpr size_t kOffValsA = align256(kOffKeysA + sizeof(uint64_t) * kNoAllocMaxN);
+constexpr size_t kNoAllocBytes = align256(kOffValsA + sizeof(uint32_t) * kNoAllocMaxN);
+
+// Held by every device that loads the library, until the process exits.
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+unsigned char* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+}  // namespace
 }  // namespace fdps
+
+extern "C" int fdps_morton_sort_noalloc(const double* x, const double* y, const double* z,
+                                        int64_t n, uint64_t* keys_sorted, uint32_t* perm,
+                                        void* stream) {
+    using namespace fdps;
+    if (!x || !y || !z || !keys_sorted || !perm) return FDPS_EINVAL;
+    if (n < 1 || n > kNoAllocMaxN) return FDPS_EINVAL;  // beyond FDPS_NOALLOC_MAX_N
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+        cudaGetLastError();
+        return FDPS_ECUDA;
+    }
+    // Once per device, with that device current: the device address of the
+    // scratch array (its host-side name is only a stand-in).
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return FDPS_ECUDA;
+        }
+        g_noalloc_ptr[dev] = static_cast<unsigned char*>(p);
+    }
+    unsigned char* base = g_noalloc_ptr[dev];
+    DevState* st = reinterpret_cast<DevState*>(base + kOffState);
+    BoxPartial* box = reinterpret_cast<BoxPartial*>(base + kOffBox);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(base + kOffHist);
+    uint32_t* dtot = reinterpret_cast<uint32_t*>(base + kOffDtot);
+    uint64_t* keys_in = reinterpret_cast<uint64_t*>(base + kOffKeysIn);
+    uint64_t* keys_a = reinterpret_cast<uint64_t*>(base + kOffKeysA);
+    uint32_t* vals_a = reinterpret_cast<uint32_t*>(base + kOffValsA);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int ntiles = (int)((n + kSortTile - 1) / kSortTile);
+    // The array keeps the previous call's contents; the state block is the
+    // one region read before it is written, so it is cleared first.
+    if (cudaMemsetAsync(st, 0, sizeof(DevState), s) != cudaSuccess) {
+        cudaGetLastError();
+        return FDPS_ECUDA;
+    }
+    k_box_partial<<<kNoAllocBoxBlocks, 256, 0, s>>>(n, x, y, z, box);
+    k_box_final<<<1, 32, 0, s>>>(kNoAllocBoxBlocks, box, st);
+    k_keys<<<ntiles, kSortBlock, 0, s>>>(n, x, y, z, st, keys_in, hist, ntiles);
+    const uint64_t* kin = keys_in;
+    const uint32_t* vin = nullptr;
+    for (int pass = 0; pass < 8; ++pass) {
+        const int shift = 8 * pass;
+        if (pass > 0) k_radix_hist<<<ntiles, kSortBlock, 0, s>>>(n, kin, shift, hist, ntiles);
+        k_radix_scan_rows<<<kRadix, 1024, 0, s>>>(hist, ntiles, dtot);
+        k_radix_scan_digits<<<1, kRadix, 0, s>>>(dtot);
+        // even passes land in the scratch pair, odd ones in the caller's
+        // output, so the eighth pass leaves the result there
+        uint64_t* ko = (pass & 1) ? keys_sorted : keys_a;
+        uint32_t* vo = (pass & 1) ? perm : vals_a;
+        k_radix_scatter<<<ntiles, kSortBlock, 0, s>>>(n, kin, vin, ko, vo, shift, hist, dtot, ntiles);
+        kin = ko;
+        vin = vo;
+    }
+    if (cudaGetLastError() != cudaSuccess) return FDPS_ECUDA;
+    return FDPS_OK;
+}
