@@ -194,6 +194,35 @@ int fdps_step(fdps_tree* tree, fdps_psys* ps, double dt);
    potential of the last force calculation. */
 int fdps_psys_energy(fdps_psys* ps, double* kinetic, double* potential);
 
+/* ------------------------------------------------ ensembles and runs */
+
+/* Declare the particle system an ensemble of n_sys independent systems
+   (the "multiwalk" use of Sect. 2.1.2: many independent interaction sets per
+   accelerator launch).  offsets is a host array [n_sys + 1] with
+   offsets[0] = 0, offsets[n_sys] = n and every system holding >= 1 row:
+   rows offsets[k] .. offsets[k+1]-1 of the arrays passed to fdps_psys_set
+   form system k.  Every force calculation then treats each system on its
+   own (its own root box, keys, octree, i-groups and lists; no system feels
+   another) in the same launches.  Clears the particle data: call
+   fdps_psys_set afterwards.  n_sys = 1 restores one system.
+   Errors: FDPS_EINVAL (bad offsets), FDPS_ENOMEM. */
+int fdps_psys_set_systems(fdps_psys* ps, int32_t n_sys, const int64_t* offsets);
+/* Number of systems (1 unless set otherwise; -1 for NULL). */
+int32_t fdps_psys_num_systems(const fdps_psys* ps);
+/* Per-system kinetic (sum m v^2 / 2) and potential (sum m phi / 2) energy
+   into host arrays [n_sys]; FDPS_ESTATE before any force calculation. */
+int fdps_psys_energy_systems(fdps_psys* ps, double* kinetic, double* potential);
+/* n_steps kick-drift-kick steps of the example's integrator (Sect. 2.2).
+   The first step runs as fdps_step and sizes every buffer with headroom;
+   each later step replays a CUDA graph of the whole step (kick, drift, the
+   full force pipeline, kick) captured on the context's stream, which must
+   therefore be a stream that can be captured (the context's own stream,
+   or a caller stream other than the legacy default stream).  A step whose
+   force calculation outgrows a captured buffer is redone with larger
+   buffers and the graphs are captured again.  Needs valid forces
+   (FDPS_ESTATE); synchronises the stream once per step. */
+int fdps_run(fdps_tree* tree, fdps_psys* ps, double dt, int64_t n_steps);
+
 /* --------------------------------------------------- introspection
    Test and diagnostic access to the last force calculation's
    intermediate data.  All outputs are host arrays; each call synchronises

@@ -98,6 +98,10 @@ _PROTOS = {
     "fdps_tree_get_groups": (C.c_int, [_vp, _i64, C.POINTER(_i64), _vp, _vp, _vp, _vp]),
     "fdps_tree_get_lists": (C.c_int, [_vp, _i64, _i64, _vp, _vp, _i64]),
     "fdps_morton_sort_noalloc": (C.c_int, [_vp, _vp, _vp, _i64, _vp, _vp, _vp]),
+    "fdps_psys_set_systems": (C.c_int, [_vp, _i32, _vp]),
+    "fdps_psys_num_systems": (_i32, [_vp]),
+    "fdps_psys_energy_systems": (C.c_int, [_vp, _vp, _vp]),
+    "fdps_run": (C.c_int, [_vp, _vp, _d, _i64]),
 }
 
 FDPS_NOALLOC_MAX_N = 1 << 18
@@ -243,6 +247,28 @@ def fdps_step(ctx, tree, ps, dt):
     _check(lib().fdps_step(tree, ps, float(dt)), ctx)
 
 
+def fdps_psys_set_systems(ctx, ps, offsets):
+    """offsets: [n_sys + 1] row offsets of the independent systems."""
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    _check(lib().fdps_psys_set_systems(ps, len(off) - 1, C.c_void_p(off.ctypes.data)), ctx)
+
+
+def fdps_psys_num_systems(ps) -> int:
+    return int(lib().fdps_psys_num_systems(ps))
+
+
+def fdps_psys_energy_systems(ctx, ps):
+    s = fdps_psys_num_systems(ps)
+    k = np.zeros(s)
+    p = np.zeros(s)
+    _check(lib().fdps_psys_energy_systems(ps, C.c_void_p(k.ctypes.data), C.c_void_p(p.ctypes.data)), ctx)
+    return k, p
+
+
+def fdps_run(ctx, tree, ps, dt, n_steps):
+    _check(lib().fdps_run(tree, ps, float(dt), int(n_steps)), ctx)
+
+
 def fdps_psys_energy(ctx, ps):
     k, p = C.c_double(), C.c_double()
     _check(lib().fdps_psys_energy(ps, C.byref(k), C.byref(p)), ctx)
@@ -382,6 +408,12 @@ class ParticleSystem:
     def energy(self):
         return fdps_psys_energy(self.ctx.h, self.h)
 
+    def set_systems(self, offsets):
+        fdps_psys_set_systems(self.ctx.h, self.h, offsets)
+
+    def energy_systems(self):
+        return fdps_psys_energy_systems(self.ctx.h, self.h)
+
     def kick(self, dt_half):
         fdps_kick(self.ctx.h, self.h, dt_half)
 
@@ -412,6 +444,9 @@ class Tree:
 
     def step(self, psys: ParticleSystem, dt: float):
         fdps_step(self.ctx.h, self.h, psys.h, dt)
+
+    def run(self, psys: ParticleSystem, dt: float, n_steps: int):
+        fdps_run(self.ctx.h, self.h, psys.h, dt, n_steps)
 
     def stats(self):
         return fdps_tree_get_stats(self.ctx.h, self.h)

@@ -13,7 +13,7 @@ namespace fdps {
 int walk_blocks(fdps_ctx* ctx);
 int walk_warps_per_block();
 unsigned long long walk_chunk();
-int launch_walk(fdps_tree* t, int blocks);
+int launch_walk(fdps_tree* t, const uint32_t* sys, int blocks);
 int energy_scratch_doubles();
 }  // namespace fdps
 
@@ -187,8 +187,44 @@ __global__ void k_reset_counters(DevState* st, int what) {
     if (what & 4) st->overflow &= ~(kOvfNodes | kOvfGroups);
 }
 
+bool g_capturing = false;  // set while fdps_run captures a step
+
 void record(fdps_tree* t, int k) {
-    if (t->ev_ok && t->ctx->profiling) cudaEventRecord(t->ev[k], t->ctx->stream);
+    if (t->ev_ok && t->ctx->profiling && !g_capturing) cudaEventRecord(t->ev[k], t->ctx->stream);
+}
+
+int ensure_systems(fdps_tree* t, int64_t n_sys) {
+    if (n_sys <= t->cap_sys) return FDPS_OK;
+    dev_free(t->sys_box);
+    t->cap_sys = 0;
+    if (dev_alloc(&t->sys_box, n_sys) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(t->ctx, FDPS_ENOMEM, "device allocation for %lld system boxes failed",
+                         (long long)n_sys);
+    }
+    t->cap_sys = n_sys;
+    return FDPS_OK;
+}
+
+// The launches of one force calculation with the buffers as they are: no
+// allocation, no host synchronisation (so it can be captured in a graph).
+// Overflow of a buffer is left in the device state word.
+int launch_force_pipeline(fdps_tree* t, fdps_psys* ps, int k_spj) {
+    fdps_ctx* ctx = t->ctx;
+    cudaStream_t s = ctx->stream;
+    int rc;
+    FDPS_CUDA_TRY(ctx, cudaMemsetAsync(t->st, 0, sizeof(DevState), s));
+    if ((rc = keys_and_sort(t, ps))) return rc;
+    if ((rc = reorder_particles(t, ps))) return rc;
+    if ((rc = build_tree(t, ps))) return rc;
+    if ((rc = compute_moments(t, ps))) return rc;
+    if ((rc = select_groups(t, ps))) return rc;
+    k_reset_counters<<<1, 32, 0, s>>>(t->st, 1);
+    FDPS_LAUNCH_CHECK(ctx);
+    if ((rc = launch_walk(t, ps->d_sys, (int)(t->n_walk_warps / walk_warps_per_block())))) return rc;
+    k_reset_counters<<<1, 32, 0, s>>>(t->st, 2);
+    FDPS_LAUNCH_CHECK(ctx);
+    return compute_forces(t, ps, k_spj);
 }
 
 int run_force(fdps_tree* t, fdps_psys* ps, int k_spj) {
@@ -196,8 +232,9 @@ int run_force(fdps_tree* t, fdps_psys* ps, int k_spj) {
     const int64_t n = ps->n;
     int rc;
     if ((rc = ensure_particles(t, n))) return rc;
+    if ((rc = ensure_systems(t, ps->n_sys))) return rc;
     const int64_t nl = t->p.n_leaf, ng = t->p.n_grp;
-    if ((rc = ensure_nodes(t, std::min<int64_t>(8 * n / nl, 3 * n) + 1024))) return rc;
+    if ((rc = ensure_nodes(t, std::min<int64_t>(8 * n / nl, 3 * n) + 1024 + ps->n_sys))) return rc;
     if ((rc = ensure_groups(t, std::min<int64_t>(n, 8 * n / ng + 1024)))) return rc;
     if ((rc = ensure_pool(t, 32 * n + t->n_walk_warps * (int64_t)walk_chunk()))) return rc;
     if ((rc = ensure_frontier(t, 4096))) return rc;
@@ -234,7 +271,7 @@ int run_force(fdps_tree* t, fdps_psys* ps, int k_spj) {
     for (int attempt = 0;; ++attempt) {
         k_reset_counters<<<1, 32, 0, s>>>(t->st, 1);
         FDPS_LAUNCH_CHECK(ctx);
-        if ((rc = launch_walk(t, wblocks))) return rc;
+        if ((rc = launch_walk(t, ps->d_sys, wblocks))) return rc;
         record(t, 7);
         if ((rc = read_state(t))) return rc;
         const uint32_t ov = t->h_st.overflow;
@@ -374,6 +411,9 @@ int fdps_psys_destroy(fdps_psys* ps) {
     dev_free(ps->d_flag);
     dev_free(ps->d_red);
     dev_free(ps->stage);
+    dev_free(ps->d_off);
+    dev_free(ps->d_sys);
+    dev_free(ps->d_sys_red);
     delete ps;
     return FDPS_OK;
 }
@@ -513,6 +553,7 @@ int fdps_tree_destroy(fdps_tree* t) {
     dev_free(t->lvl_scan);
     dev_free(t->grp_scan);
     dev_free(t->sort_dtot);
+    dev_free(t->sys_box);
     for (int k = 0; k < 10; ++k)
         if (t->ev[k]) cudaEventDestroy(t->ev[k]);
     delete t;
@@ -610,11 +651,13 @@ int fdps_tree_get_box(const fdps_tree* tc, double* out5) {
     if (!tc || !out5) return FDPS_EINVAL;
     fdps_tree* t = const_cast<fdps_tree*>(tc);
     if (!t->valid) return set_error(t->ctx, FDPS_ESTATE, "no force calculation yet");
-    int rc = read_state(t);
-    if (rc) return rc;
-    for (int a = 0; a < 3; ++a) out5[a] = t->h_st.lo[a];
-    out5[3] = t->h_st.L;
-    out5[4] = t->h_st.s;
+    SysBox b;
+    FDPS_CUDA_TRY(t->ctx, cudaMemcpyAsync(&b, t->sys_box, sizeof(SysBox), cudaMemcpyDeviceToHost,
+                                          t->ctx->stream));
+    FDPS_CUDA_TRY(t->ctx, cudaStreamSynchronize(t->ctx->stream));
+    for (int a = 0; a < 3; ++a) out5[a] = b.lo[a];
+    out5[3] = b.L;
+    out5[4] = b.s;
     return FDPS_OK;
 }
 
@@ -758,6 +801,124 @@ int fdps_tree_get_lists(const fdps_tree* tc, int64_t g0, int64_t g1, int64_t* of
     free(hlen);
     if (e) return set_error(t->ctx, FDPS_ECUDA, "list readback failed: %s", cudaGetErrorString(e));
     return FDPS_OK;
+}
+
+int fdps_psys_set_systems(fdps_psys* ps, int32_t n_sys, const int64_t* offsets) {
+    if (!ps) return FDPS_EINVAL;
+    fdps_ctx* ctx = ps->ctx;
+    if (n_sys < 1 || !offsets) return set_error(ctx, FDPS_EINVAL, "need n_sys >= 1 and offsets");
+    if (offsets[0] != 0 || offsets[n_sys] != ps->n)
+        return set_error(ctx, FDPS_EINVAL, "offsets must run from 0 to n = %lld", (long long)ps->n);
+    for (int32_t k = 0; k < n_sys; ++k)
+        if (offsets[k + 1] <= offsets[k])
+            return set_error(ctx, FDPS_EINVAL, "system %d is empty or offsets decrease", (int)k);
+    cudaSetDevice(ctx->device);
+    dev_free(ps->d_off);
+    dev_free(ps->d_sys);
+    dev_free(ps->d_sys_red);
+    ps->n_sys = 1;
+    ps->has_data = false;
+    ps->has_forces = false;
+    if (n_sys == 1) return FDPS_OK;
+    if (dev_alloc(&ps->d_off, n_sys + 1) != cudaSuccess || dev_alloc(&ps->d_sys, ps->n) != cudaSuccess ||
+        dev_alloc(&ps->d_sys_red, 2 * (int64_t)n_sys) != cudaSuccess) {
+        cudaGetLastError();
+        dev_free(ps->d_off);
+        dev_free(ps->d_sys);
+        dev_free(ps->d_sys_red);
+        return set_error(ctx, FDPS_ENOMEM, "device allocation for %d systems failed", (int)n_sys);
+    }
+    ps->n_sys = n_sys;
+    FDPS_CUDA_TRY(ctx, cudaMemcpyAsync(ps->d_off, offsets, sizeof(int64_t) * (n_sys + 1),
+                                       cudaMemcpyHostToDevice, ctx->stream));
+    int rc = launch_sys_index(ps);
+    if (rc) return rc;
+    FDPS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return FDPS_OK;
+}
+
+int32_t fdps_psys_num_systems(const fdps_psys* ps) { return ps ? ps->n_sys : -1; }
+
+int fdps_psys_energy_systems(fdps_psys* ps, double* kinetic, double* potential) {
+    if (!ps || !kinetic || !potential) return FDPS_EINVAL;
+    if (!ps->has_forces) return set_error(ps->ctx, FDPS_ESTATE, "no force calculation yet");
+    cudaSetDevice(ps->ctx->device);
+    return launch_energy_systems(ps, kinetic, potential);
+}
+
+int fdps_run(fdps_tree* t, fdps_psys* ps, double dt, int64_t n_steps) {
+    if (!t || !ps) return FDPS_EINVAL;
+    fdps_ctx* ctx = t->ctx;
+    if (!ps->has_forces) return set_error(ctx, FDPS_ESTATE, "no force calculation yet");
+    if (n_steps <= 0) return FDPS_OK;
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = ctx->stream;
+    const int k_spj = t->p.moment == FDPS_QUADRUPOLE ? FDPS_GRAV_SPJ_QUAD : FDPS_GRAV_SPJ_MONO;
+    int rc = fdps_step(t, ps, dt);  // sizes every buffer
+    if (rc || n_steps == 1) return rc;
+    // headroom so that later steps rarely outgrow the captured buffers
+    const DevState& h = t->h_st;
+    if ((rc = ensure_nodes(t, h.n_nodes + h.n_nodes / 4 + 1024))) return rc;
+    if ((rc = ensure_groups(t, std::min<int64_t>(ps->n, h.n_groups + h.n_groups / 4 + 1024)))) return rc;
+    if ((rc = ensure_pool(t, (int64_t)(h.pool_needed * 3 / 2) + 2 * t->n_walk_warps * (int64_t)walk_chunk())))
+        return rc;
+    if ((rc = ensure_frontier(t, 2 * (int64_t)h.max_frontier + 1024))) return rc;
+    const uint32_t ovf_mask = kOvfNodes | kOvfGroups | kOvfPool | kOvfFrontier;
+    // the particle buffers flip in every force calculation, so a step reads
+    // buffer `cur` and leaves buffer 1 - cur: one graph for each parity
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    for (int64_t k = 1; k < n_steps && !rc; ++k) {
+        const int par = ps->cur;
+        if (!exec[par]) {
+            cudaGraph_t graph = nullptr;
+            FDPS_CUDA_TRY(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            g_capturing = true;
+            rc = launch_kick(ps, 0.5 * dt);
+            if (!rc) rc = launch_drift(ps, dt);
+            if (!rc) rc = launch_force_pipeline(t, ps, k_spj);
+            if (!rc) rc = launch_kick_guarded(ps, 0.5 * dt, &t->st->overflow, ovf_mask);
+            g_capturing = false;
+            ps->cur = par;  // capture only records; the flip happens on replay
+            cudaError_t e = cudaStreamEndCapture(s, &graph);
+            if (!rc && e != cudaSuccess)
+                rc = set_error(ctx, FDPS_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+            if (!rc) {
+                e = cudaGraphInstantiate(&exec[par], graph, 0);
+                if (e != cudaSuccess)
+                    rc = set_error(ctx, FDPS_ECUDA, "graph instantiation failed: %s",
+                                   cudaGetErrorString(e));
+            }
+            if (graph) cudaGraphDestroy(graph);
+            if (rc) break;
+        }
+        cudaError_t e = cudaGraphLaunch(exec[par], s);
+        uint32_t ov = 0;
+        if (!e) e = cudaMemcpyAsync(&ov, &t->st->overflow, sizeof(ov), cudaMemcpyDeviceToHost, s);
+        if (!e) e = cudaStreamSynchronize(s);
+        if (e) {
+            rc = set_error(ctx, FDPS_ECUDA, "graph replay failed: %s", cudaGetErrorString(e));
+            break;
+        }
+        ps->cur = 1 - par;  // the replayed reorder flipped the buffers
+        if (ov & ovf_mask) {
+            // this step's force overflowed: redo it with growing buffers, then
+            // the skipped kick; later steps recapture with the new buffers
+            ++t->retries;
+            for (int q = 0; q < 2; ++q)
+                if (exec[q]) {
+                    cudaGraphExecDestroy(exec[q]);
+                    exec[q] = nullptr;
+                }
+            if ((rc = run_force(t, ps, k_spj))) break;
+            rc = launch_kick(ps, 0.5 * dt);
+        }
+    }
+    for (int q = 0; q < 2; ++q)
+        if (exec[q]) cudaGraphExecDestroy(exec[q]);
+    if (rc) return rc;
+    t->valid = true;
+    ps->has_forces = true;
+    return read_state(t);
 }
 
 }  // extern "C"

@@ -105,21 +105,28 @@ __device__ __forceinline__ uint32_t meta_level(uint32_t m) { return m & 0xFFu; }
 __device__ __forceinline__ uint32_t meta_nchild(uint32_t m) { return (m >> 8) & 0xFFu; }
 __device__ __forceinline__ bool meta_leaf(uint32_t m) { return (m >> 16) & 1u; }
 
-__global__ void k_root(DevState* st, int64_t n, int n_leaf, uint32_t* nd_first, uint32_t* nd_count,
-                       uint32_t* nd_child, uint32_t* nd_meta, uint32_t* nd_parent, uint64_t* nd_qlo,
-                       uint64_t* nd_prefix) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    nd_first[0] = 0;
-    nd_count[0] = (uint32_t)n;
-    nd_child[0] = 0xFFFFFFFFu;
-    nd_meta[0] = (n <= n_leaf ? 1u : 0u) << 16;
-    nd_parent[0] = 0xFFFFFFFFu;
-    nd_qlo[0] = 0;
-    nd_prefix[0] = 0;
-    st->lvl_start[0] = 0;
-    for (int l = 1; l < kMaxLevel + 3; ++l) st->lvl_start[l] = 1;
-    st->n_nodes = 1;
-    st->max_level = 0;
+// Level 0: one root per system (node k = root of system k, owning
+// positions off[k] .. off[k+1]; a single root over all n if off is null).
+__global__ void k_roots(DevState* st, int n_roots, const int64_t* __restrict__ off, int64_t n,
+                        int n_leaf, uint32_t* nd_first, uint32_t* nd_count, uint32_t* nd_child,
+                        uint32_t* nd_meta, uint32_t* nd_parent, uint64_t* nd_qlo,
+                        uint64_t* nd_prefix) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_roots; k += gridDim.x * blockDim.x) {
+        const int64_t a = off ? off[k] : 0, b = off ? off[k + 1] : n;
+        nd_first[k] = (uint32_t)a;
+        nd_count[k] = (uint32_t)(b - a);
+        nd_child[k] = 0xFFFFFFFFu;
+        nd_meta[k] = (b - a <= n_leaf ? 1u : 0u) << 16;
+        nd_parent[k] = 0xFFFFFFFFu;
+        nd_qlo[k] = 0;
+        nd_prefix[k] = 0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->lvl_start[0] = 0;
+        for (int l = 1; l < kMaxLevel + 3; ++l) st->lvl_start[l] = n_roots;
+        st->n_nodes = n_roots;
+        st->max_level = 0;
+    }
 }
 
 // Slot s = 8 * (parent - first parent of the level) + octant.
@@ -248,7 +255,8 @@ __device__ __forceinline__ void split_hilo(double v, float* hi, float* lo) {
 
 template <bool QUAD>
 __global__ void __launch_bounds__(256) k_moments_level(
-    int l, const DevState* __restrict__ st, const double* __restrict__ px,
+    int l, const DevState* __restrict__ st, const SysBox* __restrict__ box,
+    const uint32_t* __restrict__ sys, const double* __restrict__ px,
     const double* __restrict__ py, const double* __restrict__ pz, const double* __restrict__ pm,
     const uint32_t* __restrict__ nd_first, const uint32_t* __restrict__ nd_count,
     const uint32_t* __restrict__ nd_child, const uint32_t* __restrict__ nd_meta,
@@ -256,10 +264,11 @@ __global__ void __launch_bounds__(256) k_moments_level(
     dvec4* __restrict__ nd_com, double* __restrict__ nd_quad, float4* __restrict__ nd_fh,
     float4* __restrict__ nd_fl, float4* __restrict__ nd_fq0, float2* __restrict__ nd_fq1) {
     const int64_t a = st->lvl_start[l], b = st->lvl_start[l + 1];
-    const double c0x = st->c0[0], c0y = st->c0[1], c0z = st->c0[2];
     for (int64_t i = a + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < b;
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t meta = nd_meta[i];
+        const SysBox& bx = box[sys ? sys[nd_first[i]] : 0];
+        const double c0x = bx.c0[0], c0y = bx.c0[1], c0z = bx.c0[2];
         double M = 0.0, Sx = 0.0, Sy = 0.0, Sz = 0.0;
         const bool leaf = meta_leaf(meta);
         const uint32_t f = nd_first[i], cnt = nd_count[i];
@@ -336,6 +345,7 @@ __global__ void __launch_bounds__(256) k_moments_level(
 // ------------------------------------------------------------- groups
 
 __global__ void __launch_bounds__(256) k_group_mark(const DevState* __restrict__ st, int n_grp,
+                                                    int n_roots,
                                                     const uint32_t* __restrict__ nd_first,
                                                     const uint32_t* __restrict__ nd_count,
                                                     const uint32_t* __restrict__ nd_meta,
@@ -346,7 +356,7 @@ __global__ void __launch_bounds__(256) k_group_mark(const DevState* __restrict__
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t c = nd_count[i];
         const bool cand = c <= (uint32_t)n_grp || meta_leaf(nd_meta[i]);
-        if (cand && (i == 0 || nd_count[nd_parent[i]] > (uint32_t)n_grp)) head[nd_first[i]] = (uint32_t)i;
+        if (cand && (i < n_roots || nd_count[nd_parent[i]] > (uint32_t)n_grp)) head[nd_first[i]] = (uint32_t)i;
     }
 }
 
@@ -423,7 +433,8 @@ __device__ __forceinline__ uint32_t quantise(double x, double lo, double s) {
 // minimum and maximum grid coordinates of the particles), FP64 centre and
 // the FP32 copies the walk's filter and the force kernel use.
 __global__ void __launch_bounds__(256) k_group_data(
-    const DevState* __restrict__ st, const uint32_t* __restrict__ g_first,
+    const DevState* __restrict__ st, const SysBox* __restrict__ box, const uint32_t* __restrict__ sys,
+    const uint32_t* __restrict__ g_first,
     const uint32_t* __restrict__ g_count, const double* __restrict__ px,
     const double* __restrict__ py, const double* __restrict__ pz, double* __restrict__ g_box,
     uint32_t* __restrict__ g_qbox, dvec4* __restrict__ g_c64, float4* __restrict__ g_ch,
@@ -432,10 +443,11 @@ __global__ void __launch_bounds__(256) k_group_data(
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t ng = st->n_groups;
-    const double lo0 = st->lo[0], lo1 = st->lo[1], lo2 = st->lo[2], s = st->s;
-    const double c0x = st->c0[0], c0y = st->c0[1], c0z = st->c0[2];
     for (int64_t g = warp; g < ng; g += nwarps) {
         const uint32_t f = g_first[g], c = g_count[g];
+        const SysBox& bx = box[sys ? sys[f] : 0];
+        const double lo0 = bx.lo[0], lo1 = bx.lo[1], lo2 = bx.lo[2], s = bx.s;
+        const double c0x = bx.c0[0], c0y = bx.c0[1], c0z = bx.c0[2];
         unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
         for (uint32_t p = f + lane; p < f + c; p += 32) {
             unsigned long long v[3] = {ord64(px[p]), ord64(py[p]), ord64(pz[p])};
@@ -486,8 +498,9 @@ int build_tree(fdps_tree* t, fdps_psys* ps) {
     fdps_ctx* ctx = t->ctx;
     cudaStream_t s = ctx->stream;
     const int G = t->box_blocks;  // partition width of the level kernels
-    k_root<<<1, 32, 0, s>>>(t->st, ps->n, t->p.n_leaf, t->nd_first, t->nd_count, t->nd_child,
-                            t->nd_meta, t->nd_parent, t->nd_qlo, t->nd_prefix);
+    k_roots<<<grid_for(ps->n_sys, 256, 64), 256, 0, s>>>(
+        t->st, ps->n_sys, ps->d_off, ps->n, t->p.n_leaf, t->nd_first, t->nd_count, t->nd_child,
+        t->nd_meta, t->nd_parent, t->nd_qlo, t->nd_prefix);
     FDPS_LAUNCH_CHECK(ctx);
     uint32_t* slot_lb = t->lvl_scratch;
     uint32_t* slot_cnt = t->lvl_scratch + 8 * t->cap_nodes;
@@ -513,12 +526,12 @@ int compute_moments(fdps_tree* t, fdps_psys* ps) {
     for (int l = kMaxLevel; l >= 0; --l) {
         if (t->p.moment == FDPS_QUADRUPOLE)
             k_moments_level<true><<<grid, 256, 0, s>>>(
-                l, t->st, ps->x[c], ps->y[c], ps->z[c], ps->m[c], t->nd_first, t->nd_count,
+                l, t->st, t->sys_box, ps->d_sys, ps->x[c], ps->y[c], ps->z[c], ps->m[c], t->nd_first, t->nd_count,
                 t->nd_child, t->nd_meta, t->nd_sx, t->nd_sy, t->nd_sz, t->nd_com, t->nd_quad,
                 t->nd_fh, t->nd_fl, t->nd_fq0, t->nd_fq1);
         else
             k_moments_level<false><<<grid, 256, 0, s>>>(
-                l, t->st, ps->x[c], ps->y[c], ps->z[c], ps->m[c], t->nd_first, t->nd_count,
+                l, t->st, t->sys_box, ps->d_sys, ps->x[c], ps->y[c], ps->z[c], ps->m[c], t->nd_first, t->nd_count,
                 t->nd_child, t->nd_meta, t->nd_sx, t->nd_sy, t->nd_sz, t->nd_com, t->nd_quad,
                 t->nd_fh, t->nd_fl, t->nd_fq0, t->nd_fq1);
         FDPS_LAUNCH_CHECK(ctx);
@@ -533,7 +546,7 @@ int select_groups(fdps_tree* t, fdps_psys* ps) {
     const int c = ps->cur;
     const int G = t->box_blocks;
     FDPS_CUDA_TRY(ctx, cudaMemsetAsync(t->head, 0xFF, sizeof(uint32_t) * (size_t)n, s));
-    k_group_mark<<<ctx->sm_count * 8, 256, 0, s>>>(t->st, t->p.n_grp, t->nd_first, t->nd_count,
+    k_group_mark<<<ctx->sm_count * 8, 256, 0, s>>>(t->st, t->p.n_grp, ps->n_sys, t->nd_first, t->nd_count,
                                                    t->nd_meta, t->nd_parent, t->head);
     FDPS_LAUNCH_CHECK(ctx);
     k_group_count<<<G, kB, 0, s>>>(n, t->head, t->grp_scan);
@@ -543,7 +556,7 @@ int select_groups(fdps_tree* t, fdps_psys* ps) {
     k_group_write<<<G, kB, 0, s>>>(n, t->cap_groups, t->head, t->grp_scan, t->nd_count, t->g_node,
                                    t->g_first, t->g_count);
     FDPS_LAUNCH_CHECK(ctx);
-    k_group_data<<<ctx->sm_count * 8, 256, 0, s>>>(t->st, t->g_first, t->g_count, ps->x[c],
+    k_group_data<<<ctx->sm_count * 8, 256, 0, s>>>(t->st, t->sys_box, ps->d_sys, t->g_first, t->g_count, ps->x[c],
                                                    ps->y[c], ps->z[c], t->g_box, t->g_qbox,
                                                    t->g_c64, t->g_ch, t->g_cl, t->g_blo, t->g_bhi);
     FDPS_LAUNCH_CHECK(ctx);

@@ -71,6 +71,15 @@ struct DevState {
     int32_t max_level;
 };
 
+// Root box of one system: lo = per-axis minimum, L = largest extent (1 if
+// 0), s = 2^21 / L, c0 = lo + L/2 (origin of the FP32 hi/lo copies).
+struct SysBox {
+    double lo[3];
+    double L;
+    double s;
+    double c0[3];
+};
+
 // Root-box reduction partials (one per block).
 struct BoxPartial {
     double lo[3];
@@ -113,6 +122,12 @@ struct fdps_psys {
     uint32_t* d_flag = nullptr;  // validation flag
     double* d_red = nullptr;     // reduction scratch (energy)
     double* stage = nullptr;     // host-transfer staging (10 n doubles, on first use)
+    // independent systems: positions off[k] .. off[k+1] belong to system k;
+    // with one system d_off and d_sys stay null
+    int32_t n_sys = 1;
+    int64_t* d_off = nullptr;
+    uint32_t* d_sys = nullptr;   // system of each position
+    double* d_sys_red = nullptr; // per-system energies (2 n_sys)
 };
 
 struct fdps_tree {
@@ -182,6 +197,8 @@ struct fdps_tree {
     fdps::DevState h_st{};          // host copy after a call
     fdps::BoxPartial* box_part = nullptr;
     int box_blocks = 0;
+    fdps::SysBox* sys_box = nullptr;  // one per system
+    int64_t cap_sys = 0;
     int64_t retries = 0;
     bool valid = false;
     // profiling
@@ -245,12 +262,15 @@ inline int grid_for(int64_t n, int block, int max_blocks) {
 // (host functions, one per .cu file; all issue work on ctx->stream)
 
 int keys_and_sort(fdps_tree* t, fdps_psys* ps);        // keys_sort.cu
+int launch_sys_index(fdps_psys* ps);                   // integrate.cu
+int launch_energy_systems(fdps_psys* ps, double* kin, double* pot);  // integrate.cu
 int reorder_particles(fdps_tree* t, fdps_psys* ps);    // keys_sort.cu
 int build_tree(fdps_tree* t, fdps_psys* ps);           // build.cu
 int compute_moments(fdps_tree* t, fdps_psys* ps);      // build.cu
 int select_groups(fdps_tree* t, fdps_psys* ps);        // build.cu
 int compute_forces(fdps_tree* t, fdps_psys* ps, int spj_kind);  // force.cu
 int launch_kick(fdps_psys* ps, double dt_half);        // integrate.cu
+int launch_kick_guarded(fdps_psys* ps, double dt_half, const uint32_t* flags, uint32_t mask);
 int launch_drift(fdps_psys* ps, double dt);            // integrate.cu
 int launch_energy(fdps_psys* ps, double* kin, double* pot);  // integrate.cu
 int launch_validate(fdps_psys* ps, uint32_t* bad);     // integrate.cu

@@ -2,6 +2,8 @@
 // leapfrog of the paper's N-body example (Sect. 2.2: predict = kick by dt/2
 // then drift by dt; correct = kick by dt/2), all in FP64 on the current
 // (key-sorted) particle order.
+#include <stdlib.h>
+
 #include "fdps_internal.cuh"
 
 namespace fdps {
@@ -154,7 +156,104 @@ __global__ void k_energy_final(int nb, double* part) {
 
 constexpr int kEnergyBlocks = 512;
 
+__global__ void __launch_bounds__(256) k_sys_index(const int64_t* __restrict__ off, uint32_t* sys) {
+    const int64_t a = off[blockIdx.x], b = off[blockIdx.x + 1];
+    for (int64_t i = a + threadIdx.x; i < b; i += blockDim.x) sys[i] = blockIdx.x;
+}
+
+// Kinetic and potential energy of each system: one block per system.
+__global__ void __launch_bounds__(256) k_energy_seg(const int64_t* __restrict__ off,
+                                                    const double* __restrict__ vx,
+                                                    const double* __restrict__ vy,
+                                                    const double* __restrict__ vz,
+                                                    const double* __restrict__ m,
+                                                    const double* __restrict__ phi, double* out) {
+    const int64_t a = off[blockIdx.x], b = off[blockIdx.x + 1];
+    double ek = 0.0, ep = 0.0;
+    for (int64_t i = a + threadIdx.x; i < b; i += blockDim.x) {
+        ek += 0.5 * m[i] * (vx[i] * vx[i] + vy[i] * vy[i] + vz[i] * vz[i]);
+        ep += 0.5 * m[i] * phi[i];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ek += __shfl_xor_sync(0xFFFFFFFFu, ek, o);
+        ep += __shfl_xor_sync(0xFFFFFFFFu, ep, o);
+    }
+    __shared__ double s[2][8];
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        s[0][w] = ek;
+        s[1][w] = ep;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double x = 0.0, y = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            x += s[0][k];
+            y += s[1][k];
+        }
+        out[2 * blockIdx.x] = x;
+        out[2 * blockIdx.x + 1] = y;
+    }
+}
+
+// The second kick of a captured step; skipped when that step's force
+// calculation overflowed a buffer (the host then redoes the force and kick).
+__global__ void __launch_bounds__(256) k_kick_guarded(int64_t n, double h, double* vx, double* vy,
+                                                      double* vz, const double* __restrict__ ax,
+                                                      const double* __restrict__ ay,
+                                                      const double* __restrict__ az,
+                                                      const uint32_t* __restrict__ flags,
+                                                      uint32_t mask) {
+    if (*flags & mask) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        vx[i] += h * ax[i];
+        vy[i] += h * ay[i];
+        vz[i] += h * az[i];
+    }
+}
+
 }  // namespace
+
+int launch_kick_guarded(fdps_psys* ps, double dt_half, const uint32_t* flags, uint32_t mask) {
+    fdps_ctx* ctx = ps->ctx;
+    const int c = ps->cur;
+    k_kick_guarded<<<grid_for(ps->n, 256, ctx->sm_count * 16), 256, 0, ctx->stream>>>(
+        ps->n, dt_half, ps->vx[c], ps->vy[c], ps->vz[c], ps->ax, ps->ay, ps->az, flags, mask);
+    FDPS_LAUNCH_CHECK(ctx);
+    return FDPS_OK;
+}
+
+int launch_sys_index(fdps_psys* ps) {
+    fdps_ctx* ctx = ps->ctx;
+    k_sys_index<<<ps->n_sys, 256, 0, ctx->stream>>>(ps->d_off, ps->d_sys);
+    FDPS_LAUNCH_CHECK(ctx);
+    return FDPS_OK;
+}
+
+int launch_energy_systems(fdps_psys* ps, double* kin, double* pot) {
+    fdps_ctx* ctx = ps->ctx;
+    const int c = ps->cur;
+    const int64_t S = ps->n_sys;
+    if (ps->n_sys == 1) return launch_energy(ps, kin, pot);
+    k_energy_seg<<<ps->n_sys, 256, 0, ctx->stream>>>(ps->d_off, ps->vx[c], ps->vy[c], ps->vz[c],
+                                                    ps->m[c], ps->pot, ps->d_sys_red);
+    FDPS_LAUNCH_CHECK(ctx);
+    double* h = (double*)malloc(sizeof(double) * 2 * S);
+    if (!h) return set_error(ctx, FDPS_ENOMEM, "host allocation failed");
+    cudaError_t e = cudaMemcpyAsync(h, ps->d_sys_red, sizeof(double) * 2 * S, cudaMemcpyDeviceToHost,
+                                    ctx->stream);
+    if (!e) e = cudaStreamSynchronize(ctx->stream);
+    if (!e)
+        for (int64_t k = 0; k < S; ++k) {
+            kin[k] = h[2 * k];
+            pot[k] = h[2 * k + 1];
+        }
+    free(h);
+    if (e) return set_error(ctx, FDPS_ECUDA, "energy readback failed: %s", cudaGetErrorString(e));
+    return FDPS_OK;
+}
 
 int energy_scratch_doubles() { return 2 * kEnergyBlocks + 2; }
 

@@ -78,7 +78,8 @@ __global__ void __launch_bounds__(256) k_box_partial(int64_t n, const double* __
     }
 }
 
-__global__ void k_box_final(int nparts, const BoxPartial* __restrict__ part, DevState* st) {
+__global__ void k_box_final(int nparts, const BoxPartial* __restrict__ part, DevState* st,
+                            SysBox* box) {
     if (threadIdx.x != 0) return;
     unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
     for (int b = 0; b < nparts; ++b)
@@ -99,6 +100,69 @@ __global__ void k_box_final(int nparts, const BoxPartial* __restrict__ part, Dev
     st->L = L;
     st->s = __ddiv_rn(2097152.0, L);
     for (int a = 0; a < 3; ++a) st->c0[a] = __dadd_rn(st->lo[a], __dmul_rn(0.5, L));
+    for (int a = 0; a < 3; ++a) {
+        box->lo[a] = st->lo[a];
+        box->c0[a] = st->c0[a];
+    }
+    box->L = st->L;
+    box->s = st->s;
+}
+
+// Root boxes of independent systems: one block per system (positions
+// off[k] .. off[k+1]), the same definitions as for a single system.
+__global__ void __launch_bounds__(256) k_box_seg(const int64_t* __restrict__ off,
+                                                 const double* __restrict__ x,
+                                                 const double* __restrict__ y,
+                                                 const double* __restrict__ z,
+                                                 SysBox* __restrict__ box) {
+    const int64_t a0 = off[blockIdx.x], a1 = off[blockIdx.x + 1];
+    unsigned long long lo[3] = {~0ull, ~0ull, ~0ull};
+    unsigned long long hi[3] = {0ull, 0ull, 0ull};
+    for (int64_t i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
+        unsigned long long v[3] = {ord64(x[i]), ord64(y[i]), ord64(z[i])};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = v[a] < lo[a] ? v[a] : lo[a];
+            hi[a] = v[a] > hi[a] ? v[a] : hi[a];
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            unsigned long long l = __shfl_xor_sync(0xFFFFFFFFu, lo[a], o);
+            unsigned long long h = __shfl_xor_sync(0xFFFFFFFFu, hi[a], o);
+            lo[a] = l < lo[a] ? l : lo[a];
+            hi[a] = h > hi[a] ? h : hi[a];
+        }
+    __shared__ unsigned long long s_lo[8][3], s_hi[8][3];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+        for (int a = 0; a < 3; ++a) {
+            s_lo[w][a] = lo[a];
+            s_hi[w][a] = hi[a];
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double L = 0.0, l3[3];
+        for (int a = 0; a < 3; ++a) {
+            unsigned long long l = s_lo[0][a], h = s_hi[0][a];
+            for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+                l = s_lo[k][a] < l ? s_lo[k][a] : l;
+                h = s_hi[k][a] > h ? s_hi[k][a] : h;
+            }
+            l3[a] = unord64(l);
+            const double e = __dsub_rn(unord64(h), l3[a]);
+            L = e > L ? e : L;
+        }
+        if (L == 0.0) L = 1.0;
+        SysBox b;
+        for (int a = 0; a < 3; ++a) b.lo[a] = l3[a];
+        b.L = L;
+        b.s = __ddiv_rn(2097152.0, L);
+        for (int a = 0; a < 3; ++a) b.c0[a] = __dadd_rn(l3[a], __dmul_rn(0.5, L));
+        box[blockIdx.x] = b;
+    }
 }
 
 __device__ __forceinline__ uint32_t quantise(double x, double lo, double s) {
@@ -126,21 +190,22 @@ __device__ __forceinline__ uint64_t spread3(uint32_t v) {
 __global__ void __launch_bounds__(kSortBlock) k_keys(int64_t n, const double* __restrict__ x,
                                                      const double* __restrict__ y,
                                                      const double* __restrict__ z,
-                                                     const DevState* __restrict__ st,
+                                                     const SysBox* __restrict__ box,
+                                                     const uint32_t* __restrict__ sys,
                                                      uint64_t* __restrict__ keys,
                                                      uint32_t* __restrict__ hist, int ntiles) {
     __shared__ uint32_t h[kSortWarps][kRadix];
     for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortBlock) (&h[0][0])[i] = 0;
     __syncthreads();
-    const double lo0 = st->lo[0], lo1 = st->lo[1], lo2 = st->lo[2], s = st->s;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t base = (int64_t)blockIdx.x * kSortTile + w * (32 * kSortKPT);
 #pragma unroll
     for (int r = 0; r < kSortKPT; ++r) {
         int64_t i = base + r * 32 + lane;
         if (i < n) {
-            uint32_t qx = quantise(x[i], lo0, s), qy = quantise(y[i], lo1, s),
-                     qz = quantise(z[i], lo2, s);
+            const SysBox& b = box[sys ? sys[i] : 0];
+            uint32_t qx = quantise(x[i], b.lo[0], b.s), qy = quantise(y[i], b.lo[1], b.s),
+                     qz = quantise(z[i], b.lo[2], b.s);
             uint64_t k = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
             keys[i] = k;
             atomicAdd(&h[w][k & 0xFF], 1u);
@@ -165,6 +230,28 @@ __global__ void __launch_bounds__(kSortBlock) k_radix_hist(int64_t n, const uint
     for (int r = 0; r < kSortKPT; ++r) {
         int64_t i = base + r * 32 + lane;
         if (i < n) atomicAdd(&h[w][(keys[i] >> shift) & 0xFF], 1u);
+    }
+    __syncthreads();
+    uint32_t c = 0;
+#pragma unroll
+    for (int k = 0; k < kSortWarps; ++k) c += h[k][threadIdx.x];
+    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = c;
+}
+
+// Tile histograms of the digit `shift` of the system id of each pair's
+// particle (the passes that make the sort segmented by system).
+__global__ void __launch_bounds__(kSortBlock) k_radix_hist_sys(int64_t n, const uint32_t* __restrict__ vals,
+                                                               const uint32_t* __restrict__ sys, int shift,
+                                                               uint32_t* __restrict__ hist, int ntiles) {
+    __shared__ uint32_t h[kSortWarps][kRadix];
+    for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortBlock) (&h[0][0])[i] = 0;
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t base = (int64_t)blockIdx.x * kSortTile + w * (32 * kSortKPT);
+#pragma unroll
+    for (int r = 0; r < kSortKPT; ++r) {
+        int64_t i = base + r * 32 + lane;
+        if (i < n) atomicAdd(&h[w][(sys[vals[i]] >> shift) & 0xFF], 1u);
     }
     __syncthreads();
     uint32_t c = 0;
@@ -236,9 +323,11 @@ __global__ void __launch_bounds__(kRadix) k_radix_scan_digits(uint32_t* __restri
 __global__ void __launch_bounds__(kSortBlock) k_radix_scatter(
     int64_t n, const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
     uint64_t* __restrict__ kout, uint32_t* __restrict__ vout, int shift,
-    const uint32_t* __restrict__ hist, const uint32_t* __restrict__ dbase, int ntiles) {
+    const uint32_t* __restrict__ hist, const uint32_t* __restrict__ dbase, int ntiles,
+    const uint32_t* __restrict__ sys = nullptr) {
     __shared__ uint64_t sk[kSortTile];
     __shared__ uint32_t sv[kSortTile];
+    __shared__ uint8_t sd[kSortTile];
     __shared__ uint32_t wcnt[kSortWarps][kRadix];
     __shared__ uint32_t tstart[kRadix];
     __shared__ uint32_t gbase[kRadix];
@@ -249,14 +338,14 @@ __global__ void __launch_bounds__(kSortBlock) k_radix_scatter(
     const int64_t tile0 = (int64_t)blockIdx.x * kSortTile;
     const int64_t base = tile0 + w * (32 * kSortKPT);
     uint64_t mk[kSortKPT];
-    uint32_t mv[kSortKPT], mr[kSortKPT];
+    uint32_t mv[kSortKPT], mr[kSortKPT], md[kSortKPT];
 #pragma unroll
     for (int r = 0; r < kSortKPT; ++r) {
         int64_t i = base + r * 32 + lane;
         bool valid = i < n;
         uint64_t k = valid ? kin[i] : 0ull;
         uint32_t v = valid ? (vin ? vin[i] : (uint32_t)i) : 0u;
-        uint32_t d = (uint32_t)(k >> shift) & 0xFFu;
+        uint32_t d = sys ? (valid ? (sys[v] >> shift) & 0xFFu : 0u) : (uint32_t)(k >> shift) & 0xFFu;
         uint32_t vmask = __ballot_sync(0xFFFFFFFFu, valid);
         uint32_t rank = 0, before = 0, peers = 0;
         if (valid) {
@@ -270,6 +359,7 @@ __global__ void __launch_bounds__(kSortBlock) k_radix_scatter(
         mk[r] = k;
         mv[r] = v;
         mr[r] = before + rank;
+        md[r] = d;
     }
     __syncthreads();
     {
@@ -290,10 +380,11 @@ __global__ void __launch_bounds__(kSortBlock) k_radix_scatter(
     for (int r = 0; r < kSortKPT; ++r) {
         int64_t i = base + r * 32 + lane;
         if (i < n) {
-            uint32_t d = (uint32_t)(mk[r] >> shift) & 0xFFu;
+            const uint32_t d = md[r];
             uint32_t p = tstart[d] + wcnt[w][d] + mr[r];
             sk[p] = mk[r];
             sv[p] = mv[r];
+            sd[p] = (uint8_t)md[r];
         }
     }
     __syncthreads();
@@ -301,7 +392,7 @@ __global__ void __launch_bounds__(kSortBlock) k_radix_scatter(
     const int cnt = rem < kSortTile ? (int)rem : kSortTile;
     for (int p = threadIdx.x; p < cnt; p += kSortBlock) {
         uint64_t k = sk[p];
-        uint32_t d = (uint32_t)(k >> shift) & 0xFFu;
+        const uint32_t d = sd[p];
         uint32_t dst = gbase[d] + (uint32_t)p - tstart[d];
         kout[dst] = k;
         vout[dst] = sv[p];
@@ -311,7 +402,8 @@ __global__ void __launch_bounds__(kSortBlock) k_radix_scatter(
 // Reorder the particle system into key order and write the FP32 hi/lo
 // copies relative to the root centre used by the walk and force kernels.
 __global__ void __launch_bounds__(256) k_reorder(
-    int64_t n, const uint32_t* __restrict__ perm, const DevState* __restrict__ st,
+    int64_t n, const uint32_t* __restrict__ perm, const SysBox* __restrict__ box,
+    const uint32_t* __restrict__ sys,
     const double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ z,
     const double* __restrict__ vx, const double* __restrict__ vy, const double* __restrict__ vz,
     const double* __restrict__ m, const double* __restrict__ eps, const uint32_t* __restrict__ id,
@@ -319,9 +411,10 @@ __global__ void __launch_bounds__(256) k_reorder(
     double* __restrict__ vx2, double* __restrict__ vy2, double* __restrict__ vz2,
     double* __restrict__ m2, double* __restrict__ eps2, uint32_t* __restrict__ id2,
     float4* __restrict__ pf_hi, float4* __restrict__ pf_lo) {
-    const double c0 = st->c0[0], c1 = st->c0[1], c2 = st->c0[2];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
+        const SysBox& b = box[sys ? sys[i] : 0];
+        const double c0 = b.c0[0], c1 = b.c0[1], c2 = b.c0[2];
         uint32_t s = perm[i];
         double px = x[s], py = y[s], pz = z[s], pm = m[s], pe = eps[s];
         x2[i] = px;
@@ -350,22 +443,34 @@ int keys_and_sort(fdps_tree* t, fdps_psys* ps) {
     const int64_t n = ps->n;
     const int c = ps->cur;
     const int ntiles = (int)((n + kSortTile - 1) / kSortTile);
-    k_box_partial<<<t->box_blocks, 256, 0, s>>>(n, ps->x[c], ps->y[c], ps->z[c], t->box_part);
-    FDPS_LAUNCH_CHECK(ctx);
-    k_box_final<<<1, 32, 0, s>>>(t->box_blocks, t->box_part, t->st);
-    FDPS_LAUNCH_CHECK(ctx);
-    k_keys<<<ntiles, kSortBlock, 0, s>>>(n, ps->x[c], ps->y[c], ps->z[c], t->st, t->keys_in,
-                                         t->sort_hist, ntiles);
+    if (ps->n_sys == 1) {
+        k_box_partial<<<t->box_blocks, 256, 0, s>>>(n, ps->x[c], ps->y[c], ps->z[c], t->box_part);
+        FDPS_LAUNCH_CHECK(ctx);
+        k_box_final<<<1, 32, 0, s>>>(t->box_blocks, t->box_part, t->st, t->sys_box);
+        FDPS_LAUNCH_CHECK(ctx);
+    } else {
+        k_box_seg<<<ps->n_sys, 256, 0, s>>>(ps->d_off, ps->x[c], ps->y[c], ps->z[c], t->sys_box);
+        FDPS_LAUNCH_CHECK(ctx);
+    }
+    k_keys<<<ntiles, kSortBlock, 0, s>>>(n, ps->x[c], ps->y[c], ps->z[c], t->sys_box, ps->d_sys,
+                                         t->keys_in, t->sort_hist, ntiles);
     FDPS_LAUNCH_CHECK(ctx);
     if (t->ev_ok && ctx->profiling) cudaEventRecord(t->ev[1], s);
     const uint64_t* kin = t->keys_in;
     const uint32_t* vin = nullptr;
     uint64_t* kb[2] = {t->keys_a, t->keys_b};
     uint32_t* vb[2] = {t->vals_a, t->vals_b};
-    for (int pass = 0; pass < 8; ++pass) {
-        const int shift = 8 * pass;
+    // 8 passes over the key; with several systems 2 more, stable, over the
+    // system id, so each system's particles end in its own segment in key order
+    const int npass = ps->n_sys == 1 ? 8 : 10;
+    for (int pass = 0; pass < npass; ++pass) {
+        const bool by_sys = pass >= 8;
+        const int shift = by_sys ? 8 * (pass - 8) : 8 * pass;
         if (pass > 0) {
-            k_radix_hist<<<ntiles, kSortBlock, 0, s>>>(n, kin, shift, t->sort_hist, ntiles);
+            if (by_sys)
+                k_radix_hist_sys<<<ntiles, kSortBlock, 0, s>>>(n, vin, ps->d_sys, shift, t->sort_hist, ntiles);
+            else
+                k_radix_hist<<<ntiles, kSortBlock, 0, s>>>(n, kin, shift, t->sort_hist, ntiles);
             FDPS_LAUNCH_CHECK(ctx);
         }
         k_radix_scan_rows<<<kRadix, 1024, 0, s>>>(t->sort_hist, ntiles, t->sort_dtot);
@@ -375,7 +480,7 @@ int keys_and_sort(fdps_tree* t, fdps_psys* ps) {
         uint64_t* ko = kb[pass & 1];
         uint32_t* vo = vb[pass & 1];
         k_radix_scatter<<<ntiles, kSortBlock, 0, s>>>(n, kin, vin, ko, vo, shift, t->sort_hist,
-                                                      t->sort_dtot, ntiles);
+                                                      t->sort_dtot, ntiles, by_sys ? ps->d_sys : nullptr);
         FDPS_LAUNCH_CHECK(ctx);
         kin = ko;
         vin = vo;
@@ -391,7 +496,7 @@ int reorder_particles(fdps_tree* t, fdps_psys* ps) {
     const int64_t n = ps->n;
     int grid = grid_for(n, 256, ctx->sm_count * 16);
     k_reorder<<<grid, 256, 0, ctx->stream>>>(
-        n, t->perm, t->st, ps->x[c], ps->y[c], ps->z[c], ps->vx[c], ps->vy[c], ps->vz[c],
+        n, t->perm, t->sys_box, ps->d_sys, ps->x[c], ps->y[c], ps->z[c], ps->vx[c], ps->vy[c], ps->vz[c],
         ps->m[c], ps->eps[c], ps->id[c], ps->x[o], ps->y[o], ps->z[o], ps->vx[o], ps->vy[o],
         ps->vz[o], ps->m[o], ps->eps[o], ps->id[o], t->pf_hi, t->pf_lo);
     FDPS_LAUNCH_CHECK(ctx);
@@ -417,7 +522,8 @@ constexpr int64_t kNoAllocTiles = kNoAllocMaxN / kSortTile;
 
 constexpr size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 constexpr size_t kOffState = 0;
-constexpr size_t kOffBox = align256(kOffState + sizeof(DevState));
+constexpr size_t kOffSysBox = align256(kOffState + sizeof(DevState));
+constexpr size_t kOffBox = align256(kOffSysBox + sizeof(SysBox));
 constexpr size_t kOffHist = align256(kOffBox + sizeof(BoxPartial) * kNoAllocBoxBlocks);
 constexpr size_t kOffDtot = align256(kOffHist + sizeof(uint32_t) * kRadix * kNoAllocTiles);
 constexpr size_t kOffKeysIn = align256(kOffDtot + sizeof(uint32_t) * kRadix);
@@ -457,6 +563,7 @@ extern "C" int fdps_morton_sort_noalloc(const double* x, const double* y, const 
     }
     unsigned char* base = g_noalloc_ptr[dev];
     DevState* st = reinterpret_cast<DevState*>(base + kOffState);
+    SysBox* sbox = reinterpret_cast<SysBox*>(base + kOffSysBox);
     BoxPartial* box = reinterpret_cast<BoxPartial*>(base + kOffBox);
     uint32_t* hist = reinterpret_cast<uint32_t*>(base + kOffHist);
     uint32_t* dtot = reinterpret_cast<uint32_t*>(base + kOffDtot);
@@ -472,8 +579,8 @@ extern "C" int fdps_morton_sort_noalloc(const double* x, const double* y, const 
         return FDPS_ECUDA;
     }
     k_box_partial<<<kNoAllocBoxBlocks, 256, 0, s>>>(n, x, y, z, box);
-    k_box_final<<<1, 32, 0, s>>>(kNoAllocBoxBlocks, box, st);
-    k_keys<<<ntiles, kSortBlock, 0, s>>>(n, x, y, z, st, keys_in, hist, ntiles);
+    k_box_final<<<1, 32, 0, s>>>(kNoAllocBoxBlocks, box, st, sbox);
+    k_keys<<<ntiles, kSortBlock, 0, s>>>(n, x, y, z, sbox, nullptr, keys_in, hist, ntiles);
     const uint64_t* kin = keys_in;
     const uint32_t* vin = nullptr;
     for (int pass = 0; pass < 8; ++pass) {

@@ -37,6 +37,9 @@ struct WalkArgs {
     const float4* nd_fl;
     const dvec4* nd_com;
     const uint32_t* g_count;
+    const uint32_t* g_first;
+    const uint32_t* sys;  // system of each particle position (null: one system)
+    const SysBox* box;    // root box of each system
     const uint32_t* g_qbox;
     const double* g_box;
     const float4* g_ch;
@@ -82,12 +85,7 @@ __device__ __noinline__ bool open_fp64(double L, int level, double theta2, const
 }
 
 __global__ void __launch_bounds__(kWalkBlock) k_walk(WalkArgs A) {
-    __shared__ float s_ell[kMaxLevel + 1];
     DevState* st = A.st;
-    const double L = st->L;
-    if (threadIdx.x <= kMaxLevel) s_ell[threadIdx.x] = __double2float_rn(ldexp(L, -(int)threadIdx.x));
-    __syncthreads();
-    const float Lf = __double2float_rn(L);
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -108,6 +106,10 @@ __global__ void __launch_bounds__(kWalkBlock) k_walk(WalkArgs A) {
         g = __shfl_sync(0xFFFFFFFFu, g, 0);
         if (g >= ngroups) break;
 
+        // the group's system: its root node (node id = system index) and box
+        const uint32_t sysid = A.sys ? A.sys[A.g_first[g]] : 0u;
+        const double L = A.box[sysid].L;
+        const float Lf = __double2float_rn(L);
         const uint32_t* qb = A.g_qbox + 6 * (int64_t)g;
         const uint32_t qmin0 = qb[0], qmin1 = qb[1], qmin2 = qb[2];
         const uint32_t qmax0 = qb[3], qmax1 = qb[4], qmax2 = qb[5];
@@ -119,7 +121,7 @@ __global__ void __launch_bounds__(kWalkBlock) k_walk(WalkArgs A) {
         unsigned long long gstart = cursor;
         uint32_t nspj = 0, nepj = 0;
         uint32_t fsize = 1;
-        if (lane == 0) fa[0] = 0u;
+        if (lane == 0) fa[0] = sysid;
         __syncwarp();
         while (fsize > 0) {
             uint32_t nsize = 0;
@@ -151,7 +153,7 @@ __global__ void __launch_bounds__(kWalkBlock) k_walk(WalkArgs A) {
                         const float ty = fmaxf(fmaxf(blo.y - dy, dy - bhi.y), 0.0f);
                         const float tz = fmaxf(fmaxf(blo.z - dz, dz - bhi.z), 0.0f);
                         const float d2 = tx * tx + ty * ty + tz * tz;
-                        const float ell = s_ell[level];
+                        const float ell = scalbnf(Lf, -level);  // exact: L 2^-level in FP32
                         const float l2 = ell * ell;
                         const float r2 = A.theta2f * d2;
                         const float T = l2 - r2;
@@ -284,7 +286,7 @@ int walk_warps_per_block() { return kWalkBlock / 32; }
 
 unsigned long long walk_chunk() { return kChunk; }
 
-int launch_walk(fdps_tree* t, int blocks) {
+int launch_walk(fdps_tree* t, const uint32_t* sys, int blocks) {
     fdps_ctx* ctx = t->ctx;
     WalkArgs A;
     A.st = t->st;
@@ -296,6 +298,9 @@ int launch_walk(fdps_tree* t, int blocks) {
     A.nd_fl = t->nd_fl;
     A.nd_com = t->nd_com;
     A.g_count = t->g_count;
+    A.g_first = t->g_first;
+    A.sys = sys;
+    A.box = t->sys_box;
     A.g_qbox = t->g_qbox;
     A.g_box = t->g_box;
     A.g_ch = t->g_ch;
