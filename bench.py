@@ -56,6 +56,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ensemble", action="store_true",
+                    help="the ensemble workload: 4096 Plummer clusters, N log-uniform in "
+                         "[256, 65536], eps = 1/(4 N^1/3), theta 0.5 monopole, dt 1/256")
+    ap.add_argument("--n-sys", type=int, default=4096)
     return ap.parse_args()
 
 
@@ -331,6 +335,81 @@ def run_ours(args, rank, world, local_rank):
     ctx.close()
 
 
+def run_ensemble(args):
+    """Systems-steps/s of the ensemble stepped by graph-captured runs, with
+    per-system energy drift, beside one step of the all-FP64 pipeline."""
+    import torch
+    import ics
+    import paper_1601_03138_gb300 as G
+    from paper_1601_03138_gb300 import build as B
+    B.build()
+    cfg = ics.CONFIGS["ensemble4096"]
+    pos, vel, mass, eps, off = ics.ensemble(args.n_sys, cfg["seed"])
+    n = len(pos)
+    dt = cfg["dt"]
+    ctx = G.Context(0)
+    ctx.set_profiling(True)
+    stream = torch.cuda.ExternalStream(ctx.stream)
+    ps = G.ParticleSystem(ctx, n)
+    tree = G.Tree(ctx, theta=cfg["theta"], n_leaf=args.n_leaf if args.n_leaf != 16 else cfg["n_leaf"],
+                  n_grp=args.n_grp if args.n_grp != 128 else cfg["n_grp"])
+    ps.set_systems(off)
+    ps.set(pos, vel, mass, eps)
+    tree.calc_force_all_and_write_back(ps)
+    ek0, ep0 = ps.energy_systems()
+    tree.run(ps, dt, args.warmup)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = ctx.launches
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    tree.run(ps, dt, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = ctx.launches - l0
+    t = e0.elapsed_time(e1) / 1e3
+    st = tree.stats()
+    ek1, ep1 = ps.energy_systems()
+    E0, E1 = ek0 + ep0, ek1 + ep1
+    drift = np.abs((E1 - E0) / E0)
+    fp64 = None
+    if not args.no_fp64:
+        ps3 = G.ParticleSystem(ctx, n)
+        t64 = G.Tree(ctx, theta=cfg["theta"], n_leaf=cfg["n_leaf"], n_grp=cfg["n_grp"], fp64=True)
+        ps3.set_systems(off)
+        ps3.set(pos, vel, mass, eps)
+        t64.calc_force_all_and_write_back(ps3)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        t64.step(ps3, dt)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = a0.elapsed_time(a1)
+        fp64 = {"ms_per_step": ms64, "value": args.n_sys / (ms64 / 1e3), "steps": 1}
+        t64.close()
+        ps3.close()
+    inter = st["interactions_epj"] + st["interactions_spj"]
+    line = {"metric": "systems-steps/s", "value": args.n_sys * args.steps / t, "unit": "systems*steps/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"ensemble of {args.n_sys} Plummer clusters, N log-uniform "
+                                   f"[256, 65536] (total {n}), theta {cfg['theta']} monopole, "
+                                   f"n_leaf {cfg['n_leaf']}, n_grp {cfg['n_grp']}, dt {dt}, "
+                                   "graph-captured steps", "l2": "inputs larger than L2"},
+            "gpu_launches": launches, "clocks": clk,
+            "interactions_per_s_estimate": inter * args.steps / t,
+            "energy_drift": {"median": float(np.median(drift)), "p99": float(np.quantile(drift, 0.99)),
+                             "max": float(drift.max()), "steps": args.warmup + args.steps},
+            "fp64_variant": fp64, "stages_ms_last_step": {k: v for k, v in st.items() if k.startswith("ms_")}}
+    print(json.dumps(line), flush=True)
+    tree.close()
+    ps.close()
+    ctx.close()
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -338,6 +417,10 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.ensemble:
+        if rank == 0:
+            run_ensemble(args)
         return
     if world > 1:
         import torch

@@ -70,8 +70,8 @@ void free_nodes(fdps_tree* t) {
     dev_free(t->nd_sz);
     dev_free(t->nd_com);
     dev_free(t->nd_quad);
-    dev_free(t->nd_fh);
-    dev_free(t->nd_fl);
+    dev_free(t->nd_f);
+    dev_free(t->nd_walk);
     dev_free(t->nd_fq0);
     dev_free(t->nd_fq1);
     dev_free(t->lvl_scratch);
@@ -87,7 +87,7 @@ int ensure_nodes(fdps_tree* t, int64_t cap) {
               dev_alloc(&t->nd_prefix, cap) == cudaSuccess && dev_alloc(&t->nd_sx, cap) == cudaSuccess &&
               dev_alloc(&t->nd_sy, cap) == cudaSuccess && dev_alloc(&t->nd_sz, cap) == cudaSuccess &&
               dev_alloc(&t->nd_com, cap) == cudaSuccess && dev_alloc(&t->nd_quad, 6 * cap) == cudaSuccess &&
-              dev_alloc(&t->nd_fh, cap) == cudaSuccess && dev_alloc(&t->nd_fl, cap) == cudaSuccess &&
+              dev_alloc(&t->nd_f, 2 * cap) == cudaSuccess && dev_alloc(&t->nd_walk, cap) == cudaSuccess &&
               dev_alloc(&t->nd_fq0, cap) == cudaSuccess && dev_alloc(&t->nd_fq1, cap) == cudaSuccess &&
               dev_alloc(&t->lvl_scratch, 16 * cap) == cudaSuccess;
     if (!ok) {
@@ -187,10 +187,8 @@ __global__ void k_reset_counters(DevState* st, int what) {
     if (what & 4) st->overflow &= ~(kOvfNodes | kOvfGroups);
 }
 
-bool g_capturing = false;  // set while fdps_run captures a step
-
 void record(fdps_tree* t, int k) {
-    if (t->ev_ok && t->ctx->profiling && !g_capturing) cudaEventRecord(t->ev[k], t->ctx->stream);
+    if (t->ev_ok && t->ctx->profiling && !t->ctx->capturing) cudaEventRecord(t->ev[k], t->ctx->stream);
 }
 
 int ensure_systems(fdps_tree* t, int64_t n_sys) {
@@ -867,17 +865,21 @@ int fdps_run(fdps_tree* t, fdps_psys* ps, double dt, int64_t n_steps) {
     // the particle buffers flip in every force calculation, so a step reads
     // buffer `cur` and leaves buffer 1 - cur: one graph for each parity
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    int64_t kernels[2] = {0, 0};  // kernel launches recorded in each graph
     for (int64_t k = 1; k < n_steps && !rc; ++k) {
         const int par = ps->cur;
         if (!exec[par]) {
             cudaGraph_t graph = nullptr;
             FDPS_CUDA_TRY(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-            g_capturing = true;
+            ctx->capturing = true;
+            const int64_t l0 = ctx->launches;
             rc = launch_kick(ps, 0.5 * dt);
             if (!rc) rc = launch_drift(ps, dt);
             if (!rc) rc = launch_force_pipeline(t, ps, k_spj);
             if (!rc) rc = launch_kick_guarded(ps, 0.5 * dt, &t->st->overflow, ovf_mask);
-            g_capturing = false;
+            ctx->capturing = false;
+            kernels[par] = ctx->launches - l0;
+            ctx->launches = l0;  // recorded, not launched; counted per replay
             ps->cur = par;  // capture only records; the flip happens on replay
             cudaError_t e = cudaStreamEndCapture(s, &graph);
             if (!rc && e != cudaSuccess)
@@ -892,6 +894,7 @@ int fdps_run(fdps_tree* t, fdps_psys* ps, double dt, int64_t n_steps) {
             if (rc) break;
         }
         cudaError_t e = cudaGraphLaunch(exec[par], s);
+        ctx->launches += kernels[par];
         uint32_t ov = 0;
         if (!e) e = cudaMemcpyAsync(&ov, &t->st->overflow, sizeof(ov), cudaMemcpyDeviceToHost, s);
         if (!e) e = cudaStreamSynchronize(s);

@@ -260,9 +260,10 @@ __global__ void __launch_bounds__(256) k_moments_level(
     const double* __restrict__ py, const double* __restrict__ pz, const double* __restrict__ pm,
     const uint32_t* __restrict__ nd_first, const uint32_t* __restrict__ nd_count,
     const uint32_t* __restrict__ nd_child, const uint32_t* __restrict__ nd_meta,
-    double* __restrict__ nd_sx, double* __restrict__ nd_sy, double* __restrict__ nd_sz,
-    dvec4* __restrict__ nd_com, double* __restrict__ nd_quad, float4* __restrict__ nd_fh,
-    float4* __restrict__ nd_fl, float4* __restrict__ nd_fq0, float2* __restrict__ nd_fq1) {
+    const uint64_t* __restrict__ nd_qlo, double* __restrict__ nd_sx, double* __restrict__ nd_sy,
+    double* __restrict__ nd_sz, dvec4* __restrict__ nd_com, double* __restrict__ nd_quad,
+    float4* __restrict__ nd_f, uint4* __restrict__ nd_walk, float4* __restrict__ nd_fq0,
+    float2* __restrict__ nd_fq1) {
     const int64_t a = st->lvl_start[l], b = st->lvl_start[l + 1];
     for (int64_t i = a + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < b;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -303,8 +304,10 @@ __global__ void __launch_bounds__(256) k_moments_level(
         split_hilo(cx - c0x, &hx, &lx);
         split_hilo(cy - c0y, &hy, &ly);
         split_hilo(cz - c0z, &hz, &lz);
-        nd_fh[i] = make_float4(hx, hy, hz, __double2float_rn(M));
-        nd_fl[i] = make_float4(lx, ly, lz, 0.0f);
+        nd_f[2 * i] = make_float4(hx, hy, hz, __double2float_rn(M));
+        nd_f[2 * i + 1] = make_float4(lx, ly, lz, 0.0f);
+        const uint64_t q = nd_qlo[i];
+        nd_walk[i] = make_uint4((uint32_t)q, (uint32_t)(q >> 32), c0, meta);
         if (QUAD) {
             double q[6] = {0, 0, 0, 0, 0, 0};
             if (leaf) {
@@ -428,10 +431,12 @@ __device__ __forceinline__ uint32_t quantise(double x, double lo, double s) {
     return (uint32_t)f;
 }
 
-// One warp per group: FP64 box (min / max over the particles), its grid
-// box (the quantised corners: quantisation is monotone, so these are the
-// minimum and maximum grid coordinates of the particles), FP64 centre and
-// the FP32 copies the walk's filter and the force kernel use.
+// FP64 box of each group (min / max over its particles), its grid box (the
+// quantised corners: quantisation is monotone, so these are the minimum and
+// maximum grid coordinates of the particles), FP64 centre and the FP32
+// copies the walk's filter and the force kernel use.  A warp takes 32
+// groups: the lanes reduce each group's particles together, then every lane
+// finishes one group's FP64 arithmetic.
 __global__ void __launch_bounds__(256) k_group_data(
     const DevState* __restrict__ st, const SysBox* __restrict__ box, const uint32_t* __restrict__ sys,
     const uint32_t* __restrict__ g_first,
@@ -443,52 +448,58 @@ __global__ void __launch_bounds__(256) k_group_data(
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t ng = st->n_groups;
-    for (int64_t g = warp; g < ng; g += nwarps) {
-        const uint32_t f = g_first[g], c = g_count[g];
-        const SysBox& bx = box[sys ? sys[f] : 0];
-        const double lo0 = bx.lo[0], lo1 = bx.lo[1], lo2 = bx.lo[2], s = bx.s;
-        const double c0x = bx.c0[0], c0y = bx.c0[1], c0z = bx.c0[2];
-        unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
-        for (uint32_t p = f + lane; p < f + c; p += 32) {
-            unsigned long long v[3] = {ord64(px[p]), ord64(py[p]), ord64(pz[p])};
+    for (int64_t base = warp * 32; base < ng; base += nwarps * 32) {
+        unsigned long long mlo[3] = {0, 0, 0}, mhi[3] = {0, 0, 0};
+        const int nb = ng - base < 32 ? (int)(ng - base) : 32;
+        for (int j = 0; j < nb; ++j) {
+            const uint32_t f = g_first[base + j], c = g_count[base + j];
+            unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
+            for (uint32_t p = f + lane; p < f + c; p += 32) {
+                unsigned long long v[3] = {ord64(px[p]), ord64(py[p]), ord64(pz[p])};
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                lo[a] = v[a] < lo[a] ? v[a] : lo[a];
-                hi[a] = v[a] > hi[a] ? v[a] : hi[a];
+                for (int a = 0; a < 3; ++a) {
+                    lo[a] = v[a] < lo[a] ? v[a] : lo[a];
+                    hi[a] = v[a] > hi[a] ? v[a] : hi[a];
+                }
             }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    unsigned long long l2 = __shfl_xor_sync(0xFFFFFFFFu, lo[a], off);
+                    unsigned long long h2 = __shfl_xor_sync(0xFFFFFFFFu, hi[a], off);
+                    lo[a] = l2 < lo[a] ? l2 : lo[a];
+                    hi[a] = h2 > hi[a] ? h2 : hi[a];
+                }
+            if (lane == j)
+                for (int a = 0; a < 3; ++a) {
+                    mlo[a] = lo[a];
+                    mhi[a] = hi[a];
+                }
         }
+        if (lane >= nb) continue;
+        const int64_t g = base + lane;
+        const SysBox& bx = box[sys ? sys[g_first[g]] : 0];
+        double bl[3], bh[3], cc[3];
+        float ch[3], cl[3], fl[3], fh[3];
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                unsigned long long l2 = __shfl_xor_sync(0xFFFFFFFFu, lo[a], off);
-                unsigned long long h2 = __shfl_xor_sync(0xFFFFFFFFu, hi[a], off);
-                lo[a] = l2 < lo[a] ? l2 : lo[a];
-                hi[a] = h2 > hi[a] ? h2 : hi[a];
-            }
-        if (lane == 0) {
-            double bl[3], bh[3], cc[3];
-            const double lo_r[3] = {lo0, lo1, lo2};
-            const double c0r[3] = {c0x, c0y, c0z};
-            float ch[3], cl[3], fl[3], fh[3];
-            for (int a = 0; a < 3; ++a) {
-                bl[a] = unord64(lo[a]);
-                bh[a] = unord64(hi[a]);
-                g_box[6 * g + a] = bl[a];
-                g_box[6 * g + 3 + a] = bh[a];
-                g_qbox[6 * g + a] = quantise(bl[a], lo_r[a], s);
-                g_qbox[6 * g + 3 + a] = quantise(bh[a], lo_r[a], s);
-                cc[a] = __dmul_rn(__dadd_rn(bl[a], bh[a]), 0.5);
-                split_hilo(cc[a] - c0r[a], &ch[a], &cl[a]);
-                fl[a] = __double2float_rd(bl[a] - cc[a]);
-                fh[a] = __double2float_ru(bh[a] - cc[a]);
-            }
-            g_c64[g] = make_dvec4(cc[0], cc[1], cc[2], 0.0);
-            g_ch[g] = make_float4(ch[0], ch[1], ch[2], 0.0f);
-            g_cl[g] = make_float4(cl[0], cl[1], cl[2], 0.0f);
-            g_blo[g] = make_float4(fl[0], fl[1], fl[2], 0.0f);
-            g_bhi[g] = make_float4(fh[0], fh[1], fh[2], 0.0f);
+        for (int a = 0; a < 3; ++a) {
+            bl[a] = unord64(mlo[a]);
+            bh[a] = unord64(mhi[a]);
+            g_box[6 * g + a] = bl[a];
+            g_box[6 * g + 3 + a] = bh[a];
+            g_qbox[6 * g + a] = quantise(bl[a], bx.lo[a], bx.s);
+            g_qbox[6 * g + 3 + a] = quantise(bh[a], bx.lo[a], bx.s);
+            cc[a] = __dmul_rn(__dadd_rn(bl[a], bh[a]), 0.5);
+            split_hilo(cc[a] - bx.c0[a], &ch[a], &cl[a]);
+            fl[a] = __double2float_rd(bl[a] - cc[a]);
+            fh[a] = __double2float_ru(bh[a] - cc[a]);
         }
+        g_c64[g] = make_dvec4(cc[0], cc[1], cc[2], 0.0);
+        g_ch[g] = make_float4(ch[0], ch[1], ch[2], 0.0f);
+        g_cl[g] = make_float4(cl[0], cl[1], cl[2], 0.0f);
+        g_blo[g] = make_float4(fl[0], fl[1], fl[2], 0.0f);
+        g_bhi[g] = make_float4(fh[0], fh[1], fh[2], 0.0f);
     }
 }
 
@@ -527,13 +538,13 @@ int compute_moments(fdps_tree* t, fdps_psys* ps) {
         if (t->p.moment == FDPS_QUADRUPOLE)
             k_moments_level<true><<<grid, 256, 0, s>>>(
                 l, t->st, t->sys_box, ps->d_sys, ps->x[c], ps->y[c], ps->z[c], ps->m[c], t->nd_first, t->nd_count,
-                t->nd_child, t->nd_meta, t->nd_sx, t->nd_sy, t->nd_sz, t->nd_com, t->nd_quad,
-                t->nd_fh, t->nd_fl, t->nd_fq0, t->nd_fq1);
+                t->nd_child, t->nd_meta, t->nd_qlo, t->nd_sx, t->nd_sy, t->nd_sz, t->nd_com,
+                t->nd_quad, t->nd_f, t->nd_walk, t->nd_fq0, t->nd_fq1);
         else
             k_moments_level<false><<<grid, 256, 0, s>>>(
                 l, t->st, t->sys_box, ps->d_sys, ps->x[c], ps->y[c], ps->z[c], ps->m[c], t->nd_first, t->nd_count,
-                t->nd_child, t->nd_meta, t->nd_sx, t->nd_sy, t->nd_sz, t->nd_com, t->nd_quad,
-                t->nd_fh, t->nd_fl, t->nd_fq0, t->nd_fq1);
+                t->nd_child, t->nd_meta, t->nd_qlo, t->nd_sx, t->nd_sy, t->nd_sz, t->nd_com,
+                t->nd_quad, t->nd_f, t->nd_walk, t->nd_fq0, t->nd_fq1);
         FDPS_LAUNCH_CHECK(ctx);
     }
     return FDPS_OK;

@@ -95,6 +95,7 @@ struct fdps_ctx {
     cudaStream_t stream = nullptr;
     bool profiling = false;
     int64_t launches = 0;  // kernels launched by this library on this context
+    bool capturing = false;  // a graph capture of a step is in progress
     std::string last_error;
 };
 
@@ -163,8 +164,9 @@ struct fdps_tree {
     double* nd_sz = nullptr;
     fdps::dvec4* nd_com = nullptr;      // FP64 (com_x, com_y, com_z, M)
     double* nd_quad = nullptr;      // FP64 [n][6]
-    float4* nd_fh = nullptr;        // FP32 (com_hi - c0, M)
-    float4* nd_fl = nullptr;        // FP32 (com_lo, 0)
+    float4* nd_f = nullptr;         // FP32 pairs [2i] = (com_hi - c0, M), [2i+1] = (com_lo, 0)
+    uint4* nd_walk = nullptr;       // what one opening test reads: grid origin (2 words),
+                                    // first child, meta
     float4* nd_fq0 = nullptr;       // FP32 (Qxx, Qyy, Qzz, Qxy)
     float2* nd_fq1 = nullptr;       // FP32 (Qxz, Qyz)
     uint32_t* lvl_scratch = nullptr;  // child-count slots of one level

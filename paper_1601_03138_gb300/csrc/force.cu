@@ -34,8 +34,7 @@ struct ForceArgs {
     const uint32_t* pool;
     const uint32_t* nd_first;
     const uint32_t* nd_count;
-    const float4* nd_fh;
-    const float4* nd_fl;
+    const float4* nd_f;
     const float4* nd_fq0;
     const float2* nd_fq1;
     const dvec4* nd_com;
@@ -261,7 +260,7 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
             const bool spj = ent[r] != 0xFFFFFFFFu && !(ent[r] & kLeafTag);
             if (spj) {
                 const uint32_t node = ent[r];
-                const float4 fh = A.nd_fh[node], fl = A.nd_fl[node];
+                const float4 fh = A.nd_f[2 * node], fl = A.nd_f[2 * node + 1];
                 sb.s0[rs] = make_float4((fh.x - gch.x) + (fl.x - gcl.x),
                                         (fh.y - gch.y) + (fl.y - gcl.y),
                                         (fh.z - gch.z) + (fl.z - gcl.z), fh.w);
@@ -585,8 +584,7 @@ int compute_forces(fdps_tree* t, fdps_psys* ps, int spj_kind) {
     A.pool = t->pool;
     A.nd_first = t->nd_first;
     A.nd_count = t->nd_count;
-    A.nd_fh = t->nd_fh;
-    A.nd_fl = t->nd_fl;
+    A.nd_f = t->nd_f;
     A.nd_fq0 = t->nd_fq0;
     A.nd_fq1 = t->nd_fq1;
     A.nd_com = t->nd_com;

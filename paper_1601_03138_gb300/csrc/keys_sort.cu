@@ -455,7 +455,7 @@ int keys_and_sort(fdps_tree* t, fdps_psys* ps) {
     k_keys<<<ntiles, kSortBlock, 0, s>>>(n, ps->x[c], ps->y[c], ps->z[c], t->sys_box, ps->d_sys,
                                          t->keys_in, t->sort_hist, ntiles);
     FDPS_LAUNCH_CHECK(ctx);
-    if (t->ev_ok && ctx->profiling) cudaEventRecord(t->ev[1], s);
+    if (t->ev_ok && ctx->profiling && !ctx->capturing) cudaEventRecord(t->ev[1], s);
     const uint64_t* kin = t->keys_in;
     const uint32_t* vin = nullptr;
     uint64_t* kb[2] = {t->keys_a, t->keys_b};

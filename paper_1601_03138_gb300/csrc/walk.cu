@@ -30,11 +30,8 @@ namespace fdps {
 struct WalkArgs {
     DevState* st;
     const uint32_t* nd_count;
-    const uint32_t* nd_child;
-    const uint32_t* nd_meta;
-    const uint64_t* nd_qlo;
-    const float4* nd_fh;
-    const float4* nd_fl;
+    const uint4* nd_walk;  // (grid origin low, high, first child, meta) per node
+    const float4* nd_f;    // COM hi/lo pairs per node
     const dvec4* nd_com;
     const uint32_t* g_count;
     const uint32_t* g_first;
@@ -69,7 +66,7 @@ __device__ __forceinline__ unsigned long long shfl_u64(unsigned long long v, int
 }
 
 // Exact FP64 opening test (b): the reference sequence of operations.
-__device__ __noinline__ bool open_fp64(double L, int level, double theta2, const dvec4 com,
+__device__ __forceinline__ bool open_fp64(double L, int level, double theta2, const dvec4 com,
                                        const double* box) {
     const double ell = ldexp(L, -level);
     const double c[3] = {com.x, com.y, com.z};
@@ -84,7 +81,7 @@ __device__ __noinline__ bool open_fp64(double L, int level, double theta2, const
     return __dmul_rn(ell, ell) >= __dmul_rn(theta2, d2);
 }
 
-__global__ void __launch_bounds__(kWalkBlock) k_walk(WalkArgs A) {
+__global__ void __launch_bounds__(kWalkBlock, 8) k_walk(WalkArgs A) {
     DevState* st = A.st;
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
@@ -119,25 +116,34 @@ __global__ void __launch_bounds__(kWalkBlock) k_walk(WalkArgs A) {
         const double* box64 = A.g_box + 6 * (int64_t)g;
 
         unsigned long long gstart = cursor;
-        uint32_t nspj = 0, nepj = 0;
+        uint32_t nspj = 0, nepj_lane = 0;
         uint32_t fsize = 1;
         if (lane == 0) fa[0] = sysid;
         __syncwarp();
         while (fsize > 0) {
             uint32_t nsize = 0;
             max_front = fsize > max_front ? fsize : max_front;
+            // the first batch's frontier entries and node records; every batch
+            // then fetches the next one's before testing its own
+            uint32_t node_nx = lane < fsize ? fa[lane] : 0u;
+            uint4 rec_nx = lane < fsize ? A.nd_walk[node_nx] : make_uint4(0, 0, 0, 0);
             for (uint32_t base = 0; base < fsize; base += 32) {
                 const uint32_t idx = base + lane;
                 const bool act = idx < fsize;
-                const uint32_t node = act ? fa[idx] : 0u;
+                const uint32_t node = node_nx;
+                const uint4 rec = rec_nx;
+                if (idx + 32 < fsize) {
+                    node_nx = fa[idx + 32];
+                    rec_nx = A.nd_walk[node_nx];
+                }
                 int action = 0;  // 1 SPJ, 2 EPJ leaf, 3 open internal
-                uint32_t nch = 0, child = 0, pcount = 0;
+                uint32_t nch = 0, child = 0;
                 bool fallback = false;
                 if (act) {
-                    const uint32_t meta = A.nd_meta[node];
+                    const uint32_t meta = rec.w;
                     const int level = (int)(meta & 0xFFu);
                     const bool leaf = (meta >> 16) & 1u;
-                    const uint64_t q = A.nd_qlo[node];
+                    const uint64_t q = (uint64_t)rec.x | ((uint64_t)rec.y << 32);
                     const uint32_t w = (1u << (kMaxLevel - level)) - 1u;
                     const uint32_t qx = (uint32_t)(q >> 42), qy = (uint32_t)(q >> 21) & kQMax,
                                    qz = (uint32_t)q & kQMax;
@@ -145,7 +151,7 @@ __global__ void __launch_bounds__(kWalkBlock) k_walk(WalkArgs A) {
                                        qy + w >= qmin1 && qz <= qmax2 && qz + w >= qmin2;
                     bool open = true;
                     if (!meets) {
-                        const float4 fh = A.nd_fh[node], fl = A.nd_fl[node];
+                        const float4 fh = A.nd_f[2 * node], fl = A.nd_f[2 * node + 1];
                         const float dx = (fh.x - gch.x) + (fl.x - gcl.x);
                         const float dy = (fh.y - gch.y) + (fl.y - gcl.y);
                         const float dz = (fh.z - gch.z) + (fl.z - gcl.z);
@@ -177,10 +183,10 @@ __global__ void __launch_bounds__(kWalkBlock) k_walk(WalkArgs A) {
                         action = 1;
                     } else if (leaf) {
                         action = 2;
-                        pcount = A.nd_count[node];
+                        nepj_lane += A.nd_count[node];
                     } else {
                         action = 3;
-                        child = A.nd_child[node];
+                        child = rec.z;
                         nch = (meta >> 8) & 0xFFu;
                     }
                 }
@@ -219,10 +225,6 @@ __global__ void __launch_bounds__(kWalkBlock) k_walk(WalkArgs A) {
                     cursor += k;
                 }
                 nspj += __popc(__ballot_sync(0xFFFFFFFFu, action == 1));
-                uint32_t pc = pcount;
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) pc += __shfl_xor_sync(0xFFFFFFFFu, pc, off);
-                nepj += pc;
                 // ---- push children of opened internal cells
                 uint32_t inc = nch;
 #pragma unroll
@@ -246,6 +248,7 @@ __global__ void __launch_bounds__(kWalkBlock) k_walk(WalkArgs A) {
             fb = tmp;
             fsize = nsize;
         }
+        const uint32_t nepj = __reduce_add_sync(0xFFFFFFFFu, nepj_lane);
         const unsigned long long len = cursor - gstart;
         if (lane == 0) {
             A.g_off[g] = gstart;
@@ -291,11 +294,8 @@ int launch_walk(fdps_tree* t, const uint32_t* sys, int blocks) {
     WalkArgs A;
     A.st = t->st;
     A.nd_count = t->nd_count;
-    A.nd_child = t->nd_child;
-    A.nd_meta = t->nd_meta;
-    A.nd_qlo = t->nd_qlo;
-    A.nd_fh = t->nd_fh;
-    A.nd_fl = t->nd_fl;
+    A.nd_walk = t->nd_walk;
+    A.nd_f = t->nd_f;
     A.nd_com = t->nd_com;
     A.g_count = t->g_count;
     A.g_first = t->g_first;
