@@ -32,10 +32,10 @@ sys.path.insert(0, ROOT)
 
 # FP32-lane operations of one interaction as the kernels evaluate the
 # formulas (FMA = 1): particle-particle and monopole superparticle 13,
-# quadrupole superparticle 35; plus one MUFU reciprocal square root each.
+# quadrupole superparticle 34; plus one MUFU reciprocal square root each.
 OPS_EPJ = 13
 OPS_SPJ_MONO = 13
-OPS_SPJ_QUAD = 35
+OPS_SPJ_QUAD = 34
 
 
 def parse():
@@ -60,6 +60,8 @@ def parse():
                     help="the ensemble workload: 4096 Plummer clusters, N log-uniform in "
                          "[256, 65536], eps = 1/(4 N^1/3), theta 0.5 monopole, dt 1/256")
     ap.add_argument("--n-sys", type=int, default=4096)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep n_leaf / n_grp as given instead of the autotuner's choice")
     return ap.parse_args()
 
 
@@ -208,6 +210,14 @@ def run_ours(args, rank, world, local_rank):
     ps = G.ParticleSystem(ctx, n)
     tree = G.Tree(ctx, theta=args.theta, n_leaf=args.n_leaf, n_grp=args.n_grp, quad=not args.mono)
     ps.set(pos, vel, mass, eps)
+    tuned = None
+    if not args.no_autotune:
+        # n_grp in {64, 128, 256, 512} (and n_leaf, tile depth) by measured
+        # time of the whole force calculation
+        best, ms = tree.autotune(ps, n_leaf=(8, 16), n_grp=(64, 128, 256, 512),
+                                 tile_depth=(256, 512), repeats=1)
+        tuned = {**best, "force_ms": ms}
+        args.n_leaf, args.n_grp = best["n_leaf"], best["n_grp"]
     tree.calc_force_all_and_write_back(ps)
     for _ in range(args.warmup):
         tree.step(ps, args.dt)
@@ -323,7 +333,7 @@ def run_ours(args, rank, world, local_rank):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
                 "config": {"workload": workload_name(args), "l2": "inputs larger than L2",
-                           "replicas": world},
+                           "replicas": world, "autotuned": tuned},
                 "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk, "fp64_variant": fp64, "stages_ms": stages,
                 "per_step": {"interactions": inter / args.steps,

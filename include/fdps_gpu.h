@@ -80,8 +80,8 @@ typedef enum {
                        is one i-group sharing one interaction list
      moment     enum fdps_moment
      precision  enum fdps_precision
-     tile_depth 0 = default; otherwise j-entries staged per force tile
-                (32..1024, multiple of 32)                                */
+     tile_depth list entries staged in shared memory per force-kernel chunk:
+                0 (default, = 512), 256 or 512                            */
 typedef struct {
     double theta;
     int32_t n_leaf;
@@ -222,6 +222,20 @@ int fdps_psys_energy_systems(fdps_psys* ps, double* kinetic, double* potential);
    buffers and the graphs are captured again.  Needs valid forces
    (FDPS_ESTATE); synchronises the stream once per step. */
 int fdps_run(fdps_tree* tree, fdps_psys* ps, double dt, int64_t n_steps);
+
+/* Autotuner: time the full force calculation (CUDA events, best of
+   `repeats` after one untimed sizing run) for every combination of the
+   candidate n_leaf, n_grp and tile_depth values (tile_depth may be NULL:
+   default only), keep the fastest in the tree's parameters, and leave the
+   forces of that choice in ps.  Combinations the parameter rules reject
+   (n_grp < n_leaf) are skipped.  *best and *best_ms (either may be NULL)
+   receive the winning parameters and its time in milliseconds.  Theta,
+   moment and precision are not tuned: they set the accuracy.
+   Errors: FDPS_EINVAL, FDPS_ESTATE, and those of the force calculation. */
+int fdps_tree_autotune(fdps_tree* tree, fdps_psys* ps, const int32_t* n_leaf, int32_t n_nl,
+                       const int32_t* n_grp, int32_t n_ng, const int32_t* tile_depth,
+                       int32_t n_td, int32_t repeats, fdps_tree_params* best,
+                       double* best_ms);
 
 /* --------------------------------------------------- introspection
    Test and diagnostic access to the last force calculation's

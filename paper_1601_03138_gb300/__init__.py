@@ -102,6 +102,8 @@ _PROTOS = {
     "fdps_psys_num_systems": (_i32, [_vp]),
     "fdps_psys_energy_systems": (C.c_int, [_vp, _vp, _vp]),
     "fdps_run": (C.c_int, [_vp, _vp, _d, _i64]),
+    "fdps_tree_autotune": (C.c_int, [_vp, _vp, _vp, _i32, _vp, _i32, _vp, _i32, _i32,
+                                     C.POINTER(fdps_tree_params), C.POINTER(_d)]),
 }
 
 FDPS_NOALLOC_MAX_N = 1 << 18
@@ -267,6 +269,21 @@ def fdps_psys_energy_systems(ctx, ps):
 
 def fdps_run(ctx, tree, ps, dt, n_steps):
     _check(lib().fdps_run(tree, ps, float(dt), int(n_steps)), ctx)
+
+
+def fdps_tree_autotune(ctx, tree, ps, n_leaf=(8, 16), n_grp=(64, 128, 256, 512),
+                       tile_depth=(256, 512), repeats=2):
+    """Pick the fastest (n_leaf, n_grp, tile_depth); returns (params dict, ms)."""
+    nl = np.ascontiguousarray(n_leaf, dtype=np.int32)
+    ng = np.ascontiguousarray(n_grp, dtype=np.int32)
+    td = np.ascontiguousarray(tile_depth, dtype=np.int32)
+    best = fdps_tree_params()
+    ms = C.c_double()
+    _check(lib().fdps_tree_autotune(tree, ps, C.c_void_p(nl.ctypes.data), len(nl),
+                                    C.c_void_p(ng.ctypes.data), len(ng), C.c_void_p(td.ctypes.data),
+                                    len(td), int(repeats), C.byref(best), C.byref(ms)), ctx)
+    return ({"theta": best.theta, "n_leaf": best.n_leaf, "n_grp": best.n_grp,
+             "tile_depth": best.tile_depth}, ms.value)
 
 
 def fdps_psys_energy(ctx, ps):
@@ -447,6 +464,9 @@ class Tree:
 
     def run(self, psys: ParticleSystem, dt: float, n_steps: int):
         fdps_run(self.ctx.h, self.h, psys.h, dt, n_steps)
+
+    def autotune(self, psys: ParticleSystem, **kw):
+        return fdps_tree_autotune(self.ctx.h, self.h, psys.h, **kw)
 
     def stats(self):
         return fdps_tree_get_stats(self.ctx.h, self.h)

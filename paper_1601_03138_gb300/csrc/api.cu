@@ -301,7 +301,7 @@ bool valid_params(const fdps_tree_params* p) {
            p->n_leaf <= kMaxLeaf && p->n_grp >= p->n_leaf && p->n_grp <= kMaxGrp &&
            (p->moment == FDPS_MONOPOLE || p->moment == FDPS_QUADRUPOLE) &&
            (p->precision == FDPS_FP32REL || p->precision == FDPS_FP64) &&
-           (p->tile_depth == 0 || (p->tile_depth >= 32 && p->tile_depth <= 1024 && p->tile_depth % 32 == 0));
+           (p->tile_depth == 0 || p->tile_depth == 256 || p->tile_depth == 512);
 }
 
 }  // namespace
@@ -798,6 +798,68 @@ int fdps_tree_get_lists(const fdps_tree* tc, int64_t g0, int64_t g1, int64_t* of
     free(hoff);
     free(hlen);
     if (e) return set_error(t->ctx, FDPS_ECUDA, "list readback failed: %s", cudaGetErrorString(e));
+    return FDPS_OK;
+}
+
+int fdps_tree_autotune(fdps_tree* t, fdps_psys* ps, const int32_t* n_leaf, int32_t n_nl,
+                       const int32_t* n_grp, int32_t n_ng, const int32_t* tile_depth, int32_t n_td,
+                       int32_t repeats, fdps_tree_params* best, double* best_ms) {
+    if (!t || !ps || !n_leaf || !n_grp || n_nl < 1 || n_ng < 1 || repeats < 1) return FDPS_EINVAL;
+    fdps_ctx* ctx = t->ctx;
+    if (!ps->has_data) return set_error(ctx, FDPS_ESTATE, "particle data not set");
+    cudaSetDevice(ctx->device);
+    const int32_t td_default[1] = {0};
+    if (!tile_depth || n_td < 1) {
+        tile_depth = td_default;
+        n_td = 1;
+    }
+    const int k_spj = t->p.moment == FDPS_QUADRUPOLE ? FDPS_GRAV_SPJ_QUAD : FDPS_GRAV_SPJ_MONO;
+    cudaEvent_t e0, e1;
+    FDPS_CUDA_TRY(ctx, cudaEventCreate(&e0));
+    FDPS_CUDA_TRY(ctx, cudaEventCreate(&e1));
+    const fdps_tree_params orig = t->p;
+    fdps_tree_params win = orig;
+    float win_ms = -1.f;
+    int rc = FDPS_OK;
+    for (int32_t a = 0; a < n_nl && !rc; ++a)
+        for (int32_t b = 0; b < n_ng && !rc; ++b)
+            for (int32_t c = 0; c < n_td && !rc; ++c) {
+                fdps_tree_params cand = orig;
+                cand.n_leaf = n_leaf[a];
+                cand.n_grp = n_grp[b];
+                cand.tile_depth = tile_depth[c];
+                if (!valid_params(&cand)) continue;  // e.g. n_grp < n_leaf
+                t->p = cand;
+                if ((rc = run_force(t, ps, k_spj))) break;  // sizes the buffers
+                float best_here = -1.f;
+                for (int32_t r = 0; r < repeats && !rc; ++r) {
+                    cudaEventRecord(e0, ctx->stream);
+                    rc = run_force(t, ps, k_spj);
+                    cudaEventRecord(e1, ctx->stream);
+                    cudaEventSynchronize(e1);
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (best_here < 0.f || ms < best_here) best_here = ms;
+                }
+                if (!rc && (win_ms < 0.f || best_here < win_ms)) {
+                    win_ms = best_here;
+                    win = cand;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) {
+        t->p = orig;
+        return rc;
+    }
+    if (win_ms < 0.f) {
+        t->p = orig;
+        return set_error(ctx, FDPS_EINVAL, "no valid candidate parameters");
+    }
+    t->p = win;
+    if ((rc = run_force(t, ps, k_spj))) return rc;  // leave forces of the chosen parameters
+    if (best) *best = win;
+    if (best_ms) *best_ms = win_ms;
     return FDPS_OK;
 }
 

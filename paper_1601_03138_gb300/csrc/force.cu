@@ -113,8 +113,8 @@ __device__ __forceinline__ int owner(const uint32_t* scan, uint32_t item) {
 
 constexpr int kCB = 128;            // threads per CTA
 constexpr int kCW = kCB / 32;
-constexpr int kEPT = 4;             // list entries per thread per chunk
-constexpr int kCE = kCB * kEPT;     // list entries per chunk
+// list entries per thread per chunk (EPT) is a template parameter: the
+// chunk ("tile depth") holds kCB * EPT entries, 256 or 512
 constexpr int kCJ = 256;            // leaf particles per shared tile
 constexpr int kRed = 4 * kCB;       // slice-reduction slots per component
 
@@ -177,11 +177,12 @@ __device__ __forceinline__ void block_scan2(uint32_t a, uint32_t b, uint32_t* ea
     *tb = sb;
 }
 
-// Largest e in [0, kCE) with scan[e] <= item.
+// Largest e in [0, CE) with scan[e] <= item.
+template <int CE>
 __device__ __forceinline__ int owner_chunk(const uint32_t* scan, uint32_t item) {
     int lo = 0;
 #pragma unroll
-    for (int step = kCE / 2; step > 0; step >>= 1)
+    for (int step = CE / 2; step > 0; step >>= 1)
         if (scan[lo + step] <= item) lo += step;
     return lo;
 }
@@ -204,7 +205,7 @@ struct SpjBuf {
     float2* s2;  // Qxz, Qyz
 };
 
-template <bool QUAD, int K>
+template <bool QUAD, int K, int EPT>
 __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf, uint32_t ni,
                                                 unsigned long long off, uint32_t len, float4 gch,
                                                 float4 gcl, int P, int nsl, uint32_t ib,
@@ -234,18 +235,19 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
 #pragma unroll
     for (int k = 0; k < 8 * K; ++k) s_k[k * kCB + t] = 0.0f;
 
-    for (uint32_t base = 0; base < len; base += kCE) {
-        // ---- this thread's kEPT consecutive entries: type, node data, leaf range
+    constexpr int CE = kCB * EPT;
+    for (uint32_t base = 0; base < len; base += CE) {
+        // ---- this thread's EPT consecutive entries: type, node data, leaf range
         uint32_t nspj = 0, npart = 0;
-        uint32_t ent[kEPT];
+        uint32_t ent[EPT];
 #pragma unroll
-        for (int r = 0; r < kEPT; ++r) {
-            const uint32_t u = base + (uint32_t)(t * kEPT + r);
+        for (int r = 0; r < EPT; ++r) {
+            const uint32_t u = base + (uint32_t)(t * EPT + r);
             ent[r] = u < len ? A.pool[off + u] : 0xFFFFFFFFu;
         }
-        uint32_t lcnt[kEPT], lfirst[kEPT];
+        uint32_t lcnt[EPT], lfirst[EPT];
 #pragma unroll
-        for (int r = 0; r < kEPT; ++r) {
+        for (int r = 0; r < EPT; ++r) {
             const bool leaf = ent[r] != 0xFFFFFFFFu && (ent[r] & kLeafTag);
             const bool spj = ent[r] != 0xFFFFFFFFu && !(ent[r] & kLeafTag);
             lcnt[r] = leaf ? A.nd_count[ent[r] & ~kLeafTag] : 0u;
@@ -256,7 +258,7 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
         uint32_t rs, es, ns, total;
         block_scan2(nspj, npart, &rs, &es, &ns, &total, s_w);
 #pragma unroll
-        for (int r = 0; r < kEPT; ++r) {
+        for (int r = 0; r < EPT; ++r) {
             const bool spj = ent[r] != 0xFFFFFFFFu && !(ent[r] & kLeafTag);
             if (spj) {
                 const uint32_t node = ent[r];
@@ -270,8 +272,8 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
                 }
                 ++rs;
             }
-            s_ef[t * kEPT + r] = lfirst[r];
-            s_es[t * kEPT + r] = es;
+            s_ef[t * EPT + r] = lfirst[r];
+            s_es[t * EPT + r] = es;
             es += lcnt[r];
         }
         __syncthreads();
@@ -279,6 +281,7 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
 #pragma unroll
         for (int q = 0; q < K; ++q) pax[q] = pay[q] = paz[q] = pp[q] = 0.f;
         // ---- superparticles of this chunk
+#pragma unroll 2
         for (int k = kbeg; k < (int)ns; k += nsl) {
             const float4 a = sb.s0[k];
             float4 q0;
@@ -301,11 +304,12 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
                     const float Qrz = fmaf(q1.x, rx, fmaf(q1.y, ry, q0.z * rz));
                     const float rQr = fmaf(rx, Qrx, fmaf(ry, Qry, rz * Qrz));
                     const float Ri5 = Ri2 * Ri2 * Ri;
-                    const float c = fmaf(2.5f * rQr, Ri5 * Ri2, MRi3);
+                    const float u = rQr * Ri5;                  // r.Q.r / R^5
+                    const float c = fmaf(2.5f * u, Ri2, MRi3);  // M/R^3 + 5/2 r.Q.r / R^7
                     pax[q] = fmaf(Qrx, Ri5, fmaf(-c, rx, pax[q]));
                     pay[q] = fmaf(Qry, Ri5, fmaf(-c, ry, pay[q]));
                     paz[q] = fmaf(Qrz, Ri5, fmaf(-c, rz, paz[q]));
-                    pp[q] -= fmaf(0.5f * rQr, Ri5, MRi);
+                    pp[q] = fmaf(-0.5f, u, pp[q] - MRi);
                 } else {
                     pax[q] = fmaf(-MRi3, rx, pax[q]);
                     pay[q] = fmaf(-MRi3, ry, pay[q]);
@@ -320,13 +324,14 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
             if (c0 > 0) __syncthreads();  // previous tile fully consumed
             for (uint32_t k = t; k < m; k += kCB) {
                 const uint32_t item = c0 + k;
-                const int src = owner_chunk(s_es, item);
+                const int src = owner_chunk<CE>(s_es, item);
                 const uint32_t p = s_ef[src] + (item - s_es[src]);
                 const float4 h = A.pf_hi[p], l = A.pf_lo[p];
                 s_j[k] = make_float4((h.x - gch.x) + (l.x - gcl.x), (h.y - gch.y) + (l.y - gcl.y),
                                      (h.z - gch.z) + (l.z - gcl.z), h.w);
             }
             __syncthreads();
+#pragma unroll 2
             for (int k = kbeg; k < (int)m; k += nsl) {
                 const float4 j = s_j[k];
 #pragma unroll
@@ -381,8 +386,9 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
     __syncthreads();
 }
 
-template <bool QUAD>
+template <bool QUAD, int EPT>
 __global__ void __launch_bounds__(kCB) k_force_f32(ForceArgs A) {
+    constexpr int kCE = kCB * EPT;
     constexpr int kSpjBytes = kCE * (QUAD ? 40 : 16);
     constexpr int kRedBytes = 4 * kRed * 8;
     constexpr int kUnion = kSpjBytes > kRedBytes ? kSpjBytes : kRedBytes;
@@ -413,13 +419,13 @@ __global__ void __launch_bounds__(kCB) k_force_f32(ForceArgs A) {
         for (uint32_t ib = 0; ib < ni;) {
             const GroupPlan pl = plan_group(ni - ib);
             if (pl.K == 1)
-                force_round_f32<QUAD, 1>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, s_j, sb,
+                force_round_f32<QUAD, 1, EPT>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, s_j, sb,
                                          s_ef, s_es, s_w, s_red, s_k);
             else if (pl.K == 2)
-                force_round_f32<QUAD, 2>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, s_j, sb,
+                force_round_f32<QUAD, 2, EPT>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, s_j, sb,
                                          s_ef, s_es, s_w, s_red, s_k);
             else
-                force_round_f32<QUAD, 4>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, s_j, sb,
+                force_round_f32<QUAD, 4, EPT>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, s_j, sb,
                                          s_ef, s_es, s_w, s_red, s_k);
             ib += (uint32_t)(pl.P * pl.K);
         }
@@ -564,8 +570,8 @@ int force_blocks(fdps_ctx* ctx, int precision, int quad) {
         e = quad ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_f64<true>, kFBlock, 0)
                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_f64<false>, kFBlock, 0);
     else
-        e = quad ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_f32<true>, kCB, 0)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_f32<false>, kCB, 0);
+        e = quad ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_f32<true, 4>, kCB, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_f32<false, 4>, kCB, 0);
     if (e != cudaSuccess || per_sm < 1) per_sm = 4;
     return per_sm * ctx->sm_count;
 }
@@ -609,10 +615,19 @@ int compute_forces(fdps_tree* t, fdps_psys* ps, int spj_kind) {
         else
             k_force_f64<false><<<blocks, kFBlock, 0, s>>>(A);
     } else {
-        if (quad)
-            k_force_f32<true><<<blocks, kCB, 0, s>>>(A);
-        else
-            k_force_f32<false><<<blocks, kCB, 0, s>>>(A);
+        // tile depth: list entries staged per chunk (0 = default 512)
+        const bool shallow = t->p.tile_depth == 256;
+        if (quad) {
+            if (shallow)
+                k_force_f32<true, 2><<<blocks, kCB, 0, s>>>(A);
+            else
+                k_force_f32<true, 4><<<blocks, kCB, 0, s>>>(A);
+        } else {
+            if (shallow)
+                k_force_f32<false, 2><<<blocks, kCB, 0, s>>>(A);
+            else
+                k_force_f32<false, 4><<<blocks, kCB, 0, s>>>(A);
+        }
     }
     FDPS_LAUNCH_CHECK(ctx);
     return FDPS_OK;

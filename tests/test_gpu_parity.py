@@ -34,10 +34,12 @@ def ctx(G):
     c.close()
 
 
-def run_gpu(G, ctx, pos, vel, mass, eps, theta, n_leaf, n_grp, quad=False, fp64=False):
+def run_gpu(G, ctx, pos, vel, mass, eps, theta, n_leaf, n_grp, quad=False, fp64=False,
+            tile_depth=0):
     n = len(pos)
     ps = G.ParticleSystem(ctx, n)
-    tree = G.Tree(ctx, theta=theta, n_leaf=n_leaf, n_grp=n_grp, quad=quad, fp64=fp64)
+    tree = G.Tree(ctx, theta=theta, n_leaf=n_leaf, n_grp=n_grp, quad=quad, fp64=fp64,
+                  tile_depth=tile_depth)
     ps.set(np.ascontiguousarray(pos), np.ascontiguousarray(vel), np.ascontiguousarray(mass),
            np.ascontiguousarray(eps))
     tree.calc_force_all_and_write_back(ps)
@@ -345,3 +347,38 @@ def test_parity_at_full_bench_size(G, ctx):
     FP64 direct sum."""
     pos, vel, mass, eps = ics.make("hernquist", 1 << 24, ics.SEED_BASE + 3, 0.005)
     _sampled_parity(G, ctx, pos, vel, mass, eps, 0.5, 16, 128, True, 64, 256, 5e-4)
+
+
+@pytest.mark.parametrize("quad", [False, True])
+def test_shallow_tile_depth_matches_oracle(G, ctx, quad):
+    n = 20000
+    pos, vel, mass, eps = ics.make("hernquist", n, ics.SEED_BASE + 41, 0.01)
+    ps, tree = run_gpu(G, ctx, pos, vel, mass, eps, 0.5, 8, 128, quad, tile_depth=256)
+    try:
+        _, _, acc, pot = ps.get()
+        acc_r, pot_r, _ = oracle.Tree(pos, mass, eps, 0.5, 8, 128, quad).force()
+        assert rms_rel(acc, acc_r) <= RMS_FP32
+        assert rms_rel(pot, pot_r) <= RMS_FP32
+    finally:
+        tree.close()
+        ps.close()
+
+
+def test_autotuner_picks_a_candidate_and_keeps_parity(G, ctx):
+    n = 30000
+    pos, vel, mass, eps = ics.make("plummer", n, ics.SEED_BASE + 43, 0.01)
+    ps = G.ParticleSystem(ctx, n)
+    tree = G.Tree(ctx, theta=0.6, n_leaf=8, n_grp=64, quad=True)
+    try:
+        ps.set(pos, vel, mass, eps)
+        best, ms = tree.autotune(ps, n_leaf=(4, 8), n_grp=(2, 32, 128), tile_depth=(256, 512))
+        assert best["n_leaf"] in (4, 8) and best["n_grp"] in (32, 128)  # n_grp 2 < n_leaf: skipped
+        assert best["tile_depth"] in (256, 512) and best["theta"] == 0.6 and ms > 0
+        _, _, acc, pot = ps.get()
+        acc_r, _, _ = oracle.Tree(pos, mass, eps, 0.6, best["n_leaf"], best["n_grp"], True).force()
+        assert rms_rel(acc, acc_r) <= RMS_FP32
+        with pytest.raises(G.FdpsError):
+            tree.autotune(ps, n_leaf=(16,), n_grp=(4,))  # nothing valid
+    finally:
+        tree.close()
+        ps.close()
