@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--model", default="hernquist")
     ap.add_argument("--theta", type=float, default=0.5)
     ap.add_argument("--n-leaf", type=int, default=16)
-    ap.add_argument("--n-grp", type=int, default=128)
+    ap.add_argument("--n-grp", type=int, default=256)
     ap.add_argument("--eps", type=float, default=0.005)
     ap.add_argument("--dt", type=float, default=1.0 / 512.0)
     ap.add_argument("--mono", action="store_true")

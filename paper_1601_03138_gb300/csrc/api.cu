@@ -83,7 +83,8 @@ int ensure_nodes(fdps_tree* t, int64_t cap) {
     free_nodes(t);
     bool ok = dev_alloc(&t->nd_first, cap) == cudaSuccess && dev_alloc(&t->nd_count, cap) == cudaSuccess &&
               dev_alloc(&t->nd_child, cap) == cudaSuccess && dev_alloc(&t->nd_meta, cap) == cudaSuccess &&
-              dev_alloc(&t->nd_parent, cap) == cudaSuccess && dev_alloc(&t->nd_qlo, cap) == cudaSuccess &&
+              dev_alloc(&t->nd_parent, cap) == cudaSuccess &&
+              dev_alloc(&t->nd_qlo, cap) == cudaSuccess &&
               dev_alloc(&t->nd_prefix, cap) == cudaSuccess && dev_alloc(&t->nd_sx, cap) == cudaSuccess &&
               dev_alloc(&t->nd_sy, cap) == cudaSuccess && dev_alloc(&t->nd_sz, cap) == cudaSuccess &&
               dev_alloc(&t->nd_com, cap) == cudaSuccess && dev_alloc(&t->nd_quad, 6 * cap) == cudaSuccess &&
@@ -715,9 +716,21 @@ int fdps_tree_get_nodes(const fdps_tree* tc, int64_t cap, int64_t* n_out, int32_
             }
         }
         if (quad && !e) {
-            if (t->p.moment == FDPS_QUADRUPOLE) {
+            if (t->p.moment == FDPS_QUADRUPOLE && t->p.precision == FDPS_FP64) {
                 e = cudaMemcpyAsync(quad, t->nd_quad, sizeof(double) * 6 * nn, cudaMemcpyDeviceToHost, s);
                 if (!e) e = cudaStreamSynchronize(s);
+            } else if (t->p.moment == FDPS_QUADRUPOLE) {
+                // the FP32 pipeline keeps its quadrupoles in FP32
+                float* hq = (float*)malloc(sizeof(float) * 6 * (size_t)nn + 8);
+                if (!hq) e = cudaErrorMemoryAllocation;
+                if (!e) e = cudaMemcpy2DAsync(hq, 6 * sizeof(float), t->nd_fq0, sizeof(float4), sizeof(float4),
+                                              nn, cudaMemcpyDeviceToHost, s);
+                if (!e) e = cudaMemcpy2DAsync(hq + 4, 6 * sizeof(float), t->nd_fq1, sizeof(float2),
+                                              sizeof(float2), nn, cudaMemcpyDeviceToHost, s);
+                if (!e) e = cudaStreamSynchronize(s);
+                for (int64_t i = 0; !e && i < nn; ++i)
+                    for (int k = 0; k < 6; ++k) quad[6 * i + k] = hq[6 * i + k];
+                free(hq);
             } else {
                 memset(quad, 0, sizeof(double) * 6 * nn);
             }

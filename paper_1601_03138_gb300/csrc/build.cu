@@ -253,96 +253,184 @@ __device__ __forceinline__ void split_hilo(double v, float* hi, float* lo) {
     *lo = __double2float_rn(v - (double)h);
 }
 
-template <bool QUAD>
-__global__ void __launch_bounds__(256) k_moments_level(
-    int l, const DevState* __restrict__ st, const SysBox* __restrict__ box,
-    const uint32_t* __restrict__ sys, const double* __restrict__ px,
-    const double* __restrict__ py, const double* __restrict__ pz, const double* __restrict__ pm,
-    const uint32_t* __restrict__ nd_first, const uint32_t* __restrict__ nd_count,
-    const uint32_t* __restrict__ nd_child, const uint32_t* __restrict__ nd_meta,
-    const uint64_t* __restrict__ nd_qlo, double* __restrict__ nd_sx, double* __restrict__ nd_sy,
-    double* __restrict__ nd_sz, dvec4* __restrict__ nd_com, double* __restrict__ nd_quad,
-    float4* __restrict__ nd_f, uint4* __restrict__ nd_walk, float4* __restrict__ nd_fq0,
-    float2* __restrict__ nd_fq1) {
-    const int64_t a = st->lvl_start[l], b = st->lvl_start[l + 1];
-    for (int64_t i = a + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < b;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t meta = nd_meta[i];
-        const SysBox& bx = box[sys ? sys[nd_first[i]] : 0];
-        const double c0x = bx.c0[0], c0y = bx.c0[1], c0z = bx.c0[2];
-        double M = 0.0, Sx = 0.0, Sy = 0.0, Sz = 0.0;
-        const bool leaf = meta_leaf(meta);
-        const uint32_t f = nd_first[i], cnt = nd_count[i];
-        const uint32_t c0 = nd_child[i], nc = meta_nchild(meta);
+struct MomArgs {
+    const DevState* st;
+    const SysBox* box;
+    const uint32_t* sys;
+    const double* px;
+    const double* py;
+    const double* pz;
+    const double* pm;
+    const float4* pf_hi;
+    const float4* pf_lo;
+    const uint32_t* nd_first;
+    const uint32_t* nd_count;
+    const uint32_t* nd_child;
+    const uint32_t* nd_meta;
+    const uint32_t* nd_parent;
+    const uint64_t* nd_qlo;
+    // written here and read back for the parent in a later launch (read
+    // through L2 with __ldcg)
+    double* nd_sx;
+    double* nd_sy;
+    double* nd_sz;
+    dvec4* nd_com;
+    double* nd_quad;
+    float4* nd_f;
+    uint4* nd_walk;
+    float4* nd_fq0;
+    float2* nd_fq1;
+};
+
+// Moments of node i, whose children (if any) are complete.  M and S = sum
+// m x in FP64 with every operation rounded on its own: leaves sequentially
+// over their particles, internal nodes over their children in octant
+// order.  Quadrupole: FP64 (Q64) for the FP64 pipeline; otherwise FP32 from
+// positions relative to the node's COM formed from FP32 hi/lo pairs, and the
+// parallel-axis shift for internal nodes.
+template <bool QUAD, bool Q64>
+__device__ __forceinline__ void node_moments(const MomArgs& A, int64_t i) {
+    const uint32_t meta = A.nd_meta[i];
+    const bool leaf = meta_leaf(meta);
+    const uint32_t f = A.nd_first[i], cnt = A.nd_count[i];
+    const uint32_t c0 = A.nd_child[i], nc = meta_nchild(meta);
+    const SysBox& bx = A.box[A.sys ? A.sys[f] : 0];
+    double M = 0.0, Sx = 0.0, Sy = 0.0, Sz = 0.0;
+    if (leaf) {
+        for (uint32_t p = f; p < f + cnt; ++p) {
+            const double m = A.pm[p];
+            M = __dadd_rn(M, m);
+            Sx = __dadd_rn(Sx, __dmul_rn(m, A.px[p]));
+            Sy = __dadd_rn(Sy, __dmul_rn(m, A.py[p]));
+            Sz = __dadd_rn(Sz, __dmul_rn(m, A.pz[p]));
+        }
+    } else {
+        for (uint32_t c = c0; c < c0 + nc; ++c) {
+            M = __dadd_rn(M, __ldcg(&A.nd_com[c].w));
+            Sx = __dadd_rn(Sx, __ldcg(&A.nd_sx[c]));
+            Sy = __dadd_rn(Sy, __ldcg(&A.nd_sy[c]));
+            Sz = __dadd_rn(Sz, __ldcg(&A.nd_sz[c]));
+        }
+    }
+    double cx = 0.0, cy = 0.0, cz = 0.0;
+    if (M > 0.0) {
+        cx = __ddiv_rn(Sx, M);
+        cy = __ddiv_rn(Sy, M);
+        cz = __ddiv_rn(Sz, M);
+    }
+    A.nd_sx[i] = Sx;
+    A.nd_sy[i] = Sy;
+    A.nd_sz[i] = Sz;
+    A.nd_com[i] = make_dvec4(cx, cy, cz, M);
+    float hx, hy, hz, lx, ly, lz;
+    split_hilo(cx - bx.c0[0], &hx, &lx);
+    split_hilo(cy - bx.c0[1], &hy, &ly);
+    split_hilo(cz - bx.c0[2], &hz, &lz);
+    A.nd_f[2 * i] = make_float4(hx, hy, hz, __double2float_rn(M));
+    A.nd_f[2 * i + 1] = make_float4(lx, ly, lz, 0.0f);
+    const uint64_t qlo = A.nd_qlo[i];
+    A.nd_walk[i] = make_uint4((uint32_t)qlo, (uint32_t)(qlo >> 32), c0, meta);
+    if (!QUAD) return;
+    if (Q64) {
+        double q[6] = {0, 0, 0, 0, 0, 0};
         if (leaf) {
             for (uint32_t p = f; p < f + cnt; ++p) {
-                const double m = pm[p];
-                M = __dadd_rn(M, m);
-                Sx = __dadd_rn(Sx, __dmul_rn(m, px[p]));
-                Sy = __dadd_rn(Sy, __dmul_rn(m, py[p]));
-                Sz = __dadd_rn(Sz, __dmul_rn(m, pz[p]));
+                const double m = A.pm[p];
+                const double dx = A.px[p] - cx, dy = A.py[p] - cy, dz = A.pz[p] - cz;
+                const double d2 = dx * dx + dy * dy + dz * dz;
+                q[0] += m * (3.0 * dx * dx - d2);
+                q[1] += m * (3.0 * dy * dy - d2);
+                q[2] += m * (3.0 * dz * dz - d2);
+                q[3] += m * (3.0 * dx * dy);
+                q[4] += m * (3.0 * dx * dz);
+                q[5] += m * (3.0 * dy * dz);
             }
         } else {
             for (uint32_t c = c0; c < c0 + nc; ++c) {
-                M = __dadd_rn(M, nd_com[c].w);
-                Sx = __dadd_rn(Sx, nd_sx[c]);
-                Sy = __dadd_rn(Sy, nd_sy[c]);
-                Sz = __dadd_rn(Sz, nd_sz[c]);
+                const double ccx = __ldcg(&A.nd_com[c].x), ccy = __ldcg(&A.nd_com[c].y),
+                             ccz = __ldcg(&A.nd_com[c].z), ccm = __ldcg(&A.nd_com[c].w);
+                const double dx = ccx - cx, dy = ccy - cy, dz = ccz - cz;
+                const double d2 = dx * dx + dy * dy + dz * dz;
+                const double* qc = A.nd_quad + 6 * (int64_t)c;
+                q[0] += __ldcg(qc + 0) + ccm * (3.0 * dx * dx - d2);
+                q[1] += __ldcg(qc + 1) + ccm * (3.0 * dy * dy - d2);
+                q[2] += __ldcg(qc + 2) + ccm * (3.0 * dz * dz - d2);
+                q[3] += __ldcg(qc + 3) + ccm * (3.0 * dx * dy);
+                q[4] += __ldcg(qc + 4) + ccm * (3.0 * dx * dz);
+                q[5] += __ldcg(qc + 5) + ccm * (3.0 * dy * dz);
             }
         }
-        double cx = 0.0, cy = 0.0, cz = 0.0;
-        if (M > 0.0) {
-            cx = __ddiv_rn(Sx, M);
-            cy = __ddiv_rn(Sy, M);
-            cz = __ddiv_rn(Sz, M);
-        }
-        nd_sx[i] = Sx;
-        nd_sy[i] = Sy;
-        nd_sz[i] = Sz;
-        nd_com[i] = make_dvec4(cx, cy, cz, M);
-        float hx, hy, hz, lx, ly, lz;
-        split_hilo(cx - c0x, &hx, &lx);
-        split_hilo(cy - c0y, &hy, &ly);
-        split_hilo(cz - c0z, &hz, &lz);
-        nd_f[2 * i] = make_float4(hx, hy, hz, __double2float_rn(M));
-        nd_f[2 * i + 1] = make_float4(lx, ly, lz, 0.0f);
-        const uint64_t q = nd_qlo[i];
-        nd_walk[i] = make_uint4((uint32_t)q, (uint32_t)(q >> 32), c0, meta);
-        if (QUAD) {
-            double q[6] = {0, 0, 0, 0, 0, 0};
-            if (leaf) {
-                for (uint32_t p = f; p < f + cnt; ++p) {
-                    const double m = pm[p];
-                    const double dx = px[p] - cx, dy = py[p] - cy, dz = pz[p] - cz;
-                    const double d2 = dx * dx + dy * dy + dz * dz;
-                    q[0] += m * (3.0 * dx * dx - d2);
-                    q[1] += m * (3.0 * dy * dy - d2);
-                    q[2] += m * (3.0 * dz * dz - d2);
-                    q[3] += m * (3.0 * dx * dy);
-                    q[4] += m * (3.0 * dx * dz);
-                    q[5] += m * (3.0 * dy * dz);
-                }
-            } else {
-                for (uint32_t c = c0; c < c0 + nc; ++c) {
-                    const dvec4 cc = nd_com[c];
-                    const double dx = cc.x - cx, dy = cc.y - cy, dz = cc.z - cz;
-                    const double d2 = dx * dx + dy * dy + dz * dz;
-                    const double* qc = nd_quad + 6 * (int64_t)c;
-                    q[0] += qc[0] + cc.w * (3.0 * dx * dx - d2);
-                    q[1] += qc[1] + cc.w * (3.0 * dy * dy - d2);
-                    q[2] += qc[2] + cc.w * (3.0 * dz * dz - d2);
-                    q[3] += qc[3] + cc.w * (3.0 * dx * dy);
-                    q[4] += qc[4] + cc.w * (3.0 * dx * dz);
-                    q[5] += qc[5] + cc.w * (3.0 * dy * dz);
-                }
-            }
-            double* qo = nd_quad + 6 * i;
+        double* qo = A.nd_quad + 6 * i;
 #pragma unroll
-            for (int k = 0; k < 6; ++k) qo[k] = q[k];
-            nd_fq0[i] = make_float4((float)q[0], (float)q[1], (float)q[2], (float)q[3]);
-            nd_fq1[i] = make_float2((float)q[4], (float)q[5]);
+        for (int k = 0; k < 6; ++k) qo[k] = q[k];
+        A.nd_fq0[i] = make_float4((float)q[0], (float)q[1], (float)q[2], (float)q[3]);
+        A.nd_fq1[i] = make_float2((float)q[4], (float)q[5]);
+    } else {
+        float q[6] = {0, 0, 0, 0, 0, 0};
+        if (leaf) {
+            for (uint32_t p = f; p < f + cnt; ++p) {
+                const float4 ph = A.pf_hi[p], pl = A.pf_lo[p];
+                const float m = ph.w;
+                const float dx = (ph.x - hx) + (pl.x - lx), dy = (ph.y - hy) + (pl.y - ly),
+                            dz = (ph.z - hz) + (pl.z - lz);
+                const float d2 = dx * dx + dy * dy + dz * dz;
+                q[0] += m * (3.0f * dx * dx - d2);
+                q[1] += m * (3.0f * dy * dy - d2);
+                q[2] += m * (3.0f * dz * dz - d2);
+                q[3] += m * (3.0f * dx * dy);
+                q[4] += m * (3.0f * dx * dz);
+                q[5] += m * (3.0f * dy * dz);
+            }
+        } else {
+            for (uint32_t c = c0; c < c0 + nc; ++c) {
+                const float4 ch = __ldcg(&A.nd_f[2 * c]), cl = __ldcg(&A.nd_f[2 * c + 1]);
+                const float4 q0 = __ldcg(&A.nd_fq0[c]);
+                const float2 q1 = __ldcg(&A.nd_fq1[c]);
+                const float dx = (ch.x - hx) + (cl.x - lx), dy = (ch.y - hy) + (cl.y - ly),
+                            dz = (ch.z - hz) + (cl.z - lz);
+                const float d2 = dx * dx + dy * dy + dz * dz;
+                const float m = ch.w;
+                q[0] += q0.x + m * (3.0f * dx * dx - d2);
+                q[1] += q0.y + m * (3.0f * dy * dy - d2);
+                q[2] += q0.z + m * (3.0f * dz * dz - d2);
+                q[3] += q0.w + m * (3.0f * dx * dy);
+                q[4] += q1.x + m * (3.0f * dx * dz);
+                q[5] += q1.y + m * (3.0f * dy * dz);
+            }
         }
+        A.nd_fq0[i] = make_float4(q[0], q[1], q[2], q[3]);
+        A.nd_fq1[i] = make_float2(q[4], q[5]);
     }
+}
+
+// Leaves (of every level) in one launch, then the internal nodes level by
+// level from the deepest up: each internal node finds its children complete.
+template <bool QUAD, bool Q64>
+__global__ void __launch_bounds__(256) k_moments_leaves(MomArgs A) {
+    const int64_t nn = A.st->n_nodes;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (meta_leaf(A.nd_meta[i])) node_moments<QUAD, Q64>(A, i);
+}
+
+template <bool QUAD, bool Q64>
+__global__ void __launch_bounds__(256) k_moments_internal(MomArgs A, int l) {
+    const int64_t a = A.st->lvl_start[l], b = A.st->lvl_start[l + 1];
+    for (int64_t i = a + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < b;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (!meta_leaf(A.nd_meta[i])) node_moments<QUAD, Q64>(A, i);
+}
+
+template <bool QUAD, bool Q64>
+int launch_moments(fdps_ctx* ctx, const MomArgs& A) {
+    const int grid = ctx->sm_count * 8;
+    k_moments_leaves<QUAD, Q64><<<grid, 256, 0, ctx->stream>>>(A);
+    FDPS_LAUNCH_CHECK(ctx);
+    for (int l = kMaxLevel - 1; l >= 0; --l) {
+        k_moments_internal<QUAD, Q64><<<grid, 256, 0, ctx->stream>>>(A, l);
+        FDPS_LAUNCH_CHECK(ctx);
+    }
+    return FDPS_OK;
 }
 
 // ------------------------------------------------------------- groups
@@ -533,21 +621,34 @@ int compute_moments(fdps_tree* t, fdps_psys* ps) {
     fdps_ctx* ctx = t->ctx;
     cudaStream_t s = ctx->stream;
     const int c = ps->cur;
-    const int grid = ctx->sm_count * 8;
-    for (int l = kMaxLevel; l >= 0; --l) {
-        if (t->p.moment == FDPS_QUADRUPOLE)
-            k_moments_level<true><<<grid, 256, 0, s>>>(
-                l, t->st, t->sys_box, ps->d_sys, ps->x[c], ps->y[c], ps->z[c], ps->m[c], t->nd_first, t->nd_count,
-                t->nd_child, t->nd_meta, t->nd_qlo, t->nd_sx, t->nd_sy, t->nd_sz, t->nd_com,
-                t->nd_quad, t->nd_f, t->nd_walk, t->nd_fq0, t->nd_fq1);
-        else
-            k_moments_level<false><<<grid, 256, 0, s>>>(
-                l, t->st, t->sys_box, ps->d_sys, ps->x[c], ps->y[c], ps->z[c], ps->m[c], t->nd_first, t->nd_count,
-                t->nd_child, t->nd_meta, t->nd_qlo, t->nd_sx, t->nd_sy, t->nd_sz, t->nd_com,
-                t->nd_quad, t->nd_f, t->nd_walk, t->nd_fq0, t->nd_fq1);
-        FDPS_LAUNCH_CHECK(ctx);
-    }
-    return FDPS_OK;
+    MomArgs A;
+    A.st = t->st;
+    A.box = t->sys_box;
+    A.sys = ps->d_sys;
+    A.px = ps->x[c];
+    A.py = ps->y[c];
+    A.pz = ps->z[c];
+    A.pm = ps->m[c];
+    A.pf_hi = t->pf_hi;
+    A.pf_lo = t->pf_lo;
+    A.nd_first = t->nd_first;
+    A.nd_count = t->nd_count;
+    A.nd_child = t->nd_child;
+    A.nd_meta = t->nd_meta;
+    A.nd_parent = t->nd_parent;
+    A.nd_qlo = t->nd_qlo;
+    A.nd_sx = t->nd_sx;
+    A.nd_sy = t->nd_sy;
+    A.nd_sz = t->nd_sz;
+    A.nd_com = t->nd_com;
+    A.nd_quad = t->nd_quad;
+    A.nd_f = t->nd_f;
+    A.nd_walk = t->nd_walk;
+    A.nd_fq0 = t->nd_fq0;
+    A.nd_fq1 = t->nd_fq1;
+    if (t->p.moment != FDPS_QUADRUPOLE) return launch_moments<false, false>(ctx, A);
+    if (t->p.precision == FDPS_FP64) return launch_moments<true, true>(ctx, A);
+    return launch_moments<true, false>(ctx, A);
 }
 
 int select_groups(fdps_tree* t, fdps_psys* ps) {

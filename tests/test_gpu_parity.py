@@ -123,8 +123,10 @@ def test_parity_with_oracle(G, ctx, name, model, n, theta, n_leaf, n_grp, quad):
             ref.n_groups, 400, replace=False)
         ng, nr = check_structure(G, tree, ref, n, sample)
         if quad:
-            np.testing.assert_allclose(ng["quad"], nr["quad"], rtol=1e-9,
-                                       atol=1e-12 * np.abs(nr["quad"]).max())
+            # FP32 quadrupoles in the FP32 pipeline: error relative to M ell^2
+            _, L, _ = tree.box()
+            scale = nr["mass"] * (L * 2.0 ** -nr["level"].astype(float)) ** 2
+            assert np.all(np.abs(ng["quad"] - nr["quad"]).max(1) <= 1e-5 * scale + 1e-300)
         _, _, acc, pot = ps.get()
         acc_r, pot_r, tot = ref.force()
         assert rms_rel(acc, acc_r) <= RMS_FP32
