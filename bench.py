@@ -60,6 +60,10 @@ def parse():
                     help="the ensemble workload: 4096 Plummer clusters, N log-uniform in "
                          "[256, 65536], eps = 1/(4 N^1/3), theta 0.5 monopole, dt 1/256")
     ap.add_argument("--n-sys", type=int, default=4096)
+    ap.add_argument("--suite", action="store_true",
+                    help="one JSON line per workload configuration: Plummer 2^20 (10 steps), "
+                         "Hernquist 2^24 at theta 0.3/0.5/0.7, clumpy 2^26; with force errors "
+                         "against the FP64 direct sum on a random subsample and energy drift")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep n_leaf / n_grp as given instead of the autotuner's choice")
     return ap.parse_args()
@@ -361,10 +365,14 @@ def run_ensemble(args):
     ctx.set_profiling(True)
     stream = torch.cuda.ExternalStream(ctx.stream)
     ps = G.ParticleSystem(ctx, n)
-    tree = G.Tree(ctx, theta=cfg["theta"], n_leaf=args.n_leaf if args.n_leaf != 16 else cfg["n_leaf"],
-                  n_grp=args.n_grp if args.n_grp != 128 else cfg["n_grp"])
+    tree = G.Tree(ctx, theta=cfg["theta"], n_leaf=cfg["n_leaf"], n_grp=cfg["n_grp"])
     ps.set_systems(off)
     ps.set(pos, vel, mass, eps)
+    tuned = None
+    if not args.no_autotune:
+        best, ms = tree.autotune(ps, n_leaf=(8, 16), n_grp=(32, 64, 128, 256), tile_depth=(256, 512),
+                                 repeats=1)
+        tuned = {**best, "force_ms": ms}
     tree.calc_force_all_and_write_back(ps)
     ek0, ep0 = ps.energy_systems()
     tree.run(ps, dt, args.warmup)
@@ -387,7 +395,8 @@ def run_ensemble(args):
     fp64 = None
     if not args.no_fp64:
         ps3 = G.ParticleSystem(ctx, n)
-        t64 = G.Tree(ctx, theta=cfg["theta"], n_leaf=cfg["n_leaf"], n_grp=cfg["n_grp"], fp64=True)
+        p64 = tuned or {"n_leaf": cfg["n_leaf"], "n_grp": cfg["n_grp"]}
+        t64 = G.Tree(ctx, theta=cfg["theta"], n_leaf=p64["n_leaf"], n_grp=p64["n_grp"], fp64=True)
         ps3.set_systems(off)
         ps3.set(pos, vel, mass, eps)
         t64.calc_force_all_and_write_back(ps3)
@@ -407,8 +416,8 @@ def run_ensemble(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"ensemble of {args.n_sys} Plummer clusters, N log-uniform "
                                    f"[256, 65536] (total {n}), theta {cfg['theta']} monopole, "
-                                   f"n_leaf {cfg['n_leaf']}, n_grp {cfg['n_grp']}, dt {dt}, "
-                                   "graph-captured steps", "l2": "inputs larger than L2"},
+                                   f"dt {dt}, graph-captured steps", "l2": "inputs larger than L2",
+                       "params": tuned or {"n_leaf": cfg["n_leaf"], "n_grp": cfg["n_grp"]}},
             "gpu_launches": launches, "clocks": clk,
             "interactions_per_s_estimate": inter * args.steps / t,
             "energy_drift": {"median": float(np.median(drift)), "p99": float(np.quantile(drift, 0.99)),
@@ -418,6 +427,92 @@ def run_ensemble(args):
     tree.close()
     ps.close()
     ctx.close()
+
+
+def run_config(G, torch, name, model, n, eps, theta, quad, n_leaf, n_grp, steps, dt, n_direct,
+               autotune, fp64_step, seed):
+    """One configuration: time `steps` graph-replayed KDK steps, force error of
+    the first force calculation against the FP64 direct sum on n_direct random
+    particles (oracle), relative energy drift over the run."""
+    import ics
+    import oracle
+    pos, vel, mass, e = ics.make(model, n, seed, eps)
+    ctx = G.Context(0)
+    ctx.set_profiling(True)
+    stream = torch.cuda.ExternalStream(ctx.stream)
+    ps = G.ParticleSystem(ctx, n)
+    tree = G.Tree(ctx, theta=theta, n_leaf=n_leaf, n_grp=n_grp, quad=quad)
+    ps.set(pos, vel, mass, e)
+    tuned = None
+    if autotune:
+        best, ms = tree.autotune(ps, n_leaf=(8, 16), n_grp=(64, 128, 256, 512), tile_depth=(256, 512),
+                                 repeats=1)
+        tuned = {**best, "force_ms": ms}
+    tree.calc_force_all_and_write_back(ps)
+    st0 = tree.stats()
+    _, _, acc, pot = ps.get()
+    idx = np.random.default_rng(seed).choice(n, n_direct, replace=False)
+    t0 = time.perf_counter()
+    ad, _ = oracle.direct(pos, mass, e, idx)
+    t_direct = time.perf_counter() - t0
+    err = np.linalg.norm(acc[idx] - ad, axis=1) / np.linalg.norm(ad, axis=1)
+    ek0, ep0 = ps.energy()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    tree.run(ps, dt, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    st = tree.stats()
+    ek1, ep1 = ps.energy()
+    inter = st0["interactions_epj"] + st0["interactions_spj"]
+    line = {"config": name, "workload": f"{model} N={n} theta={theta} {'quad' if quad else 'mono'} "
+                                        f"eps={eps} dt={dt:.6g}",
+            "params": tuned or {"n_leaf": n_leaf, "n_grp": n_grp},
+            "steps": steps, "ms_per_step": 1e3 * t / steps,
+            "interactions_per_step": inter, "interactions_per_s": inter * steps / t,
+            "force_ms_first_call": st0["ms_force"], "stages_ms_first_call":
+                {k: round(v, 3) for k, v in st0.items() if k.startswith("ms_")},
+            "force_error_vs_direct": {"n_sample": n_direct, "median": float(np.median(err)),
+                                      "rms": float(np.sqrt(np.mean(err ** 2))),
+                                      "p99": float(np.quantile(err, 0.99)),
+                                      "oracle_direct_s": round(t_direct, 1)},
+            "energy": {"E0": ek0 + ep0, "rel_drift": abs((ek1 + ep1) - (ek0 + ep0)) / abs(ek0 + ep0)},
+            "n_nodes": st0["n_nodes"], "n_groups": st0["n_groups"], "fp64_fallbacks": st0["fp64_fallbacks"]}
+    tree.close()
+    ps.close()
+    if fp64_step:
+        ps3 = G.ParticleSystem(ctx, n)
+        p = line["params"]
+        t64 = G.Tree(ctx, theta=theta, n_leaf=p["n_leaf"], n_grp=p["n_grp"], quad=quad, fp64=True)
+        ps3.set(pos, vel, mass, e)
+        t64.calc_force_all_and_write_back(ps3)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        t64.step(ps3, dt)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        line["fp64_ms_per_step"] = a0.elapsed_time(a1)
+        t64.close()
+        ps3.close()
+    ctx.close()
+    print(json.dumps(line), flush=True)
+
+
+def run_suite(args):
+    import torch
+    import ics
+    import paper_1601_03138_gb300 as G
+    from paper_1601_03138_gb300 import build as B
+    B.build()
+    S = ics.SEED_BASE
+    run_config(G, torch, "plummer1m", "plummer", 1 << 20, 1.0 / 64.0, 0.5, True, 16, 128, 10,
+               1.0 / 256.0, 4096, False, True, S + 2)
+    for th in (0.3, 0.5, 0.7):
+        run_config(G, torch, f"hernquist16m-theta{th}", "hernquist", 1 << 24, 0.005, th, True, 16, 128,
+                   20, 1.0 / 512.0, 1024, True, th == 0.5, S + 3)
+    run_config(G, torch, "clumpy64m", "clumpy", 1 << 26, 0.002, 0.5, True, 16, 128, 2, 1.0 / 512.0,
+               256, True, False, S + 4)
 
 
 def main():
@@ -431,6 +526,10 @@ def main():
     if args.ensemble:
         if rank == 0:
             run_ensemble(args)
+        return
+    if args.suite:
+        if rank == 0:
+            run_suite(args)
         return
     if world > 1:
         import torch
