@@ -135,6 +135,12 @@ int fdps_set_stream(fdps_ctx* ctx, void* stream);
 /* Number of CUDA kernels this library has launched on the context so far
    (-1 for NULL). */
 int64_t fdps_kernel_launches(const fdps_ctx* ctx);
+/* Diagnostic of the failure path of the library's one kind of device-side
+   wait (the radix sort's look-back on earlier tiles, bounded to about 2^20
+   polls): runs a single look-back whose predecessor never publishes.
+   Returns FDPS_ETIMEOUT when the wait gave up and reported it, as designed;
+   the context stays usable.  Any other result is a fault of the library. */
+int fdps_selftest_bounded_wait(fdps_ctx* ctx);
 /* Enable (1) / disable (0) per-stage CUDA-event timing in fdps_tree_stats. */
 int fdps_set_profiling(fdps_ctx* ctx, int on);
 

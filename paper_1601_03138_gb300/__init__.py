@@ -78,6 +78,7 @@ _PROTOS = {
     "fdps_set_stream": (C.c_int, [_vp, _vp]),
     "fdps_set_profiling": (C.c_int, [_vp, C.c_int]),
     "fdps_kernel_launches": (_i64, [_vp]),
+    "fdps_selftest_bounded_wait": (C.c_int, [_vp]),
     "fdps_psys_create": (C.c_int, [_vp, _i64, C.POINTER(_vp)]),
     "fdps_psys_destroy": (C.c_int, [_vp]),
     "fdps_psys_size": (_i64, [_vp]),
@@ -178,6 +179,11 @@ def fdps_set_stream(ctx, stream_ptr: int | None):
 
 def fdps_kernel_launches(ctx) -> int:
     return int(lib().fdps_kernel_launches(ctx))
+
+
+def fdps_selftest_bounded_wait(ctx) -> int:
+    """Status code of the bounded-wait self-test (FDPS_ETIMEOUT is the pass)."""
+    return int(lib().fdps_selftest_bounded_wait(ctx))
 
 
 def fdps_set_profiling(ctx, on: bool):

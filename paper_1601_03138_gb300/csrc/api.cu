@@ -230,6 +230,8 @@ int run_force(fdps_tree* t, fdps_psys* ps, int k_spj) {
     fdps_ctx* ctx = t->ctx;
     const int64_t n = ps->n;
     int rc;
+    if (n >= (int64_t(1) << 30))
+        return set_error(ctx, FDPS_EINVAL, "the tree handles fewer than 2^30 particles");
     if ((rc = ensure_particles(t, n))) return rc;
     if ((rc = ensure_systems(t, ps->n_sys))) return rc;
     const int64_t nl = t->p.n_leaf, ng = t->p.n_grp;
@@ -255,6 +257,8 @@ int run_force(fdps_tree* t, fdps_psys* ps, int k_spj) {
         record(t, 6);
         if ((rc = read_state(t))) return rc;
         const uint32_t ov = t->h_st.overflow;
+        if (ov & kSortStall)
+            return set_error(ctx, FDPS_ETIMEOUT, "a radix-sort look-back wait exceeded its bound");
         if (!(ov & (kOvfNodes | kOvfGroups))) break;
         if (attempt > 8)
             return set_error(ctx, FDPS_EOVERFLOW, "tree build did not fit after %d resizes", attempt);
@@ -353,6 +357,16 @@ int fdps_set_stream(fdps_ctx* ctx, void* stream) {
 }
 
 int64_t fdps_kernel_launches(const fdps_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+int fdps_selftest_bounded_wait(fdps_ctx* ctx) {
+    if (!ctx) return FDPS_EINVAL;
+    cudaSetDevice(ctx->device);
+    uint32_t flags = 0;
+    int rc = selftest_lookback_timeout(ctx, &flags);
+    if (rc) return rc;
+    if (flags & kSortStall) return set_error(ctx, FDPS_ETIMEOUT, "bounded wait gave up as designed");
+    return FDPS_OK;
+}
 
 int fdps_set_profiling(fdps_ctx* ctx, int on) {
     if (!ctx) return FDPS_EINVAL;
@@ -525,7 +539,7 @@ int fdps_tree_create(fdps_ctx* ctx, const fdps_tree_params* params, fdps_tree** 
     bool ok = dev_alloc(&t->st, 1) == cudaSuccess && dev_alloc(&t->box_part, t->box_blocks) == cudaSuccess &&
               dev_alloc(&t->lvl_scan, t->box_blocks) == cudaSuccess &&
               dev_alloc(&t->grp_scan, t->box_blocks) == cudaSuccess &&
-              dev_alloc(&t->sort_dtot, 256) == cudaSuccess;
+              dev_alloc(&t->sort_dtot, 4096) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         fdps_tree_destroy(t);
@@ -936,7 +950,7 @@ int fdps_run(fdps_tree* t, fdps_psys* ps, double dt, int64_t n_steps) {
     if ((rc = ensure_pool(t, (int64_t)(h.pool_needed * 3 / 2) + 2 * t->n_walk_warps * (int64_t)walk_chunk())))
         return rc;
     if ((rc = ensure_frontier(t, 2 * (int64_t)h.max_frontier + 1024))) return rc;
-    const uint32_t ovf_mask = kOvfNodes | kOvfGroups | kOvfPool | kOvfFrontier;
+    const uint32_t ovf_mask = kOvfNodes | kOvfGroups | kOvfPool | kOvfFrontier | kSortStall;
     // the particle buffers flip in every force calculation, so a step reads
     // buffer `cur` and leaves buffer 1 - cur: one graph for each parity
     cudaGraphExec_t exec[2] = {nullptr, nullptr};

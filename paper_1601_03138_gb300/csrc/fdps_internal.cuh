@@ -45,6 +45,7 @@ constexpr uint32_t kOvfFrontier = 4u;
 constexpr uint32_t kOvfGroups = 8u;
 constexpr uint32_t kBadInput = 16u;
 constexpr uint32_t kOvfChunk = 32u;
+constexpr uint32_t kSortStall = 64u;  // a radix-sort look-back wait gave up
 
 // Per-tree device-resident state written by the kernels of one force call.
 struct DevState {
@@ -145,7 +146,7 @@ struct fdps_tree {
     uint32_t* perm = nullptr;      // result of the sort (points into vals_*)
     uint64_t* keys_sorted = nullptr;
     uint32_t* sort_hist = nullptr; // [256][tiles]
-    uint32_t* sort_dtot = nullptr; // [256] digit totals
+    uint32_t* sort_dtot = nullptr; // [4096]: digit totals / bases of every pass, tile counters
     int64_t cap_tiles = 0;
     float4* pf_hi = nullptr;       // (x_hi, y_hi, z_hi, m) relative to c0
     float4* pf_lo = nullptr;       // (x_lo, y_lo, z_lo, eps^2)
@@ -267,6 +268,7 @@ int keys_and_sort(fdps_tree* t, fdps_psys* ps);        // keys_sort.cu
 int launch_sys_index(fdps_psys* ps);                   // integrate.cu
 int launch_energy_systems(fdps_psys* ps, double* kin, double* pot);  // integrate.cu
 int reorder_particles(fdps_tree* t, fdps_psys* ps);    // keys_sort.cu
+int selftest_lookback_timeout(fdps_ctx* ctx, uint32_t* flags_out);  // keys_sort.cu
 int build_tree(fdps_tree* t, fdps_psys* ps);           // build.cu
 int compute_moments(fdps_tree* t, fdps_psys* ps);      // build.cu
 int select_groups(fdps_tree* t, fdps_psys* ps);        // build.cu

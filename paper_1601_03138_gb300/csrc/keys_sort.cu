@@ -6,9 +6,12 @@
 //   key   q_a = min(2^21 - 1, floor((x_a - lo_a) * s)) with the subtraction
 //         and the product each rounded to nearest in FP64 (no FMA), then
 //         bits of q_x / q_y / q_z interleaved to key bits 3b+2 / 3b+1 / 3b
-//   sort  stable by key: 8 LSD passes of 8-bit digits, each pass
-//         reduce-then-scan (tile histograms, a scan, a stable scatter).
-// The first pass's tile histograms are produced by the key kernel itself.
+//   sort  stable by key: 8 LSD passes of 8-bit digits.  The force pipeline
+//         takes the digit counts of all passes while it computes the keys,
+//         then runs one kernel per pass (tile ranking, a bounded look-back
+//         over earlier tiles for the global offsets, a staged scatter).
+//         The allocation-free entry point keeps the reduce-then-scan form
+//         (tile histograms, a scan, a stable scatter).
 #include "fdps_internal.cuh"
 
 namespace fdps {
@@ -238,28 +241,6 @@ __global__ void __launch_bounds__(kSortBlock) k_radix_hist(int64_t n, const uint
     hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = c;
 }
 
-// Tile histograms of the digit `shift` of the system id of each pair's
-// particle (the passes that make the sort segmented by system).
-__global__ void __launch_bounds__(kSortBlock) k_radix_hist_sys(int64_t n, const uint32_t* __restrict__ vals,
-                                                               const uint32_t* __restrict__ sys, int shift,
-                                                               uint32_t* __restrict__ hist, int ntiles) {
-    __shared__ uint32_t h[kSortWarps][kRadix];
-    for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortBlock) (&h[0][0])[i] = 0;
-    __syncthreads();
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t base = (int64_t)blockIdx.x * kSortTile + w * (32 * kSortKPT);
-#pragma unroll
-    for (int r = 0; r < kSortKPT; ++r) {
-        int64_t i = base + r * 32 + lane;
-        if (i < n) atomicAdd(&h[w][(sys[vals[i]] >> shift) & 0xFF], 1u);
-    }
-    __syncthreads();
-    uint32_t c = 0;
-#pragma unroll
-    for (int k = 0; k < kSortWarps; ++k) c += h[k][threadIdx.x];
-    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = c;
-}
-
 // Exclusive block scan of one value per thread (blockDim.x <= 1024); the
 // block total is kept apart from the 32 per-warp offsets.
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total) {
@@ -399,6 +380,261 @@ __global__ void __launch_bounds__(kSortBlock) k_radix_scatter(
     }
 }
 
+// ---------------------------------------------- single-pass radix passes
+//
+// The force pipeline sorts with one kernel per digit pass: the digit
+// histograms of every pass are taken up front (they do not depend on the
+// order), and within a pass each 2048-key tile learns where its keys go by
+// looking back over the tiles before it ("decoupled look-back": every tile
+// publishes its per-digit count, then its inclusive prefix once known).
+// Tiles take their index in the order they start, so a tile only ever
+// waits on tiles already running; every wait is bounded and gives up with
+// an error flag instead of spinning on.
+
+constexpr uint32_t kFlagAgg = 1u << 30;   // tile count published
+constexpr uint32_t kFlagInc = 1u << 31;   // inclusive prefix published
+constexpr uint32_t kValMask = kFlagAgg - 1u;
+constexpr int kMaxSpin = 1 << 20;
+constexpr int kHistBlocks = 608;
+
+// Morton keys (as k_keys) plus the histograms of all digit passes: hist
+// [pass][256] with passes 0..7 the key bytes and, for several systems,
+// passes 8, 9 the two low bytes of the system id.
+__global__ void __launch_bounds__(kSortBlock) k_keys_hist(int64_t n, const double* __restrict__ x,
+                                                          const double* __restrict__ y,
+                                                          const double* __restrict__ z,
+                                                          const SysBox* __restrict__ box,
+                                                          const uint32_t* __restrict__ sys,
+                                                          uint64_t* __restrict__ keys,
+                                                          uint32_t* __restrict__ hist) {
+    __shared__ uint32_t h[10][kRadix];
+    for (int i = threadIdx.x; i < 10 * kRadix; i += kSortBlock) (&h[0][0])[i] = 0;
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t sid = sys ? sys[i] : 0u;
+        const SysBox& b = box[sid];
+        const uint32_t qx = quantise(x[i], b.lo[0], b.s), qy = quantise(y[i], b.lo[1], b.s),
+                       qz = quantise(z[i], b.lo[2], b.s);
+        const uint64_t k = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+        keys[i] = k;
+#pragma unroll
+        for (int p = 0; p < 8; ++p) atomicAdd(&h[p][(k >> (8 * p)) & 0xFF], 1u);
+        if (sys) {
+            atomicAdd(&h[8][sid & 0xFF], 1u);
+            atomicAdd(&h[9][(sid >> 8) & 0xFF], 1u);
+        }
+    }
+    __syncthreads();
+    const int np = sys ? 10 : 8;
+    for (int i = threadIdx.x; i < np * kRadix; i += kSortBlock) {
+        const uint32_t c = (&h[0][0])[i];
+        if (c) atomicAdd(&hist[i], c);
+    }
+}
+
+// Exclusive scan of each pass's 256 digit counts: block p scans pass p.
+__global__ void __launch_bounds__(kRadix) k_digit_bases(uint32_t* hist) {
+    uint32_t* row = hist + blockIdx.x * kRadix;
+    const uint32_t v = row[threadIdx.x];
+    row[threadIdx.x] = block_excl_scan(v, nullptr);
+}
+
+// Tile shape of the single-pass kernel and the look-back window: each
+// look-back step reads the statuses of kLook earlier tiles at once.
+constexpr int kOsBlock = 256;
+constexpr int kOsKPT = 12;
+constexpr int kOsTile = kOsBlock * kOsKPT;
+constexpr int kOsMinBlocks = 3;
+constexpr int kLook = 8;
+// the look-back status buffer is sized for tiles of at least 2048 keys
+static_assert(kOsTile >= 2048, "status rows sized for 2048-key tiles");
+
+constexpr uint32_t kFlags = kFlagInc | kFlagAgg;
+// Warp ranking by one match instruction per key (else eight ballots).
+constexpr bool kRankMatch = false;
+
+// One tile of one pass.  FULL tiles hold kOsTile keys and skip every bound
+// check; the last tile of a pass may be ragged.  Indices fit in 32 bits
+// (the tree takes fewer than 2^30 particles).
+template <bool SYSKEY, bool FULL>
+__device__ __forceinline__ void onesweep_tile(
+    const int n, const int tile, const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+    uint64_t* __restrict__ kout, uint32_t* __restrict__ vout, const int shift,
+    const uint32_t* __restrict__ dbase, volatile uint32_t* st, const uint32_t* __restrict__ sys,
+    uint32_t* err, uint64_t* sk, uint32_t* sv, uint8_t* sd, uint32_t (*wcnt)[kRadix], uint32_t* tstart,
+    uint32_t* gdelta) {
+    constexpr int kWarps = kOsBlock / 32;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const int tile0 = tile * kOsTile;
+    const int nv = FULL ? kOsTile : min(n - tile0, kOsTile);  // keys in this tile
+    const int wb = w * (32 * kOsKPT);                         // the warp's first key
+    // all loads of the tile first, so they are in flight together
+    uint64_t mk[kOsKPT];
+    uint32_t mv[kOsKPT], mr[kOsKPT];
+#pragma unroll
+    for (int r = 0; r < kOsKPT; ++r) {
+        const int o = wb + r * 32 + lane;
+        const bool ok = FULL || o < nv;
+        mk[r] = ok ? kin[tile0 + o] : 0ull;
+        mv[r] = ok ? (vin ? vin[tile0 + o] : (uint32_t)(tile0 + o)) : 0u;
+    }
+    uint32_t md[SYSKEY ? kOsKPT : 1];
+    if (SYSKEY) {
+#pragma unroll
+        for (int r = 0; r < kOsKPT; ++r)
+            md[r] = (FULL || wb + r * 32 + lane < nv) ? (sys[mv[r]] >> shift) & 0xFFu : 0u;
+    }
+    auto digit = [&](int r) -> uint32_t {
+        return SYSKEY ? md[r] : (uint32_t)(mk[r] >> shift) & 0xFFu;
+    };
+    // lanes holding the same digit; invalid lanes get an empty mask
+#pragma unroll
+    for (int r = 0; r < kOsKPT; ++r) {
+        const bool ok = FULL || wb + r * 32 + lane < nv;
+        const uint32_t d = digit(r);
+        uint32_t peers;
+        if (kRankMatch) {
+            peers = __match_any_sync(0xFFFFFFFFu, ok ? d : 0x100u);
+        } else {
+            peers = FULL ? 0xFFFFFFFFu : __ballot_sync(0xFFFFFFFFu, ok);
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const uint32_t bb = __ballot_sync(0xFFFFFFFFu, (d >> b) & 1u);
+                peers &= ((d >> b) & 1u) ? bb : ~bb;
+            }
+        }
+        mr[r] = ok ? peers : 0u;
+    }
+    // running per-warp digit counts, in key order: the first lane of each
+    // digit group reads and advances the counter, the group takes its base
+#pragma unroll
+    for (int r = 0; r < kOsKPT; ++r) {
+        const uint32_t peers = mr[r], d = digit(r);
+        const uint32_t rank = __popc(peers & lt_mask);
+        uint32_t b0 = 0;
+        if (peers && rank == 0) {
+            b0 = wcnt[w][d];
+            wcnt[w][d] = b0 + __popc(peers);
+        }
+        __syncwarp();
+        b0 = __shfl_sync(0xFFFFFFFFu, b0, (__ffs(peers) - 1) & 31);
+        mr[r] = b0 + rank;
+    }
+    __syncthreads();
+    // threads below kRadix own one digit each from here to the scatter
+    const int d = threadIdx.x;
+    uint32_t run = 0;
+    if (d < kRadix) {
+#pragma unroll
+        for (int k = 0; k < kWarps; ++k) {
+            const uint32_t c = wcnt[k][d];
+            wcnt[k][d] = run;
+            run += c;
+        }
+        // publish this tile's count at once, so later tiles can look past it
+        st[(size_t)tile * kRadix + d] = (tile == 0 ? kFlagInc : kFlagAgg) | run;
+    }
+    const uint32_t ts = block_excl_scan(run, nullptr);
+    if (d < kRadix) tstart[d] = ts;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kOsKPT; ++r) {
+        if (FULL || wb + r * 32 + lane < nv) {
+            const uint32_t dd = digit(r);
+            const uint32_t p = tstart[dd] + wcnt[w][dd] + mr[r];
+            sk[p] = mk[r];
+            sv[p] = mv[r];
+            if (SYSKEY) sd[p] = (uint8_t)dd;
+        }
+    }
+    // look back over the tiles before this one for the keys of digit d:
+    // add published counts, newest first, until an inclusive prefix.  A
+    // window of kLook statuses is read at once; a tile not yet published
+    // is waited on alone, within a bound.
+    if (d < kRadix) {
+        uint32_t excl = 0;
+        if (tile > 0) {
+            int j = tile - 1;
+            int spins = 0;
+            for (;;) {
+                uint32_t v[kLook];
+#pragma unroll
+                for (int q = 0; q < kLook; ++q) {
+                    // before tile 0: an inclusive prefix of zero
+                    uint32_t x = kFlagInc;
+                    if (j - q >= 0) x = st[(size_t)(j - q) * kRadix + d];
+                    v[q] = x;
+                }
+                int adv = 0;
+                bool done = false;
+#pragma unroll
+                for (int q = 0; q < kLook; ++q) {
+                    if (!done && adv == q && (v[q] & kFlags)) {
+                        excl += v[q] & kValMask;
+                        if (v[q] & kFlagInc) done = true;
+                        else adv = q + 1;
+                    }
+                }
+                if (done) break;
+                j -= adv;
+                if (adv == 0) {
+                    uint32_t x;
+                    while (!((x = st[(size_t)j * kRadix + d]) & kFlags) && spins <= kMaxSpin) {
+                        ++spins;
+                        __nanosleep(64);
+                    }
+                    if (spins > kMaxSpin) {
+                        atomicOr(err, kSortStall);
+                        break;
+                    }
+                    excl += x & kValMask;
+                    if (x & kFlagInc) break;
+                    --j;
+                }
+            }
+            st[(size_t)tile * kRadix + d] = kFlagInc | (excl + run);
+        }
+        gdelta[d] = dbase[d] + excl - ts;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int p = threadIdx.x; p < nv; p += kOsBlock) {
+        const uint64_t k = sk[p];
+        const uint32_t dd = SYSKEY ? (uint32_t)sd[p] : (uint32_t)(k >> shift) & 0xFFu;
+        const uint32_t dst = gdelta[dd] + (uint32_t)p;
+        kout[dst] = k;
+        vout[dst] = sv[p];
+    }
+}
+
+template <bool SYSKEY>
+__global__ void __launch_bounds__(kOsBlock, kOsMinBlocks) k_onesweep(
+    int64_t n, const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+    uint64_t* __restrict__ kout, uint32_t* __restrict__ vout, int shift,
+    const uint32_t* __restrict__ dbase, uint32_t* status, uint32_t* tile_ctr,
+    const uint32_t* __restrict__ sys, uint32_t* err) {
+    constexpr int kWarps = kOsBlock / 32;
+    __shared__ uint64_t sk[kOsTile];
+    __shared__ uint32_t sv[kOsTile];
+    __shared__ uint8_t sd[SYSKEY ? kOsTile : 1];
+    __shared__ uint32_t wcnt[kWarps][kRadix];
+    __shared__ uint32_t tstart[kRadix];
+    __shared__ uint32_t gdelta[kRadix];
+    __shared__ uint32_t s_tile;
+    if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
+    for (int i = threadIdx.x; i < kWarps * kRadix; i += kOsBlock) (&wcnt[0][0])[i] = 0;
+    __syncthreads();
+    const int tile = (int)s_tile;
+    if ((int64_t)(tile + 1) * kOsTile <= n)
+        onesweep_tile<SYSKEY, true>((int)n, tile, kin, vin, kout, vout, shift, dbase, status, sys, err, sk, sv,
+                                    sd, wcnt, tstart, gdelta);
+    else
+        onesweep_tile<SYSKEY, false>((int)n, tile, kin, vin, kout, vout, shift, dbase, status, sys, err, sk,
+                                     sv, sd, wcnt, tstart, gdelta);
+}
+
 // Reorder the particle system into key order and write the FP32 hi/lo
 // copies relative to the root centre used by the walk and force kernels.
 __global__ void __launch_bounds__(256) k_reorder(
@@ -442,7 +678,7 @@ int keys_and_sort(fdps_tree* t, fdps_psys* ps) {
     cudaStream_t s = ctx->stream;
     const int64_t n = ps->n;
     const int c = ps->cur;
-    const int ntiles = (int)((n + kSortTile - 1) / kSortTile);
+    const int ntiles = (int)((n + kOsTile - 1) / kOsTile);
     if (ps->n_sys == 1) {
         k_box_partial<<<t->box_blocks, 256, 0, s>>>(n, ps->x[c], ps->y[c], ps->z[c], t->box_part);
         FDPS_LAUNCH_CHECK(ctx);
@@ -452,35 +688,37 @@ int keys_and_sort(fdps_tree* t, fdps_psys* ps) {
         k_box_seg<<<ps->n_sys, 256, 0, s>>>(ps->d_off, ps->x[c], ps->y[c], ps->z[c], t->sys_box);
         FDPS_LAUNCH_CHECK(ctx);
     }
-    k_keys<<<ntiles, kSortBlock, 0, s>>>(n, ps->x[c], ps->y[c], ps->z[c], t->sys_box, ps->d_sys,
-                                         t->keys_in, t->sort_hist, ntiles);
+    // 8 passes over the key; with several systems 2 more, stable, over the
+    // system id, so each system's particles end in its own segment in key order
+    const int npass = ps->n_sys == 1 ? 8 : 10;
+    uint32_t* hist = t->sort_dtot;          // [pass][256] counts, then bases
+    uint32_t* tile_ctr = t->sort_dtot + 3072;
+    FDPS_CUDA_TRY(ctx, cudaMemsetAsync(t->sort_dtot, 0, sizeof(uint32_t) * 4096, s));
+    k_keys_hist<<<kHistBlocks, kSortBlock, 0, s>>>(n, ps->x[c], ps->y[c], ps->z[c], t->sys_box, ps->d_sys,
+                                                   t->keys_in, hist);
+    FDPS_LAUNCH_CHECK(ctx);
+    k_digit_bases<<<npass, kRadix, 0, s>>>(hist);
     FDPS_LAUNCH_CHECK(ctx);
     if (t->ev_ok && ctx->profiling && !ctx->capturing) cudaEventRecord(t->ev[1], s);
     const uint64_t* kin = t->keys_in;
     const uint32_t* vin = nullptr;
     uint64_t* kb[2] = {t->keys_a, t->keys_b};
     uint32_t* vb[2] = {t->vals_a, t->vals_b};
-    // 8 passes over the key; with several systems 2 more, stable, over the
-    // system id, so each system's particles end in its own segment in key order
-    const int npass = ps->n_sys == 1 ? 8 : 10;
+    uint32_t* status = t->sort_hist;  // [tile][256] look-back words of the pass
     for (int pass = 0; pass < npass; ++pass) {
         const bool by_sys = pass >= 8;
         const int shift = by_sys ? 8 * (pass - 8) : 8 * pass;
-        if (pass > 0) {
-            if (by_sys)
-                k_radix_hist_sys<<<ntiles, kSortBlock, 0, s>>>(n, vin, ps->d_sys, shift, t->sort_hist, ntiles);
-            else
-                k_radix_hist<<<ntiles, kSortBlock, 0, s>>>(n, kin, shift, t->sort_hist, ntiles);
-            FDPS_LAUNCH_CHECK(ctx);
-        }
-        k_radix_scan_rows<<<kRadix, 1024, 0, s>>>(t->sort_hist, ntiles, t->sort_dtot);
-        FDPS_LAUNCH_CHECK(ctx);
-        k_radix_scan_digits<<<1, kRadix, 0, s>>>(t->sort_dtot);
-        FDPS_LAUNCH_CHECK(ctx);
+        FDPS_CUDA_TRY(ctx, cudaMemsetAsync(status, 0, sizeof(uint32_t) * kRadix * (size_t)ntiles, s));
         uint64_t* ko = kb[pass & 1];
         uint32_t* vo = vb[pass & 1];
-        k_radix_scatter<<<ntiles, kSortBlock, 0, s>>>(n, kin, vin, ko, vo, shift, t->sort_hist,
-                                                      t->sort_dtot, ntiles, by_sys ? ps->d_sys : nullptr);
+        if (by_sys)
+            k_onesweep<true><<<ntiles, kOsBlock, 0, s>>>(n, kin, vin, ko, vo, shift, hist + pass * kRadix,
+                                                           status, tile_ctr + pass, ps->d_sys,
+                                                           &t->st->overflow);
+        else
+            k_onesweep<false><<<ntiles, kOsBlock, 0, s>>>(n, kin, vin, ko, vo, shift, hist + pass * kRadix,
+                                                            status, tile_ctr + pass, nullptr,
+                                                            &t->st->overflow);
         FDPS_LAUNCH_CHECK(ctx);
         kin = ko;
         vin = vo;
@@ -488,6 +726,45 @@ int keys_and_sort(fdps_tree* t, fdps_psys* ps) {
     t->keys_sorted = kb[1];
     t->perm = vb[1];
     return FDPS_OK;
+}
+
+// One look-back whose predecessor tile never publishes: the tile counter
+// starts at 1, so the single block takes tile 1 and waits on tile 0 until
+// its bound runs out.  Every access stays inside the 2-tile buffers.
+int selftest_lookback_timeout(fdps_ctx* ctx, uint32_t* flags_out) {
+    const int64_t n = 2 * kOsTile;
+    uint64_t* keys = nullptr;
+    unsigned char* raw = nullptr;
+    const size_t bytes = sizeof(uint64_t) * 2 * n + sizeof(uint32_t) * (2 * n + 2 * kRadix + kRadix + 2);
+    if (cudaMalloc(&raw, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ctx, FDPS_ENOMEM, "self-test allocation failed");
+    }
+    keys = reinterpret_cast<uint64_t*>(raw);
+    uint64_t* kout = keys + n;
+    uint32_t* vout = reinterpret_cast<uint32_t*>(kout + n);
+    uint32_t* status = vout + n;            // 2 tiles x 256
+    uint32_t* dbase = status + 2 * kRadix;  // 256
+    uint32_t* ctr = dbase + kRadix;
+    uint32_t* err = ctr + 1;
+    cudaStream_t s = ctx->stream;
+    int rc = FDPS_OK;
+    const uint32_t one = 1u;
+    if (cudaMemsetAsync(raw, 0, bytes, s) != cudaSuccess ||
+        cudaMemcpyAsync(ctr, &one, sizeof(one), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        rc = set_error(ctx, FDPS_ECUDA, "self-test set-up failed");
+    if (!rc) {
+        k_onesweep<false><<<1, kOsBlock, 0, s>>>(n, keys, nullptr, kout, vout, 0, dbase, status, ctr,
+                                                   nullptr, err);
+        if (cudaGetLastError() != cudaSuccess) rc = set_error(ctx, FDPS_ECUDA, "self-test launch failed");
+    }
+    uint32_t h = 0;
+    if (!rc && (cudaMemcpyAsync(&h, err, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess))
+        rc = set_error(ctx, FDPS_ECUDA, "self-test readback failed");
+    cudaFree(raw);
+    *flags_out = h;
+    return rc;
 }
 
 int reorder_particles(fdps_tree* t, fdps_psys* ps) {
