@@ -81,17 +81,28 @@ __global__ void __launch_bounds__(256) k_box_partial(int64_t n, const double* __
     }
 }
 
+// One warp: lanes reduce strided subsets of the block partials, then the
+// lanes' results are combined by shuffles.
 __global__ void k_box_final(int nparts, const BoxPartial* __restrict__ part, DevState* st,
                             SysBox* box) {
-    if (threadIdx.x != 0) return;
     unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
-    for (int b = 0; b < nparts; ++b)
+    for (int b = threadIdx.x; b < nparts; b += 32)
         for (int a = 0; a < 3; ++a) {
             unsigned long long l = (unsigned long long)__double_as_longlong(part[b].lo[a]);
             unsigned long long h = (unsigned long long)__double_as_longlong(part[b].hi[a]);
             lo[a] = l < lo[a] ? l : lo[a];
             hi[a] = h > hi[a] ? h : hi[a];
         }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const unsigned long long l = __shfl_xor_sync(0xFFFFFFFFu, lo[a], off);
+            const unsigned long long h = __shfl_xor_sync(0xFFFFFFFFu, hi[a], off);
+            lo[a] = l < lo[a] ? l : lo[a];
+            hi[a] = h > hi[a] ? h : hi[a];
+        }
+    if (threadIdx.x != 0) return;
     double L = 0.0;
     for (int a = 0; a < 3; ++a) {
         double l = unord64(lo[a]), h = unord64(hi[a]);
@@ -169,12 +180,11 @@ __global__ void __launch_bounds__(256) k_box_seg(const int64_t* __restrict__ off
 }
 
 __device__ __forceinline__ uint32_t quantise(double x, double lo, double s) {
-    double t = __dsub_rn(x, lo);
-    double u = __dmul_rn(t, s);
-    double f = floor(u);
-    f = f > (double)kQMax ? (double)kQMax : f;
-    f = f < 0.0 ? 0.0 : f;
-    return (uint32_t)f;
+    const double u = __dmul_rn(__dsub_rn(x, lo), s);
+    // floor as a conversion rounding down (saturating), then the clamp in
+    // integers: the same value as flooring and clamping in FP64
+    const int f = __double2int_rd(u);
+    return (uint32_t)min(max(f, 0), (int)kQMax);
 }
 
 // Spread the low 21 bits of v to every third bit (bit b -> bit 3b).
