@@ -329,7 +329,8 @@ __device__ __forceinline__ void node_moments(const MomArgs& A, int64_t i) {
     A.nd_f[2 * i] = make_float4(hx, hy, hz, __double2float_rn(M));
     A.nd_f[2 * i + 1] = make_float4(lx, ly, lz, 0.0f);
     const uint64_t qlo = A.nd_qlo[i];
-    A.nd_walk[i] = make_uint4((uint32_t)qlo, (uint32_t)(qlo >> 32), c0, meta);
+    // third word: first child of an internal node, particle count of a leaf
+    A.nd_walk[i] = make_uint4((uint32_t)qlo, (uint32_t)(qlo >> 32), leaf ? cnt : c0, meta);
     if (!QUAD) return;
     if (Q64) {
         double q[6] = {0, 0, 0, 0, 0, 0};

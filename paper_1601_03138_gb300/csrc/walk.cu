@@ -30,7 +30,7 @@ namespace fdps {
 struct WalkArgs {
     DevState* st;
     const uint32_t* nd_count;
-    const uint4* nd_walk;  // (grid origin low, high, first child, meta) per node
+    const uint4* nd_walk;  // (grid origin low, high, first child | leaf count, meta) per node
     const float4* nd_f;    // COM hi/lo pairs per node
     const dvec4* nd_com;
     const uint32_t* g_count;
@@ -123,18 +123,27 @@ __global__ void __launch_bounds__(kWalkBlock, 8) k_walk(WalkArgs A) {
         while (fsize > 0) {
             uint32_t nsize = 0;
             max_front = fsize > max_front ? fsize : max_front;
-            // the first batch's frontier entries and node records; every batch
-            // then fetches the next one's before testing its own
+            // the first batch's frontier entries, node records and COM pairs;
+            // every batch then fetches the next one's before testing its own
             uint32_t node_nx = lane < fsize ? fa[lane] : 0u;
-            uint4 rec_nx = lane < fsize ? A.nd_walk[node_nx] : make_uint4(0, 0, 0, 0);
+            uint4 rec_nx = make_uint4(0, 0, 0, 0);
+            float4 fh_nx = make_float4(0.f, 0.f, 0.f, 0.f), fl_nx = fh_nx;
+            if (lane < fsize) {
+                rec_nx = A.nd_walk[node_nx];
+                fh_nx = A.nd_f[2 * node_nx];
+                fl_nx = A.nd_f[2 * node_nx + 1];
+            }
             for (uint32_t base = 0; base < fsize; base += 32) {
                 const uint32_t idx = base + lane;
                 const bool act = idx < fsize;
                 const uint32_t node = node_nx;
                 const uint4 rec = rec_nx;
+                const float4 fh = fh_nx, fl = fl_nx;
                 if (idx + 32 < fsize) {
                     node_nx = fa[idx + 32];
                     rec_nx = A.nd_walk[node_nx];
+                    fh_nx = A.nd_f[2 * node_nx];
+                    fl_nx = A.nd_f[2 * node_nx + 1];
                 }
                 int action = 0;  // 1 SPJ, 2 EPJ leaf, 3 open internal
                 uint32_t nch = 0, child = 0;
@@ -151,7 +160,6 @@ __global__ void __launch_bounds__(kWalkBlock, 8) k_walk(WalkArgs A) {
                                        qy + w >= qmin1 && qz <= qmax2 && qz + w >= qmin2;
                     bool open = true;
                     if (!meets) {
-                        const float4 fh = A.nd_f[2 * node], fl = A.nd_f[2 * node + 1];
                         const float dx = (fh.x - gch.x) + (fl.x - gcl.x);
                         const float dy = (fh.y - gch.y) + (fl.y - gcl.y);
                         const float dz = (fh.z - gch.z) + (fl.z - gcl.z);
@@ -183,7 +191,7 @@ __global__ void __launch_bounds__(kWalkBlock, 8) k_walk(WalkArgs A) {
                         action = 1;
                     } else if (leaf) {
                         action = 2;
-                        nepj_lane += A.nd_count[node];
+                        nepj_lane += rec.z;  // the leaf's particle count
                     } else {
                         action = 3;
                         child = rec.z;
