@@ -14,8 +14,10 @@
 // FP32-relative kernel (one CTA per i-group): list entries are gathered
 // into shared memory as FP32 coordinates relative to the group centre,
 // formed from FP32 hi/lo pairs so that near pairs keep full FP32 precision.
-// The pair loop takes two list entries per step with packed two-lane FP32
-// instructions plus two MUFU rsqrt; each thread accumulates one chunk of
+// A thread's i-particles are paired: the pair loop evaluates one list entry
+// against two i-particles with packed two-lane FP32 instructions plus two
+// MUFU rsqrt (one i-particle per thread: plain FP32); each thread
+// accumulates one chunk of
 // the list in plain FP32 and adds the chunk's sum to its running total with
 // Kahan compensation.  Small groups split their list over several threads
 // per i-particle ("slices"), reduced in FP64 at the end.  The FP64 kernel
@@ -200,10 +202,10 @@ __device__ __forceinline__ void kahan_smem_add(float* s_k, int q, int c, float v
     *s = t;
 }
 
-// Two FP32 lanes in one 64-bit register (low = even list entry, high =
-// odd): each packed instruction evaluates one operation of the pair law
-// for two list entries, halving the instructions the scheduler issues per
-// interaction.  Each lane is rounded exactly as the scalar instruction.
+// Two FP32 lanes in one 64-bit register (low = i-particle 2h, high =
+// 2h+1): each packed instruction evaluates one operation of the pair law
+// for two interactions, halving the FP32 instructions the scheduler issues.
+// Each lane is rounded exactly as the scalar instruction.
 typedef unsigned long long f2;
 __device__ __forceinline__ f2 f2_pk(float lo, float hi) {
     f2 r;
@@ -244,51 +246,56 @@ __device__ __forceinline__ float f2_sum(f2 v) {
     return a + b;
 }
 
-// Shared-memory layouts, by pairs of list entries (2e, 2e+1):
-//   superparticles: floats [20] (quadrupole) or [8] (monopole) per pair,
-//     x0 x1 y0 y1 | z0 z1 -M0 -M1 | Qxx0 Qxx1 Qyy0 Qyy1 | Qzz0 Qzz1 Qxy0 Qxy1
-//     | Qxz0 Qxz1 Qyz0 Qyz1   (coordinates relative to the group centre)
-//   leaf particles: floats [8] per pair, x0 x1 y0 y1 | z0 z1 m0 m1.
-// An odd count is padded by one entry of zero mass and moments placed far
-// away (kFar), whose every contribution is an exact zero.
-constexpr float kFar = 1.0e18f;
+// Shared-memory layouts (coordinates relative to the group centre):
+//   superparticles: float4 (x, y, z, -M), float4 (Qxx, Qyy, Qzz, Qxy),
+//     float2 (Qxz, Qyz) in three arrays
+//   leaf particles: float4 (x, y, z, m).
+// A thread's i-particles are paired (2h, 2h+1) in the two lanes; each list
+// entry is broadcast to both lanes.
 template <bool QUAD>
-struct SpjW {
-    static constexpr int W = QUAD ? 20 : 8;
+struct SpjBuf {
+    float4* s0;
+    float4* s1;
+    float2* s2;
 };
+__device__ __forceinline__ f2 f2_bc(float v) { return f2_pk(v, v); }
 
 template <bool QUAD, int K, int EPT>
 __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf, uint32_t ni,
                                                 unsigned long long off, uint32_t len, float4 gch,
                                                 float4 gcl, int P, int nsl, uint32_t ib,
-                                                float4* s_j, float* sp, uint32_t* s_ef,
+                                                float4* s_j, SpjBuf<QUAD> sb, uint32_t* s_ef,
                                                 uint32_t* s_es, uint32_t* s_w, double* s_red,
                                                 float* s_k) {
-    constexpr int SW = SpjW<QUAD>::W;
+    constexpr int KP = K / 2;  // i-pairs (K = 1 takes the scalar path)
     const int t = threadIdx.x;
     const int ip = t % P, sl = t / P;
     const bool on = sl < nsl;
-    // i-particles, each coordinate broadcast to both lanes of a pair
-    f2 xi[K], yi[K], zi[K], e2[K];
+    float xi[K], yi[K], zi[K], e2[K];
     bool iv[K];
 #pragma unroll
     for (int q = 0; q < K; ++q) {
         const uint32_t i = ib + (uint32_t)(ip + q * P);
         iv[q] = on && i < ni;
-        float x = 0.f, y = 0.f, z = 0.f, e = 1.f;
+        xi[q] = yi[q] = zi[q] = 0.f;
+        e2[q] = 1.f;
         if (iv[q]) {
             const float4 h = A.pf_hi[gf + i], l = A.pf_lo[gf + i];
-            x = (h.x - gch.x) + (l.x - gcl.x);
-            y = (h.y - gch.y) + (l.y - gcl.y);
-            z = (h.z - gch.z) + (l.z - gcl.z);
-            e = l.w;
+            xi[q] = (h.x - gch.x) + (l.x - gcl.x);
+            yi[q] = (h.y - gch.y) + (l.y - gcl.y);
+            zi[q] = (h.z - gch.z) + (l.z - gcl.z);
+            e2[q] = l.w;
         }
-        xi[q] = f2_pk(x, x);
-        yi[q] = f2_pk(y, y);
-        zi[q] = f2_pk(z, z);
-        e2[q] = f2_pk(e, e);
     }
-    const f2 cm25 = f2_pk(-2.5f, -2.5f), cm05 = f2_pk(-0.5f, -0.5f);
+    f2 xp[KP > 0 ? KP : 1], yp[KP > 0 ? KP : 1], zp[KP > 0 ? KP : 1], ep[KP > 0 ? KP : 1];
+#pragma unroll
+    for (int h = 0; h < KP; ++h) {
+        xp[h] = f2_pk(xi[2 * h], xi[2 * h + 1]);
+        yp[h] = f2_pk(yi[2 * h], yi[2 * h + 1]);
+        zp[h] = f2_pk(zi[2 * h], zi[2 * h + 1]);
+        ep[h] = f2_pk(e2[2 * h], e2[2 * h + 1]);
+    }
+    const f2 cm25 = f2_bc(-2.5f), cm05 = f2_bc(-0.5f);
     const int kbeg = on ? sl : 0x3FFFFFFF;
 #pragma unroll
     for (int k = 0; k < 8 * K; ++k) s_k[k * kCB + t] = 0.0f;
@@ -321,20 +328,12 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
             if (spj) {
                 const uint32_t node = ent[r];
                 const float4 fh = A.nd_f[2 * node], fl = A.nd_f[2 * node + 1];
-                float* d = sp + (rs >> 1) * SW + (rs & 1);
-                d[0] = (fh.x - gch.x) + (fl.x - gcl.x);
-                d[2] = (fh.y - gch.y) + (fl.y - gcl.y);
-                d[4] = (fh.z - gch.z) + (fl.z - gcl.z);
-                d[6] = -fh.w;
+                sb.s0[rs] = make_float4((fh.x - gch.x) + (fl.x - gcl.x),
+                                        (fh.y - gch.y) + (fl.y - gcl.y),
+                                        (fh.z - gch.z) + (fl.z - gcl.z), -fh.w);
                 if (QUAD) {
-                    const float4 q0 = A.nd_fq0[node];  // Qxx Qyy Qzz Qxy
-                    const float2 q1 = A.nd_fq1[node];  // Qxz Qyz
-                    d[8] = q0.x;
-                    d[10] = q0.y;
-                    d[12] = q0.z;
-                    d[14] = q0.w;
-                    d[16] = q1.x;
-                    d[18] = q1.y;
+                    sb.s1[rs] = A.nd_fq0[node];
+                    sb.s2[rs] = A.nd_fq1[node];
                 }
                 ++rs;
             }
@@ -342,109 +341,152 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
             s_es[t * EPT + r] = es;
             es += lcnt[r];
         }
-        if (t == 0 && (ns & 1u)) {
-            float* d = sp + (ns >> 1) * SW + 1;
-#pragma unroll
-            for (int c = 0; c < SW; c += 2) d[c] = c < 6 ? kFar : 0.0f;
-        }
         __syncthreads();
-        f2 pax[K], pay[K], paz[K], pp[K];
+        float sax[K], say[K], saz[K], spp[K];  // scalar path (K = 1)
+        f2 pax[KP > 0 ? KP : 1], pay[KP > 0 ? KP : 1], paz[KP > 0 ? KP : 1], pp[KP > 0 ? KP : 1];
 #pragma unroll
-        for (int q = 0; q < K; ++q) pax[q] = pay[q] = paz[q] = pp[q] = 0ull;
-        // ---- superparticles of this chunk, two per step
-        const int nsp = (int)((ns + 1u) >> 1);
+        for (int q = 0; q < K; ++q) sax[q] = say[q] = saz[q] = spp[q] = 0.f;
+#pragma unroll
+        for (int h = 0; h < KP; ++h) pax[h] = pay[h] = paz[h] = pp[h] = 0ull;
+        // ---- superparticles of this chunk
 #pragma unroll 2
-        for (int k = kbeg; k < nsp; k += nsl) {
-            const float4* e4 = reinterpret_cast<const float4*>(sp + k * SW);
-            const float4 v0 = e4[0], v1 = e4[1];
-            const f2 jx = f2_pk(v0.x, v0.y), jy = f2_pk(v0.z, v0.w), jz = f2_pk(v1.x, v1.y),
-                     nM = f2_pk(v1.z, v1.w);
-            f2 qxx, qyy, qzz, qxy, qxz, qyz;
+        for (int k = kbeg; k < (int)ns; k += nsl) {
+            const float4 a = sb.s0[k];
+            float4 q0;
+            float2 q1;
             if (QUAD) {
-                const float4 v2 = e4[2], v3 = e4[3], v4 = e4[4];
-                qxx = f2_pk(v2.x, v2.y);
-                qyy = f2_pk(v2.z, v2.w);
-                qzz = f2_pk(v3.x, v3.y);
-                qxy = f2_pk(v3.z, v3.w);
-                qxz = f2_pk(v4.x, v4.y);
-                qyz = f2_pk(v4.z, v4.w);
+                q0 = sb.s1[k];
+                q1 = sb.s2[k];
             }
-#pragma unroll
-            for (int q = 0; q < K; ++q) {
-                const f2 rx = f2_sub(xi[q], jx), ry = f2_sub(yi[q], jy), rz = f2_sub(zi[q], jz);
-                const f2 R2 = f2_fma(rx, rx, f2_fma(ry, ry, f2_fma(rz, rz, e2[q])));
-                const f2 Ri = f2_rsqrt(R2);
-                const f2 Ri2 = f2_mul(Ri, Ri);
-                const f2 nMRi = f2_mul(nM, Ri);      // -M/R
-                const f2 nMRi3 = f2_mul(nMRi, Ri2);  // -M/R^3
+            if (K == 1) {
+                const float rx = xi[0] - a.x, ry = yi[0] - a.y, rz = zi[0] - a.z;
+                const float R2 = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, e2[0])));
+                const float Ri = rsqrtf(R2);
+                const float Ri2 = Ri * Ri;
+                const float nMRi = a.w * Ri;
+                const float nMRi3 = nMRi * Ri2;
                 if (QUAD) {
-                    const f2 Qrx = f2_fma(qxx, rx, f2_fma(qxy, ry, f2_mul(qxz, rz)));
-                    const f2 Qry = f2_fma(qxy, rx, f2_fma(qyy, ry, f2_mul(qyz, rz)));
-                    const f2 Qrz = f2_fma(qxz, rx, f2_fma(qyz, ry, f2_mul(qzz, rz)));
-                    const f2 rQr = f2_fma(rx, Qrx, f2_fma(ry, Qry, f2_mul(rz, Qrz)));
-                    const f2 Ri5 = f2_mul(f2_mul(Ri2, Ri2), Ri);
-                    const f2 u = f2_mul(rQr, Ri5);                    // r.Q.r / R^5
-                    const f2 nc = f2_fma(f2_mul(cm25, u), Ri2, nMRi3);  // -(M/R^3 + 5/2 r.Q.r / R^7)
-                    pax[q] = f2_fma(Qrx, Ri5, f2_fma(nc, rx, pax[q]));
-                    pay[q] = f2_fma(Qry, Ri5, f2_fma(nc, ry, pay[q]));
-                    paz[q] = f2_fma(Qrz, Ri5, f2_fma(nc, rz, paz[q]));
-                    pp[q] = f2_fma(cm05, u, f2_add(pp[q], nMRi));
+                    const float Qrx = fmaf(q0.x, rx, fmaf(q0.w, ry, q1.x * rz));
+                    const float Qry = fmaf(q0.w, rx, fmaf(q0.y, ry, q1.y * rz));
+                    const float Qrz = fmaf(q1.x, rx, fmaf(q1.y, ry, q0.z * rz));
+                    const float rQr = fmaf(rx, Qrx, fmaf(ry, Qry, rz * Qrz));
+                    const float Ri5 = Ri2 * Ri2 * Ri;
+                    const float u = rQr * Ri5;
+                    const float nc = fmaf(-2.5f * u, Ri2, nMRi3);
+                    sax[0] = fmaf(Qrx, Ri5, fmaf(nc, rx, sax[0]));
+                    say[0] = fmaf(Qry, Ri5, fmaf(nc, ry, say[0]));
+                    saz[0] = fmaf(Qrz, Ri5, fmaf(nc, rz, saz[0]));
+                    spp[0] = fmaf(-0.5f, u, spp[0] + nMRi);
                 } else {
-                    pax[q] = f2_fma(nMRi3, rx, pax[q]);
-                    pay[q] = f2_fma(nMRi3, ry, pay[q]);
-                    paz[q] = f2_fma(nMRi3, rz, paz[q]);
-                    pp[q] = f2_add(pp[q], nMRi);
+                    sax[0] = fmaf(nMRi3, rx, sax[0]);
+                    say[0] = fmaf(nMRi3, ry, say[0]);
+                    saz[0] = fmaf(nMRi3, rz, saz[0]);
+                    spp[0] += nMRi;
+                }
+            } else {
+                const f2 jx = f2_bc(a.x), jy = f2_bc(a.y), jz = f2_bc(a.z), nM = f2_bc(a.w);
+                f2 qxx, qyy, qzz, qxy, qxz, qyz;
+                if (QUAD) {
+                    qxx = f2_bc(q0.x);
+                    qyy = f2_bc(q0.y);
+                    qzz = f2_bc(q0.z);
+                    qxy = f2_bc(q0.w);
+                    qxz = f2_bc(q1.x);
+                    qyz = f2_bc(q1.y);
+                }
+#pragma unroll
+                for (int h = 0; h < KP; ++h) {
+                    const f2 rx = f2_sub(xp[h], jx), ry = f2_sub(yp[h], jy), rz = f2_sub(zp[h], jz);
+                    const f2 R2 = f2_fma(rx, rx, f2_fma(ry, ry, f2_fma(rz, rz, ep[h])));
+                    const f2 Ri = f2_rsqrt(R2);
+                    const f2 Ri2 = f2_mul(Ri, Ri);
+                    const f2 nMRi = f2_mul(nM, Ri);      // -M/R
+                    const f2 nMRi3 = f2_mul(nMRi, Ri2);  // -M/R^3
+                    if (QUAD) {
+                        const f2 Qrx = f2_fma(qxx, rx, f2_fma(qxy, ry, f2_mul(qxz, rz)));
+                        const f2 Qry = f2_fma(qxy, rx, f2_fma(qyy, ry, f2_mul(qyz, rz)));
+                        const f2 Qrz = f2_fma(qxz, rx, f2_fma(qyz, ry, f2_mul(qzz, rz)));
+                        const f2 rQr = f2_fma(rx, Qrx, f2_fma(ry, Qry, f2_mul(rz, Qrz)));
+                        const f2 Ri5 = f2_mul(f2_mul(Ri2, Ri2), Ri);
+                        const f2 u = f2_mul(rQr, Ri5);                      // r.Q.r / R^5
+                        const f2 nc = f2_fma(f2_mul(cm25, u), Ri2, nMRi3);  // -(M/R^3 + 5/2 r.Q.r / R^7)
+                        pax[h] = f2_fma(Qrx, Ri5, f2_fma(nc, rx, pax[h]));
+                        pay[h] = f2_fma(Qry, Ri5, f2_fma(nc, ry, pay[h]));
+                        paz[h] = f2_fma(Qrz, Ri5, f2_fma(nc, rz, paz[h]));
+                        pp[h] = f2_fma(cm05, u, f2_add(pp[h], nMRi));
+                    } else {
+                        pax[h] = f2_fma(nMRi3, rx, pax[h]);
+                        pay[h] = f2_fma(nMRi3, ry, pay[h]);
+                        paz[h] = f2_fma(nMRi3, rz, paz[h]);
+                        pp[h] = f2_add(pp[h], nMRi);
+                    }
                 }
             }
         }
-        // ---- particles of the opened leaves, in shared tiles of kCJ, two per step
+        // ---- particles of the opened leaves, in shared tiles of kCJ
         for (uint32_t c0 = 0; c0 < total; c0 += kCJ) {
             const uint32_t m = total - c0 < (uint32_t)kCJ ? total - c0 : (uint32_t)kCJ;
             if (c0 > 0) __syncthreads();  // previous tile fully consumed
-            float* sj = reinterpret_cast<float*>(s_j);
             for (uint32_t k = t; k < m; k += kCB) {
                 const uint32_t item = c0 + k;
                 const int src = owner_chunk<CE>(s_es, item);
                 const uint32_t p = s_ef[src] + (item - s_es[src]);
                 const float4 h = A.pf_hi[p], l = A.pf_lo[p];
-                float* d = sj + (k >> 1) * 8 + (k & 1);
-                d[0] = (h.x - gch.x) + (l.x - gcl.x);
-                d[2] = (h.y - gch.y) + (l.y - gcl.y);
-                d[4] = (h.z - gch.z) + (l.z - gcl.z);
-                d[6] = h.w;
-            }
-            if (t == 0 && (m & 1u)) {
-                float* d = sj + (m >> 1) * 8 + 1;
-                d[0] = d[2] = d[4] = kFar;
-                d[6] = 0.0f;
+                s_j[k] = make_float4((h.x - gch.x) + (l.x - gcl.x), (h.y - gch.y) + (l.y - gcl.y),
+                                     (h.z - gch.z) + (l.z - gcl.z), h.w);
             }
             __syncthreads();
-            const int mp = (int)((m + 1u) >> 1);
 #pragma unroll 2
-            for (int k = kbeg; k < mp; k += nsl) {
-                const float4 v0 = s_j[2 * k], v1 = s_j[2 * k + 1];
-                const f2 jx = f2_pk(v0.x, v0.y), jy = f2_pk(v0.z, v0.w), jz = f2_pk(v1.x, v1.y),
-                         jm = f2_pk(v1.z, v1.w);
+            for (int k = kbeg; k < (int)m; k += nsl) {
+                const float4 j = s_j[k];
+                if (K == 1) {
+                    const float dx = j.x - xi[0], dy = j.y - yi[0], dz = j.z - zi[0];
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, e2[0])));
+                    const float ri = rsqrtf(r2);
+                    const float mri = j.w * ri;
+                    const float mri3 = mri * (ri * ri);
+                    sax[0] = fmaf(mri3, dx, sax[0]);
+                    say[0] = fmaf(mri3, dy, say[0]);
+                    saz[0] = fmaf(mri3, dz, saz[0]);
+                    spp[0] -= mri;
+                } else {
+                    const f2 jx = f2_bc(j.x), jy = f2_bc(j.y), jz = f2_bc(j.z), jm = f2_bc(j.w);
 #pragma unroll
-                for (int q = 0; q < K; ++q) {
-                    const f2 dx = f2_sub(jx, xi[q]), dy = f2_sub(jy, yi[q]), dz = f2_sub(jz, zi[q]);
-                    const f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_fma(dz, dz, e2[q])));
-                    const f2 ri = f2_rsqrt(r2);
-                    const f2 mri = f2_mul(jm, ri);
-                    const f2 mri3 = f2_mul(mri, f2_mul(ri, ri));
-                    pax[q] = f2_fma(mri3, dx, pax[q]);
-                    pay[q] = f2_fma(mri3, dy, pay[q]);
-                    paz[q] = f2_fma(mri3, dz, paz[q]);
-                    pp[q] = f2_sub(pp[q], mri);
+                    for (int h = 0; h < KP; ++h) {
+                        const f2 dx = f2_sub(jx, xp[h]), dy = f2_sub(jy, yp[h]), dz = f2_sub(jz, zp[h]);
+                        const f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_fma(dz, dz, ep[h])));
+                        const f2 ri = f2_rsqrt(r2);
+                        const f2 mri = f2_mul(jm, ri);
+                        const f2 mri3 = f2_mul(mri, f2_mul(ri, ri));
+                        pax[h] = f2_fma(mri3, dx, pax[h]);
+                        pay[h] = f2_fma(mri3, dy, pay[h]);
+                        paz[h] = f2_fma(mri3, dz, paz[h]);
+                        pp[h] = f2_sub(pp[h], mri);
+                    }
                 }
             }
         }
+        if (K == 1) {
+            kahan_smem_add(s_k, 0, 0, sax[0]);
+            kahan_smem_add(s_k, 0, 1, say[0]);
+            kahan_smem_add(s_k, 0, 2, saz[0]);
+            kahan_smem_add(s_k, 0, 3, spp[0]);
+        }
 #pragma unroll
-        for (int q = 0; q < K; ++q) {
-            kahan_smem_add(s_k, q, 0, f2_sum(pax[q]));
-            kahan_smem_add(s_k, q, 1, f2_sum(pay[q]));
-            kahan_smem_add(s_k, q, 2, f2_sum(paz[q]));
-            kahan_smem_add(s_k, q, 3, f2_sum(pp[q]));
+        for (int h = 0; h < KP; ++h) {
+            float lo, hi;
+            f2_up(pax[h], lo, hi);
+            kahan_smem_add(s_k, 2 * h, 0, lo);
+            kahan_smem_add(s_k, 2 * h + 1, 0, hi);
+            f2_up(pay[h], lo, hi);
+            kahan_smem_add(s_k, 2 * h, 1, lo);
+            kahan_smem_add(s_k, 2 * h + 1, 1, hi);
+            f2_up(paz[h], lo, hi);
+            kahan_smem_add(s_k, 2 * h, 2, lo);
+            kahan_smem_add(s_k, 2 * h + 1, 2, hi);
+            f2_up(pp[h], lo, hi);
+            kahan_smem_add(s_k, 2 * h, 3, lo);
+            kahan_smem_add(s_k, 2 * h + 1, 3, hi);
         }
         __syncthreads();  // chunk buffers are rewritten next
     }
@@ -480,7 +522,7 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
 template <bool QUAD, int EPT>
 __global__ void __launch_bounds__(kCB, (QUAD ? 4 : 1)) k_force_f32(ForceArgs A) {
     constexpr int kCE = kCB * EPT;
-    constexpr int kSpjBytes = (kCE / 2) * SpjW<QUAD>::W * 4;  // pairs of superparticles
+    constexpr int kSpjBytes = kCE * (QUAD ? 40 : 16);
     constexpr int kRedBytes = 4 * kRed * 8;
     constexpr int kUnion = kSpjBytes > kRedBytes ? kSpjBytes : kRedBytes;
     __shared__ __align__(16) unsigned char s_union[kUnion];
@@ -490,7 +532,10 @@ __global__ void __launch_bounds__(kCB, (QUAD ? 4 : 1)) k_force_f32(ForceArgs A) 
     __shared__ uint32_t s_w[2 * kCW];
     __shared__ uint32_t s_g;
     __shared__ float s_k[4 * 8 * kCB];  // Kahan sums and compensations
-    float* sp = reinterpret_cast<float*>(s_union);
+    SpjBuf<QUAD> sb;
+    sb.s0 = reinterpret_cast<float4*>(s_union);
+    sb.s1 = reinterpret_cast<float4*>(s_union + kCE * 16);
+    sb.s2 = reinterpret_cast<float2*>(s_union + kCE * 32);
     double* s_red = reinterpret_cast<double*>(s_union);
     DevState* st = A.st;
     const uint32_t ngroups = (uint32_t)st->n_groups;
@@ -507,13 +552,13 @@ __global__ void __launch_bounds__(kCB, (QUAD ? 4 : 1)) k_force_f32(ForceArgs A) 
         for (uint32_t ib = 0; ib < ni;) {
             const GroupPlan pl = plan_group(ni - ib);
             if (pl.K == 1)
-                force_round_f32<QUAD, 1, EPT>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, s_j, sp,
+                force_round_f32<QUAD, 1, EPT>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, s_j, sb,
                                          s_ef, s_es, s_w, s_red, s_k);
             else if (pl.K == 2)
-                force_round_f32<QUAD, 2, EPT>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, s_j, sp,
+                force_round_f32<QUAD, 2, EPT>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, s_j, sb,
                                          s_ef, s_es, s_w, s_red, s_k);
             else
-                force_round_f32<QUAD, 4, EPT>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, s_j, sp,
+                force_round_f32<QUAD, 4, EPT>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, s_j, sb,
                                          s_ef, s_es, s_w, s_red, s_k);
             ib += (uint32_t)(pl.P * pl.K);
         }
