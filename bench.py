@@ -341,8 +341,13 @@ def run_ours(args, rank, world, local_rank):
                 "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk, "fp64_variant": fp64, "stages_ms": stages,
                 "per_step": {"interactions": inter / args.steps,
+                             "interactions_epj": inter_e / args.steps,
+                             "interactions_spj": inter_s / args.steps,
+                             "spj_kind": "monopole" if args.mono else "quadrupole",
                              "n_nodes": last["n_nodes"], "n_groups": last["n_groups"],
-                             "fp64_fallbacks": last["fp64_fallbacks"]}}
+                             "fp64_fallbacks": last["fp64_fallbacks"]},
+                "interactions_per_s_force_kernel": (inter / args.steps) / statistics.median(
+                    [f / 1e3 for f in force_ms])}
         print(json.dumps(line), flush=True)
     tree.close()
     ps.close()
