@@ -274,6 +274,65 @@ int fdps_tree_get_groups(const fdps_tree* tree, int64_t cap, int64_t* n_out,
 int fdps_tree_get_lists(const fdps_tree* tree, int64_t g0, int64_t g1,
                         int64_t* offsets, uint32_t* entries, int64_t cap);
 
+/* --------------------------------------- user interaction kernels
+   FDPS takes the interaction law as user functors (Sect. 2.2: the EPJ and
+   SPJ force kernels passed to calcForceAllAndWriteBack).  A C ABI cannot
+   take a device functor, so user laws are compiled by the user against
+   the header template fdps_user_force.cuh, which walks the lists described
+   by a view.
+
+   fdps_tree_build_lists runs the force calculation up to and including
+   the interaction lists (root box, keys, sort, reorder, octree, moments,
+   i-groups, lists) and computes no force.  Errors as for
+   fdps_tree_calc_force_all_and_write_back.
+
+   fdps_tree_get_view fills *view with device pointers into the tree's
+   buffers for the lists of `ps` (built by either call above).  They stay
+   valid until the next call that rebuilds the tree or destroys it or `ps`;
+   kick or drift do not move the copies the view points to.  Layouts (all
+   device memory, owned by the library, read only; float4 = 4 consecutive
+   floats, 16-byte aligned):
+     g_first, g_count  [n_groups] first sorted position and size of group g
+     g_off, g_len      [n_groups] list of g = pool[g_off[g] .. + g_len[g])
+     g_ch, g_cl        [n_groups] float4: group centre relative to the
+                       system's root centre c0 as FP32 hi and lo parts
+     pool              list entries: a node id; (id | leaf_tag) marks an
+                       opened leaf, whose particles are EPJ; else an SPJ
+     nd_first, nd_count  [nodes] first sorted position and size of a node
+     nd_f              [2 nodes] float4: (COM hi - c0, M), (COM lo, 0)
+     nd_fq0, nd_fq1    [nodes] float4 (Qxx, Qyy, Qzz, Qxy) and float2
+                       (Qxz, Qyz): traceless quadrupole about the COM
+                       (NULL for a monopole tree)
+     pf_hi, pf_lo      [n] float4: (x hi - c0, y hi, z hi, m) and
+                       (x lo, y lo, z lo, eps^2) of sorted particle p
+     id                [n] sorted position -> the caller's row
+   A position relative to a group centre is (hi - ch) + (lo - cl) per axis.
+   Errors: FDPS_EINVAL (NULL, FP64-precision tree), FDPS_ESTATE (no lists
+   of ps), FDPS_ECUDA. */
+typedef struct {
+    int64_t n;
+    int64_t n_groups;
+    int32_t quadrupole;
+    uint32_t leaf_tag;
+    const uint32_t* g_first;
+    const uint32_t* g_count;
+    const unsigned long long* g_off;
+    const uint32_t* g_len;
+    const float* g_ch;
+    const float* g_cl;
+    const uint32_t* pool;
+    const uint32_t* nd_first;
+    const uint32_t* nd_count;
+    const float* nd_f;
+    const float* nd_fq0;
+    const float* nd_fq1;
+    const float* pf_hi;
+    const float* pf_lo;
+    const uint32_t* id;
+} fdps_tree_view;
+int fdps_tree_build_lists(fdps_tree* tree, fdps_psys* ps);
+int fdps_tree_get_view(const fdps_tree* tree, const fdps_psys* ps, fdps_tree_view* view);
+
 /* ------------------------------------------- allocation-free key sort
    The paper has no counterpart to this call; it is a service for callers
    that may not allocate device memory themselves: code running while a

@@ -66,6 +66,17 @@ class fdps_tree_stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class fdps_tree_view(C.Structure):
+    """Device pointers into a tree's lists (see fdps_tree_get_view)."""
+    _fields_ = [("n", C.c_int64), ("n_groups", C.c_int64), ("quadrupole", C.c_int32),
+                ("leaf_tag", C.c_uint32)] + [(k, C.c_void_p) for k in (
+        "g_first", "g_count", "g_off", "g_len", "g_ch", "g_cl", "pool", "nd_first", "nd_count",
+        "nd_f", "nd_fq0", "nd_fq1", "pf_hi", "pf_lo", "id")]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _vp = C.c_void_p
 _i64 = C.c_int64
 _i32 = C.c_int32
@@ -98,6 +109,8 @@ _PROTOS = {
                                       _vp, _vp]),
     "fdps_tree_get_groups": (C.c_int, [_vp, _i64, C.POINTER(_i64), _vp, _vp, _vp, _vp]),
     "fdps_tree_get_lists": (C.c_int, [_vp, _i64, _i64, _vp, _vp, _i64]),
+    "fdps_tree_build_lists": (C.c_int, [_vp, _vp]),
+    "fdps_tree_get_view": (C.c_int, [_vp, _vp, C.POINTER(fdps_tree_view)]),
     "fdps_morton_sort_noalloc": (C.c_int, [_vp, _vp, _vp, _i64, _vp, _vp, _vp]),
     "fdps_psys_set_systems": (C.c_int, [_vp, _i32, _vp]),
     "fdps_psys_num_systems": (_i32, [_vp]),
@@ -355,6 +368,19 @@ def fdps_tree_get_lists(ctx, tree, g0, g1):
     return offs, ent[: offs[-1]]
 
 
+def fdps_tree_build_lists(ctx, tree, ps):
+    """Force calculation up to the interaction lists, no forces."""
+    _check(lib().fdps_tree_build_lists(tree, ps), ctx)
+
+
+def fdps_tree_get_view(ctx, tree, ps) -> dict:
+    """Device pointers (ints) and sizes of the lists of ps, for user kernels."""
+    v = fdps_tree_view()
+    _check(lib().fdps_tree_get_view(tree, ps, C.byref(v)), ctx)
+    return {k: (v or 0) if k not in ("n", "n_groups", "quadrupole", "leaf_tag") else v
+            for k, v in v.as_dict().items()}
+
+
 def fdps_morton_sort_noalloc(x, y, z, n, keys_sorted, perm, stream=None):
     """Allocation-free Morton keys + stable sort of n <= FDPS_NOALLOC_MAX_N
     positions; every argument is a device pointer (int) or has data_ptr()."""
@@ -491,3 +517,9 @@ class Tree:
 
     def lists(self, g0, g1):
         return fdps_tree_get_lists(self.ctx.h, self.h, g0, g1)
+
+    def build_lists(self, psys: ParticleSystem):
+        fdps_tree_build_lists(self.ctx.h, self.h, psys.h)
+
+    def view(self, psys: ParticleSystem) -> dict:
+        return fdps_tree_get_view(self.ctx.h, self.h, psys.h)

@@ -226,7 +226,7 @@ int launch_force_pipeline(fdps_tree* t, fdps_psys* ps, int k_spj) {
     return compute_forces(t, ps, k_spj);
 }
 
-int run_force(fdps_tree* t, fdps_psys* ps, int k_spj) {
+int run_force(fdps_tree* t, fdps_psys* ps, int k_spj, bool lists_only = false) {
     fdps_ctx* ctx = t->ctx;
     const int64_t n = ps->n;
     int rc;
@@ -291,12 +291,19 @@ int run_force(fdps_tree* t, fdps_psys* ps, int k_spj) {
             if ((rc = ensure_pool(t, std::max<int64_t>(need, 2 * t->cap_pool)))) return rc;
         }
     }
+    if (lists_only) {  // S0-S7 only: the lists stay for user interaction kernels
+        FDPS_CUDA_TRY(ctx, cudaGetLastError());
+        t->valid = true;
+        t->lists_of = ps;
+        return FDPS_OK;
+    }
     k_reset_counters<<<1, 32, 0, s>>>(t->st, 2);
     FDPS_LAUNCH_CHECK(ctx);
     if ((rc = compute_forces(t, ps, k_spj))) return rc;
     record(t, 8);
     FDPS_CUDA_TRY(ctx, cudaGetLastError());
     t->valid = true;
+    t->lists_of = ps;
     ps->has_forces = true;
     return FDPS_OK;
 }
@@ -585,6 +592,48 @@ int fdps_tree_calc_force_all_and_write_back(fdps_tree* t, fdps_psys* ps, int k_e
     if (!ps->has_data) return set_error(ctx, FDPS_ESTATE, "particle data not set");
     cudaSetDevice(ctx->device);
     return run_force(t, ps, k_spj);
+}
+
+int fdps_tree_build_lists(fdps_tree* t, fdps_psys* ps) {
+    if (!t || !ps) return FDPS_EINVAL;
+    fdps_ctx* ctx = t->ctx;
+    if (ps->ctx != ctx) return set_error(ctx, FDPS_EINVAL, "tree and particle system belong to different contexts");
+    if (!ps->has_data) return set_error(ctx, FDPS_ESTATE, "particle data not set");
+    cudaSetDevice(ctx->device);
+    const int k_spj = t->p.moment == FDPS_QUADRUPOLE ? FDPS_GRAV_SPJ_QUAD : FDPS_GRAV_SPJ_MONO;
+    return run_force(t, ps, k_spj, true);
+}
+
+int fdps_tree_get_view(const fdps_tree* tc, const fdps_psys* ps, fdps_tree_view* v) {
+    if (!tc || !ps || !v) return FDPS_EINVAL;
+    fdps_tree* t = const_cast<fdps_tree*>(tc);
+    if (!t->valid || t->lists_of != ps)
+        return set_error(t->ctx, FDPS_ESTATE, "no lists of this particle system: build them first");
+    if (t->p.precision != FDPS_FP32REL)
+        return set_error(t->ctx, FDPS_EINVAL, "views are of FP32-relative trees");
+    int rc = read_state(t);
+    if (rc) return rc;
+    *v = fdps_tree_view{};
+    v->n = ps->n;
+    v->n_groups = t->h_st.n_groups;
+    v->quadrupole = t->p.moment == FDPS_QUADRUPOLE ? 1 : 0;
+    v->leaf_tag = kLeafTag;
+    v->g_first = t->g_first;
+    v->g_count = t->g_count;
+    v->g_off = t->g_off;
+    v->g_len = t->g_len;
+    v->g_ch = reinterpret_cast<const float*>(t->g_ch);
+    v->g_cl = reinterpret_cast<const float*>(t->g_cl);
+    v->pool = t->pool;
+    v->nd_first = t->nd_first;
+    v->nd_count = t->nd_count;
+    v->nd_f = reinterpret_cast<const float*>(t->nd_f);
+    v->nd_fq0 = v->quadrupole ? reinterpret_cast<const float*>(t->nd_fq0) : nullptr;
+    v->nd_fq1 = v->quadrupole ? reinterpret_cast<const float*>(t->nd_fq1) : nullptr;
+    v->pf_hi = reinterpret_cast<const float*>(t->pf_hi);
+    v->pf_lo = reinterpret_cast<const float*>(t->pf_lo);
+    v->id = ps->id[ps->cur];
+    return FDPS_OK;
 }
 
 int fdps_kick(fdps_psys* ps, double dt_half) {

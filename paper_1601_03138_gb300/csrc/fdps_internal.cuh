@@ -145,6 +145,7 @@ struct fdps_tree {
     uint32_t* vals_b = nullptr;
     uint32_t* perm = nullptr;      // result of the sort (points into vals_*)
     uint64_t* keys_sorted = nullptr;
+    const fdps_psys* lists_of = nullptr;  // particle system of the current lists
     uint32_t* sort_hist = nullptr; // [256][tiles]
     uint32_t* sort_dtot = nullptr; // [4096]: digit totals / bases of every pass, tile counters
     int64_t cap_tiles = 0;
