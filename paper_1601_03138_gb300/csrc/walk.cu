@@ -125,7 +125,10 @@ __global__ void __launch_bounds__(kWalkBlock, 8) k_walk(WalkArgs A) {
             max_front = fsize > max_front ? fsize : max_front;
             // the first batch's frontier entries, node records and COM pairs;
             // every batch then fetches the next one's before testing its own
+            // (frontier ids two batches ahead, records one batch ahead, so
+            // no batch waits on a load that depends on another load)
             uint32_t node_nx = lane < fsize ? fa[lane] : 0u;
+            uint32_t node_nx2 = lane + 32 < fsize ? fa[lane + 32] : 0u;
             uint4 rec_nx = make_uint4(0, 0, 0, 0);
             float4 fh_nx = make_float4(0.f, 0.f, 0.f, 0.f), fl_nx = fh_nx;
             if (lane < fsize) {
@@ -140,11 +143,12 @@ __global__ void __launch_bounds__(kWalkBlock, 8) k_walk(WalkArgs A) {
                 const uint4 rec = rec_nx;
                 const float4 fh = fh_nx, fl = fl_nx;
                 if (idx + 32 < fsize) {
-                    node_nx = fa[idx + 32];
+                    node_nx = node_nx2;
                     rec_nx = A.nd_walk[node_nx];
                     fh_nx = A.nd_f[2 * node_nx];
                     fl_nx = A.nd_f[2 * node_nx + 1];
                 }
+                if (idx + 64 < fsize) node_nx2 = fa[idx + 64];
                 int action = 0;  // 1 SPJ, 2 EPJ leaf, 3 open internal
                 uint32_t nch = 0, child = 0;
                 bool fallback = false;
