@@ -316,16 +316,17 @@ def run_ours(args, rank, world, local_rank):
         t0 = time.perf_counter()
         ie = 0
         for _ in range(args.e2e_steps):
-            ps2.set(hp, hv, hm, he)
+            # the force calculation's inputs: positions, masses, softenings
+            ps2.set(hp, None, hm, he)
             tree.calc_force_all_and_write_back(ps2)
             G.fdps_psys_get(ctx.h, ps2.h, None, None, hacc, hpot)
             s2 = tree.stats()
             ie += s2["interactions_epj"] + s2["interactions_spj"]
         t_e2e = time.perf_counter() - t0
         ps2.close()
-        e2e = {"value": ie / t_e2e, "unit": "interactions/s", "h2d_bytes_per_step": 64 * n,
+        e2e = {"value": ie / t_e2e, "unit": "interactions/s", "h2d_bytes_per_step": 40 * n,
                "d2h_bytes_per_step": 32 * n, "steps": args.e2e_steps,
-               "what": "psys_set from pinned host + calcForceAllAndWriteBack + get(acc, pot)"}
+               "what": "psys_set(pos, mass, eps) from pinned host + calcForceAllAndWriteBack + get(acc, pot) into pinned host"}
 
     # all-FP64 pipeline of the same library on the same particles: one step
     fp64 = None
