@@ -328,9 +328,12 @@ __device__ __forceinline__ void node_moments(const MomArgs& A, int64_t i) {
     split_hilo(cz - bx.c0[2], &hz, &lz);
     A.nd_f[2 * i] = make_float4(hx, hy, hz, __double2float_rn(M));
     A.nd_f[2 * i + 1] = make_float4(lx, ly, lz, 0.0f);
+    // walk record: (q_x | level << 21 | leaf << 26 | children << 27, q_y, q_z,
+    // first child of an internal node or particle count of a leaf)
     const uint64_t qlo = A.nd_qlo[i];
-    // third word: first child of an internal node, particle count of a leaf
-    A.nd_walk[i] = make_uint4((uint32_t)qlo, (uint32_t)(qlo >> 32), leaf ? cnt : c0, meta);
+    const uint32_t lev = meta & 0xFFu, nch = (meta >> 8) & 0xFFu;
+    A.nd_walk[i] = make_uint4((uint32_t)(qlo >> 42) | (lev << 21) | ((leaf ? 1u : 0u) << 26) | (nch << 27),
+                              (uint32_t)(qlo >> 21) & kQMax, (uint32_t)qlo & kQMax, leaf ? cnt : c0);
     if (!QUAD) return;
     if (Q64) {
         double q[6] = {0, 0, 0, 0, 0, 0};

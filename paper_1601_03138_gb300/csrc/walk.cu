@@ -30,7 +30,7 @@ namespace fdps {
 struct WalkArgs {
     DevState* st;
     const uint32_t* nd_count;
-    const uint4* nd_walk;  // (grid origin low, high, first child | leaf count, meta) per node
+    const uint4* nd_walk;  // (q_x | level, leaf, children; q_y; q_z; first child | leaf count)
     const float4* nd_f;    // COM hi/lo pairs per node
     const dvec4* nd_com;
     const uint32_t* g_count;
@@ -153,13 +153,10 @@ __global__ void __launch_bounds__(kWalkBlock, 8) k_walk(WalkArgs A) {
                 uint32_t nch = 0, child = 0;
                 bool fallback = false;
                 if (act) {
-                    const uint32_t meta = rec.w;
-                    const int level = (int)(meta & 0xFFu);
-                    const bool leaf = (meta >> 16) & 1u;
-                    const uint64_t q = (uint64_t)rec.x | ((uint64_t)rec.y << 32);
+                    const int level = (int)((rec.x >> 21) & 31u);
+                    const bool leaf = (rec.x >> 26) & 1u;
                     const uint32_t w = (1u << (kMaxLevel - level)) - 1u;
-                    const uint32_t qx = (uint32_t)(q >> 42), qy = (uint32_t)(q >> 21) & kQMax,
-                                   qz = (uint32_t)q & kQMax;
+                    const uint32_t qx = rec.x & kQMax, qy = rec.y, qz = rec.z;
                     const bool meets = qx <= qmax0 && qx + w >= qmin0 && qy <= qmax1 &&
                                        qy + w >= qmin1 && qz <= qmax2 && qz + w >= qmin2;
                     bool open = true;
@@ -171,7 +168,8 @@ __global__ void __launch_bounds__(kWalkBlock, 8) k_walk(WalkArgs A) {
                         const float ty = fmaxf(fmaxf(blo.y - dy, dy - bhi.y), 0.0f);
                         const float tz = fmaxf(fmaxf(blo.z - dz, dz - bhi.z), 0.0f);
                         const float d2 = tx * tx + ty * ty + tz * tz;
-                        const float ell = scalbnf(Lf, -level);  // exact: L 2^-level in FP32
+                        // L 2^-level, exact: an exponent decrement of the normal FP32 L
+                        const float ell = __int_as_float(__float_as_int(Lf) - (level << 23));
                         const float l2 = ell * ell;
                         const float r2 = A.theta2f * d2;
                         const float T = l2 - r2;
@@ -195,11 +193,11 @@ __global__ void __launch_bounds__(kWalkBlock, 8) k_walk(WalkArgs A) {
                         action = 1;
                     } else if (leaf) {
                         action = 2;
-                        nepj_lane += rec.z;  // the leaf's particle count
+                        nepj_lane += rec.w;  // the leaf's particle count
                     } else {
                         action = 3;
-                        child = rec.z;
-                        nch = (meta >> 8) & 0xFFu;
+                        child = rec.w;
+                        nch = rec.x >> 27;
                     }
                 }
                 acc_fb += __popc(__ballot_sync(0xFFFFFFFFu, fallback));
