@@ -90,6 +90,32 @@ def force_traffic(workload: str):
     return rec[1] if sha.startswith(rec[0]) else None
 
 
+def combine_ranks(t_local: float, units_local: float, world: int, device: str):
+    """Whole-job numbers over ranks: the slowest rank's time and the sum of
+    the units every rank processed (all_gather over the default group)."""
+    if world <= 1:
+        return t_local, units_local
+    import torch
+    tt = torch.tensor([t_local, float(units_local)], device=device, dtype=torch.float64)
+    gathered = [torch.zeros_like(tt) for _ in range(world)]
+    torch.distributed.all_gather(gathered, tt)
+    return max(float(g[0]) for g in gathered), sum(float(g[1]) for g in gathered)
+
+
+def partition_systems(sizes, world: int):
+    """Contiguous ranges [a, b) of systems per rank, balanced by the tree
+    cost of a system, taken as N log2 N; every system in exactly one range."""
+    sizes = np.asarray(sizes, dtype=np.float64)
+    cost = sizes * np.log2(np.maximum(sizes, 2.0))
+    cum = np.concatenate([[0.0], np.cumsum(cost)])
+    cuts = [0]
+    for r in range(1, world):
+        k = int(np.searchsorted(cum, cum[-1] * r / world))
+        cuts.append(min(max(k, cuts[-1]), len(sizes)))
+    cuts.append(len(sizes))
+    return [(cuts[r], cuts[r + 1]) for r in range(world)]
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -275,11 +301,7 @@ def run_ours(args, rank, world, local_rank):
     inter = inter_e + inter_s
     t_max = t_total
     if dist:
-        tt = torch.tensor([t_total, float(inter)], device="cuda", dtype=torch.float64)
-        gathered = [torch.zeros_like(tt) for _ in range(world)]
-        torch.distributed.all_gather(gathered, tt)
-        t_max = max(float(g[0]) for g in gathered)
-        inter = sum(float(g[1]) for g in gathered)
+        t_max, inter = combine_ranks(t_total, inter, world, "cuda")
     value = inter / t_max
     last = stage[-1]
 
@@ -377,9 +399,12 @@ def run_ours(args, rank, world, local_rank):
     ctx.close()
 
 
-def run_ensemble(args):
+def run_ensemble(args, rank=0, world=1, local_rank=0):
     """Systems-steps/s of the ensemble stepped by graph-captured runs, with
-    per-system energy drift, beside one step of the all-FP64 pipeline."""
+    per-system energy drift, beside one step of the all-FP64 pipeline.  With
+    several ranks the systems are split into contiguous ranges (no exchange
+    between ranks); the whole job's value is all systems' steps over the
+    slowest rank's time."""
     import torch
     import ics
     import paper_1601_03138_gb300 as G
@@ -387,9 +412,17 @@ def run_ensemble(args):
     B.build()
     cfg = ics.CONFIGS["ensemble4096"]
     pos, vel, mass, eps, off = ics.ensemble(args.n_sys, cfg["seed"])
+    n_sys_all, n_all = args.n_sys, len(pos)
+    if world > 1:
+        a, b = partition_systems(np.diff(off), world)[rank]
+        p0, p1 = off[a], off[b]
+        pos, vel, mass, eps = pos[p0:p1], vel[p0:p1], mass[p0:p1], eps[p0:p1]
+        off = off[a:b + 1] - p0
+    n_sys = len(off) - 1
     n = len(pos)
     dt = cfg["dt"]
-    ctx = G.Context(0)
+    torch.cuda.set_device(local_rank)
+    ctx = G.Context(local_rank)
     ctx.set_profiling(True)
     stream = torch.cuda.ExternalStream(ctx.stream)
     ps = G.ParticleSystem(ctx, n)
@@ -405,7 +438,9 @@ def run_ensemble(args):
     ek0, ep0 = ps.energy_systems()
     tree.run(ps, dt, args.warmup)
     torch.cuda.synchronize()
-    clocks = ClockSampler(0)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local_rank)
     clocks.start()
     l0 = ctx.launches
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -413,9 +448,11 @@ def run_ensemble(args):
     tree.run(ps, dt, args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     clk = clocks.stop()
     launches = ctx.launches - l0
-    t = e0.elapsed_time(e1) / 1e3
+    t, systems_steps = combine_ranks(e0.elapsed_time(e1) / 1e3, n_sys * args.steps, world, "cuda")
     st = tree.stats()
     ek1, ep1 = ps.energy_systems()
     E0, E1 = ek0 + ep0, ek1 + ep1
@@ -434,17 +471,25 @@ def run_ensemble(args):
         a1.record(stream)
         torch.cuda.synchronize()
         ms64 = a0.elapsed_time(a1)
-        fp64 = {"ms_per_step": ms64, "value": args.n_sys / (ms64 / 1e3), "steps": 1}
+        fp64 = {"ms_per_step": ms64, "value": n_sys / (ms64 / 1e3), "steps": 1, "rank": rank}
         t64.close()
         ps3.close()
     inter = st["interactions_epj"] + st["interactions_spj"]
-    line = {"metric": "systems-steps/s", "value": args.n_sys * args.steps / t, "unit": "systems*steps/s",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+    if rank != 0:
+        tree.close()
+        ps.close()
+        ctx.close()
+        return
+    line = {"metric": "systems-steps/s", "value": systems_steps / t, "unit": "systems*steps/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "strong" if world > 1 else "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"ensemble of {args.n_sys} Plummer clusters, N log-uniform "
-                                   f"[256, 65536] (total {n}), theta {cfg['theta']} monopole, "
+            "config": {"workload": f"ensemble of {n_sys_all} Plummer clusters, N log-uniform "
+                                   f"[256, 65536] (total {n_all}), theta {cfg['theta']} monopole, "
                                    f"dt {dt}, graph-captured steps", "l2": "inputs larger than L2",
+                       "ranks": "systems split in contiguous ranges balanced by N log N"
+                                if world > 1 else "one GPU",
                        "params": tuned or {"n_leaf": cfg["n_leaf"], "n_grp": cfg["n_grp"]}},
             "gpu_launches": launches, "clocks": clk,
             "interactions_per_s_estimate": inter * args.steps / t,
@@ -552,8 +597,14 @@ def main():
         run_reference(args, rank, world)
         return
     if args.ensemble:
-        if rank == 0:
-            run_ensemble(args)
+        if world > 1:
+            import torch
+            torch.cuda.set_device(local_rank)
+            torch.distributed.init_process_group("nccl")
+        run_ensemble(args, rank, world, local_rank)
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
         return
     if args.suite:
         if rank == 0:
