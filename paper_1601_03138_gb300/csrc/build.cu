@@ -331,7 +331,7 @@ __device__ __forceinline__ void node_moments(const MomArgs& A, int64_t i) {
     // walk record: (q_x | level << 21 | leaf << 26 | children << 27, q_y, q_z,
     // first child of an internal node or particle count of a leaf)
     const uint64_t qlo = A.nd_qlo[i];
-    const uint32_t lev = meta & 0xFFu, nch = (meta >> 8) & 0xFFu;
+    const uint32_t lev = meta_level(meta), nch = nc;
     A.nd_walk[i] = make_uint4((uint32_t)(qlo >> 42) | (lev << 21) | ((leaf ? 1u : 0u) << 26) | (nch << 27),
                               (uint32_t)(qlo >> 21) & kQMax, (uint32_t)qlo & kQMax, leaf ? cnt : c0);
     if (!QUAD) return;
@@ -623,7 +623,6 @@ int build_tree(fdps_tree* t, fdps_psys* ps) {
 
 int compute_moments(fdps_tree* t, fdps_psys* ps) {
     fdps_ctx* ctx = t->ctx;
-    cudaStream_t s = ctx->stream;
     const int c = ps->cur;
     MomArgs A;
     A.st = t->st;

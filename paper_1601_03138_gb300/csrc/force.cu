@@ -60,24 +60,7 @@ namespace {
 
 constexpr int kFBlock = 128;
 constexpr int kFWarps = kFBlock / 32;
-constexpr int kJCap = 256;    // EPJ particles per FP32 tile
 constexpr int kJCap64 = 128;  // EPJ particles per FP64 tile
-
-struct Kahan4 {
-    float s[4];
-    float c[4];
-    __device__ __forceinline__ void init() {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) s[k] = c[k] = 0.0f;
-    }
-    __device__ __forceinline__ void add(int k, float v) {
-        const float y = v - c[k];
-        const float t = s[k] + y;
-        c[k] = (t - s[k]) - y;
-        s[k] = t;
-    }
-    __device__ __forceinline__ double value(int k) const { return (double)s[k] - (double)c[k]; }
-};
 
 // Lane -> (i offset, slice) split of a group of n_i particles.
 struct Split {
@@ -240,12 +223,6 @@ __device__ __forceinline__ f2 f2_rsqrt(f2 v) {
     f2_up(v, a, b);
     return f2_pk(rsqrtf(a), rsqrtf(b));
 }
-__device__ __forceinline__ float f2_sum(f2 v) {
-    float a, b;
-    f2_up(v, a, b);
-    return a + b;
-}
-
 // Shared-memory layouts (coordinates relative to the group centre):
 //   superparticles: float4 (x, y, z, -M), float4 (Qxx, Qyy, Qzz, Qxy),
 //     float2 (Qxz, Qyz) in three arrays
