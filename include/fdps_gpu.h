@@ -333,6 +333,31 @@ typedef struct {
 int fdps_tree_build_lists(fdps_tree* tree, fdps_psys* ps);
 int fdps_tree_get_view(const fdps_tree* tree, const fdps_psys* ps, fdps_tree_view* view);
 
+/* User laws from source text, compiled at run time (NVRTC, sm_103a).
+   `source` is CUDA C++ defining
+     struct Force { ...; __device__ void clear(); };   (trivially copyable)
+     struct Law   { the two __device__ call operators of
+                    fdps_user_force.cuh, for Epj and for Spj tiles };
+   with Epi, Epj, Spj and the rest of that header in scope; it is compiled
+   together with the header's device part as the library was built.
+   fdps_user_law_compile: on success *law is a handle owned by the caller
+   (fdps_user_law_destroy); on a compile error it returns FDPS_EINVAL and
+   the compiler's messages, with line numbers of `source`, go to `log`
+   (log_cap bytes, NUL-terminated; NULL for none), as they also do on
+   success (warnings).  FDPS_ECUDA if the result cannot be loaded.
+   fdps_user_law_force_size: sizeof(Force) as compiled, -1 for NULL.
+   fdps_user_law_run: queues the law over the lists of `ps` (built by
+   fdps_tree_build_lists or a force calculation) on the context's stream;
+   `out` is a device array of n Force values, out[row] for the caller's
+   row `row`.  Errors as fdps_tree_get_view, and FDPS_ECUDA. */
+typedef struct fdps_user_law fdps_user_law;
+int fdps_user_law_compile(fdps_ctx* ctx, const char* source, fdps_user_law** law,
+                          char* log, int64_t log_cap);
+int64_t fdps_user_law_force_size(const fdps_user_law* law);
+int fdps_user_law_run(fdps_user_law* law, const fdps_tree* tree, const fdps_psys* ps,
+                      void* out);
+int fdps_user_law_destroy(fdps_user_law* law);
+
 /* ------------------------------------------- allocation-free key sort
    The paper has no counterpart to this call; it is a service for callers
    that may not allocate device memory themselves: code running while a

@@ -29,11 +29,17 @@
  * the Force of the particle in row `row` of the caller's arrays (cleared,
  * then accumulated by the functors), for every particle.  The work is
  * queued on `stream`; calc_force returns the launch status.
+ *
+ * The device part of this header (the types and calc_force_body) also
+ * compiles under NVRTC, where fdps_user_law_compile builds user laws given
+ * as source text at run time.
  */
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <cstdint>
 #include <cuda_runtime.h>
+#endif
 
 #include "fdps_gpu.h"
 
@@ -67,9 +73,10 @@ __device__ __forceinline__ float4 ld4(const float* p, uint64_t i) {
     return reinterpret_cast<const float4*>(p)[i];
 }
 
+// The whole walk over the view's groups, for a block of kWarps warps.
 template <class Force, class FEpj, class FSpj>
-__global__ void __launch_bounds__(kWarps * 32)
-    calc_force_kernel(fdps_tree_view v, FEpj f_epj, FSpj f_spj, Force* out) {
+__device__ __forceinline__ void calc_force_body(const fdps_tree_view& v, const FEpj& f_epj,
+                                                const FSpj& f_spj, Force* out) {
     __shared__ Spj s_spj[kWarps][kTile];
     __shared__ Epj s_epj[kWarps][kEpjTile];
     __shared__ uint32_t s_first[kWarps][kTile];
@@ -165,7 +172,15 @@ __global__ void __launch_bounds__(kWarps * 32)
     }
 }
 
+template <class Force, class FEpj, class FSpj>
+__global__ void __launch_bounds__(kWarps * 32)
+    calc_force_kernel(fdps_tree_view v, FEpj f_epj, FSpj f_spj, Force* out) {
+    calc_force_body<Force>(v, f_epj, f_spj, out);
+}
+
 }  // namespace detail
+
+#ifndef __CUDACC_RTC__
 
 // Launch the user laws over every group of the view (see the top of this
 // file).  `out` is a device array of v.n Force values.
@@ -187,5 +202,6 @@ cudaError_t calc_force(const fdps_tree_view& v, const FEpj& f_epj, const FSpj& f
         <<<blocks, detail::kWarps * 32, 0, stream>>>(v, f_epj, f_spj, out);
     return cudaGetLastError();
 }
+#endif  // __CUDACC_RTC__
 
 }  // namespace fdps_user

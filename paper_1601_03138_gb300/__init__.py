@@ -111,6 +111,10 @@ _PROTOS = {
     "fdps_tree_get_lists": (C.c_int, [_vp, _i64, _i64, _vp, _vp, _i64]),
     "fdps_tree_build_lists": (C.c_int, [_vp, _vp]),
     "fdps_tree_get_view": (C.c_int, [_vp, _vp, C.POINTER(fdps_tree_view)]),
+    "fdps_user_law_compile": (C.c_int, [_vp, C.c_char_p, C.POINTER(_vp), C.c_char_p, _i64]),
+    "fdps_user_law_force_size": (_i64, [_vp]),
+    "fdps_user_law_run": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "fdps_user_law_destroy": (C.c_int, [_vp]),
     "fdps_morton_sort_noalloc": (C.c_int, [_vp, _vp, _vp, _i64, _vp, _vp, _vp]),
     "fdps_psys_set_systems": (C.c_int, [_vp, _i32, _vp]),
     "fdps_psys_num_systems": (_i32, [_vp]),
@@ -381,6 +385,29 @@ def fdps_tree_get_view(ctx, tree, ps) -> dict:
             for k, v in v.as_dict().items()}
 
 
+def fdps_user_law_compile(ctx, source: str, log_cap: int = 1 << 16):
+    """(handle, compiler log) of a user law given as CUDA source text."""
+    h = _vp()
+    log = C.create_string_buffer(log_cap)
+    rc = lib().fdps_user_law_compile(ctx, source.encode(), C.byref(h), log, log_cap)
+    text = log.value.decode(errors="replace")
+    if rc != 0:
+        raise FdpsError(rc, f"{fdps_last_error(ctx)}\n{text}")
+    return h.value, text
+
+
+def fdps_user_law_force_size(law) -> int:
+    return int(lib().fdps_user_law_force_size(law))
+
+
+def fdps_user_law_run(ctx, law, tree, ps, out_ptr: int):
+    _check(lib().fdps_user_law_run(law, tree, ps, C.c_void_p(out_ptr)), ctx)
+
+
+def fdps_user_law_destroy(law):
+    lib().fdps_user_law_destroy(law)
+
+
 def fdps_morton_sort_noalloc(x, y, z, n, keys_sorted, perm, stream=None):
     """Allocation-free Morton keys + stable sort of n <= FDPS_NOALLOC_MAX_N
     positions; every argument is a device pointer (int) or has data_ptr()."""
@@ -421,6 +448,26 @@ class Context:
     @property
     def launches(self) -> int:
         return fdps_kernel_launches(self.h)
+
+
+class UserLaw:
+    """A user interaction law compiled from source at run time."""
+
+    def __init__(self, ctx: "Context", source: str):
+        self.ctx = ctx
+        self.h, self.log = fdps_user_law_compile(ctx.h, source)
+        self.force_size = fdps_user_law_force_size(self.h)
+
+    def run(self, tree: "Tree", psys: "ParticleSystem", out):
+        """Queue the law over tree's lists of psys; out: device buffer (pointer
+        or tensor) of psys.n Force values."""
+        ptr = out if isinstance(out, int) else out.data_ptr()
+        fdps_user_law_run(self.ctx.h, self.h, tree.h, psys.h, ptr)
+
+    def close(self):
+        if self.h:
+            fdps_user_law_destroy(self.h)
+            self.h = None
 
 
 class ParticleSystem:
