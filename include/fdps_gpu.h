@@ -274,6 +274,33 @@ int fdps_tree_get_groups(const fdps_tree* tree, int64_t cap, int64_t* n_out,
 int fdps_tree_get_lists(const fdps_tree* tree, int64_t g0, int64_t g1,
                         int64_t* offsets, uint32_t* entries, int64_t cap);
 
+/* ------------------------------------------ accuracy diagnostics
+   fdps_direct_sample: the exact reference of the force law (Eq.
+   ParticleParticleNbody summed over every other particle of the same
+   system, softening of the receiving particle) for n_sample particles
+   given by their rows in the caller's arrays (host array `rows`, values in
+   0 .. n-1).  Arithmetic: separations from FP32 hi/lo position parts (about
+   48 bits), FP32 pair terms, compensated sums finished in FP64 (relative
+   error about 1e-6 or below).  acc3 [n_sample][3] and pot [n_sample] are
+   host outputs (either may be NULL).  Synchronous.  Errors: FDPS_EINVAL,
+   FDPS_ESTATE (no data), FDPS_ENOMEM, FDPS_ECUDA.
+
+   fdps_tree_choose_theta: the largest opening angle among `candidates`
+   (n_candidates values; NULL: 0.2, 0.3, ..., 1.0) whose median relative
+   acceleration error |a_tree - a_direct| / |a_direct| over n_sample evenly
+   spaced rows stays at or below `target`.  It tries the candidates in
+   increasing order with full force calculations, stops at the first that
+   misses the target, sets the tree's theta to the choice (the smallest
+   candidate if none meets the target) and leaves the forces of that
+   choice in ps.  *theta_out and *median_out (either may be NULL) receive
+   the choice and its measured median.  Errors as for the force
+   calculation and fdps_direct_sample. */
+int fdps_direct_sample(fdps_psys* ps, int64_t n_sample, const int64_t* rows,
+                       double* acc3, double* pot);
+int fdps_tree_choose_theta(fdps_tree* tree, fdps_psys* ps, double target,
+                           int64_t n_sample, const double* candidates,
+                           int32_t n_candidates, double* theta_out, double* median_out);
+
 /* --------------------------------------- user interaction kernels
    FDPS takes the interaction law as user functors (Sect. 2.2: the EPJ and
    SPJ force kernels passed to calcForceAllAndWriteBack).  A C ABI cannot

@@ -111,6 +111,8 @@ _PROTOS = {
     "fdps_tree_get_lists": (C.c_int, [_vp, _i64, _i64, _vp, _vp, _i64]),
     "fdps_tree_build_lists": (C.c_int, [_vp, _vp]),
     "fdps_tree_get_view": (C.c_int, [_vp, _vp, C.POINTER(fdps_tree_view)]),
+    "fdps_direct_sample": (C.c_int, [_vp, _i64, _vp, _vp, _vp]),
+    "fdps_tree_choose_theta": (C.c_int, [_vp, _vp, _d, _i64, _vp, _i32, C.POINTER(_d), C.POINTER(_d)]),
     "fdps_user_law_compile": (C.c_int, [_vp, C.c_char_p, C.POINTER(_vp), C.c_char_p, _i64]),
     "fdps_user_law_force_size": (_i64, [_vp]),
     "fdps_user_law_run": (C.c_int, [_vp, _vp, _vp, _vp]),
@@ -385,6 +387,26 @@ def fdps_tree_get_view(ctx, tree, ps) -> dict:
             for k, v in v.as_dict().items()}
 
 
+def fdps_direct_sample(ctx, ps, rows):
+    """(acc [k][3], pot [k]) of the direct sum for the caller's rows."""
+    r = np.ascontiguousarray(rows, dtype=np.int64)
+    acc = np.zeros((len(r), 3))
+    pot = np.zeros(len(r))
+    _check(lib().fdps_direct_sample(ps, len(r), C.c_void_p(r.ctypes.data), C.c_void_p(acc.ctypes.data),
+                                    C.c_void_p(pot.ctypes.data)), ctx)
+    return acc, pot
+
+
+def fdps_tree_choose_theta(ctx, tree, ps, target, n_sample=4096, candidates=None):
+    """(theta, median error) of the largest candidate meeting the target."""
+    th, med = _d(), _d()
+    c = None if candidates is None else np.ascontiguousarray(candidates, dtype=np.float64)
+    _check(lib().fdps_tree_choose_theta(tree, ps, float(target), int(n_sample),
+                                        None if c is None else C.c_void_p(c.ctypes.data),
+                                        0 if c is None else len(c), C.byref(th), C.byref(med)), ctx)
+    return th.value, med.value
+
+
 def fdps_user_law_compile(ctx, source: str, log_cap: int = 1 << 16):
     """(handle, compiler log) of a user law given as CUDA source text."""
     h = _vp()
@@ -486,6 +508,10 @@ class ParticleSystem:
     def set(self, pos, vel, mass, eps):
         fdps_psys_set(self.ctx.h, self.h, pos, vel, mass, eps)
 
+    def direct(self, rows):
+        """Direct-sum (acc, pot) at the caller's rows (exact reference)."""
+        return fdps_direct_sample(self.ctx.h, self.h, rows)
+
     def get(self):
         """(pos, vel, acc, pot) as numpy arrays in the caller's order."""
         pos = np.zeros((self.n, 3))
@@ -564,6 +590,9 @@ class Tree:
 
     def lists(self, g0, g1):
         return fdps_tree_get_lists(self.ctx.h, self.h, g0, g1)
+
+    def choose_theta(self, psys: ParticleSystem, target: float, n_sample: int = 4096, candidates=None):
+        return fdps_tree_choose_theta(self.ctx.h, self.h, psys.h, target, n_sample, candidates)
 
     def build_lists(self, psys: ParticleSystem):
         fdps_tree_build_lists(self.ctx.h, self.h, psys.h)

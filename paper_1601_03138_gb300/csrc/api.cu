@@ -5,7 +5,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <new>
+#include <vector>
 
 #include "fdps_internal.cuh"
 
@@ -592,6 +594,117 @@ int fdps_tree_calc_force_all_and_write_back(fdps_tree* t, fdps_psys* ps, int k_e
     if (!ps->has_data) return set_error(ctx, FDPS_ESTATE, "particle data not set");
     cudaSetDevice(ctx->device);
     return run_force(t, ps, k_spj);
+}
+
+int fdps_direct_sample(fdps_psys* ps, int64_t n_sample, const int64_t* rows, double* acc3, double* pot) {
+    if (!ps || n_sample < 1 || !rows || (!acc3 && !pot)) return FDPS_EINVAL;
+    fdps_ctx* ctx = ps->ctx;
+    if (!ps->has_data) return set_error(ctx, FDPS_ESTATE, "particle data not set");
+    for (int64_t k = 0; k < n_sample; ++k)
+        if (rows[k] < 0 || rows[k] >= ps->n) return set_error(ctx, FDPS_EINVAL, "row %lld out of range", (long long)rows[k]);
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = ctx->stream;
+    int64_t* d_rows = nullptr;
+    double* d_out = nullptr;
+    if (cudaMalloc(&d_rows, sizeof(int64_t) * n_sample) != cudaSuccess ||
+        cudaMalloc(&d_out, sizeof(double) * 4 * n_sample) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(d_rows);
+        return set_error(ctx, FDPS_ENOMEM, "sample allocation failed");
+    }
+    std::vector<double> h(4 * (size_t)n_sample);
+    int rc = cudaMemcpyAsync(d_rows, rows, sizeof(int64_t) * n_sample, cudaMemcpyHostToDevice, s) == cudaSuccess
+                 ? direct_sample_device(ps, n_sample, d_rows, d_out)
+                 : set_error(ctx, FDPS_ECUDA, "row copy failed");
+    if (!rc && cudaMemcpy(h.data(), d_out, sizeof(double) * 4 * n_sample, cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = set_error(ctx, FDPS_ECUDA, "result copy failed");
+    cudaFree(d_rows);
+    cudaFree(d_out);
+    if (rc) return rc;
+    for (int64_t k = 0; k < n_sample; ++k) {
+        if (acc3)
+            for (int a = 0; a < 3; ++a) acc3[3 * k + a] = h[4 * k + a];
+        if (pot) pot[k] = h[4 * k + 3];
+    }
+    return FDPS_OK;
+}
+
+int fdps_tree_choose_theta(fdps_tree* t, fdps_psys* ps, double target, int64_t n_sample,
+                           const double* candidates, int32_t n_candidates, double* theta_out,
+                           double* median_out) {
+    if (!t || !ps || !(target > 0.0) || n_sample < 1 || (candidates && n_candidates < 1)) return FDPS_EINVAL;
+    fdps_ctx* ctx = t->ctx;
+    if (ps->ctx != ctx) return set_error(ctx, FDPS_EINVAL, "tree and particle system belong to different contexts");
+    if (!ps->has_data) return set_error(ctx, FDPS_ESTATE, "particle data not set");
+    std::vector<double> cand;
+    if (candidates) {
+        cand.assign(candidates, candidates + n_candidates);
+    } else {
+        for (int k = 2; k <= 10; ++k) cand.push_back(0.1 * k);
+    }
+    for (double c : cand)
+        if (!(c >= 0.0 && c < 1e6)) return set_error(ctx, FDPS_EINVAL, "candidate opening angle %g", c);
+    std::sort(cand.begin(), cand.end());
+    cudaSetDevice(ctx->device);
+    const int64_t ns = std::min<int64_t>(n_sample, ps->n);
+    std::vector<int64_t> rows(ns);
+    for (int64_t k = 0; k < ns; ++k) rows[k] = (int64_t)(((__int128)k * ps->n) / ns);  // evenly spaced rows
+    int64_t* d_rows = nullptr;
+    double *d_ref = nullptr, *d_tree = nullptr;
+    if (cudaMalloc(&d_rows, sizeof(int64_t) * ns) != cudaSuccess ||
+        cudaMalloc(&d_ref, sizeof(double) * 4 * ns) != cudaSuccess ||
+        cudaMalloc(&d_tree, sizeof(double) * 4 * ns) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(d_rows);
+        cudaFree(d_ref);
+        return set_error(ctx, FDPS_ENOMEM, "sample allocation failed");
+    }
+    const int k_spj = t->p.moment == FDPS_QUADRUPOLE ? FDPS_GRAV_SPJ_QUAD : FDPS_GRAV_SPJ_MONO;
+    const double theta0 = t->p.theta;
+    std::vector<double> ref(4 * ns), got(4 * ns), err(ns);
+    int rc = cudaMemcpy(d_rows, rows.data(), sizeof(int64_t) * ns, cudaMemcpyHostToDevice) == cudaSuccess
+                 ? direct_sample_device(ps, ns, d_rows, d_ref)
+                 : set_error(ctx, FDPS_ECUDA, "row copy failed");
+    if (!rc && cudaMemcpy(ref.data(), d_ref, sizeof(double) * 4 * ns, cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = set_error(ctx, FDPS_ECUDA, "result copy failed");
+    double best = cand.front(), best_med = -1.0;
+    for (size_t q = 0; !rc && q < cand.size(); ++q) {
+        t->p.theta = cand[q];
+        if ((rc = run_force(t, ps, k_spj))) break;
+        if ((rc = gather_rows_device(ps, ns, d_rows, d_tree))) break;
+        if (cudaMemcpy(got.data(), d_tree, sizeof(double) * 4 * ns, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            rc = set_error(ctx, FDPS_ECUDA, "result copy failed");
+            break;
+        }
+        for (int64_t k = 0; k < ns; ++k) {
+            double dn = 0.0, rn = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                const double d = got[4 * k + a] - ref[4 * k + a];
+                dn += d * d;
+                rn += ref[4 * k + a] * ref[4 * k + a];
+            }
+            err[k] = rn > 0.0 ? std::sqrt(dn / rn) : std::sqrt(dn);
+        }
+        std::nth_element(err.begin(), err.begin() + ns / 2, err.end());
+        const double med = err[ns / 2];
+        if (q == 0 || med <= target) {
+            best = cand[q];
+            best_med = med;
+        }
+        if (med > target) break;  // larger angles only lose accuracy
+    }
+    cudaFree(d_rows);
+    cudaFree(d_ref);
+    cudaFree(d_tree);
+    if (rc) {
+        t->p.theta = theta0;
+        return rc;
+    }
+    t->p.theta = best;
+    if ((rc = run_force(t, ps, k_spj))) return rc;  // leave the forces of the chosen angle
+    if (theta_out) *theta_out = best;
+    if (median_out) *median_out = best_med;
+    return FDPS_OK;
 }
 
 int fdps_tree_build_lists(fdps_tree* t, fdps_psys* ps) {

@@ -274,6 +274,10 @@ int build_tree(fdps_tree* t, fdps_psys* ps);           // build.cu
 int compute_moments(fdps_tree* t, fdps_psys* ps);      // build.cu
 int select_groups(fdps_tree* t, fdps_psys* ps);        // build.cu
 int compute_forces(fdps_tree* t, fdps_psys* ps, int spj_kind);  // force.cu
+// sampled rows (caller rows, device array): FP32-compensated direct sums
+// and the last tree results, each as (ax, ay, az, phi) per row in d_out4
+int direct_sample_device(fdps_psys* ps, int64_t ns, const int64_t* d_rows, double* d_out4);  // direct.cu
+int gather_rows_device(fdps_psys* ps, int64_t ns, const int64_t* d_rows, double* d_out4);    // direct.cu
 int launch_kick(fdps_psys* ps, double dt_half);        // integrate.cu
 int launch_kick_guarded(fdps_psys* ps, double dt_half, const uint32_t* flags, uint32_t mask);
 int launch_drift(fdps_psys* ps, double dt);            // integrate.cu
