@@ -60,6 +60,10 @@ def parse():
                     help="the ensemble workload: 4096 Plummer clusters, N log-uniform in "
                          "[256, 65536], eps = 1/(4 N^1/3), theta 0.5 monopole, dt 1/256")
     ap.add_argument("--n-sys", type=int, default=4096)
+    ap.add_argument("--theta-target", type=float, default=None,
+                    help="choose the opening angle whose median force error against the GPU direct "
+                         "sum on --n-sample rows meets this target (one JSON line)")
+    ap.add_argument("--n-sample", type=int, default=4096)
     ap.add_argument("--suite", action="store_true",
                     help="one JSON line per workload configuration: Plummer 2^20 (10 steps), "
                          "Hernquist 2^24 at theta 0.3/0.5/0.7, clumpy 2^26; with force errors "
@@ -572,6 +576,44 @@ def run_config(G, torch, name, model, n, eps, theta, quad, n_leaf, n_grp, steps,
     print(json.dumps(line), flush=True)
 
 
+def run_theta_target(args):
+    """The opening angle chosen for a median acceleration-error target on the
+    benchmark workload: time of the direct-sum reference and of the choice,
+    and the forces' error at the choice (against the GPU direct sum)."""
+    import torch
+    import paper_1601_03138_gb300 as G
+    from paper_1601_03138_gb300 import build as B
+    B.build()
+    pos, vel, mass, eps = make_inputs(args)
+    n = len(pos)
+    ctx = G.Context(0)
+    ctx.set_profiling(True)
+    ps = G.ParticleSystem(ctx, n)
+    tree = G.Tree(ctx, theta=args.theta, n_leaf=args.n_leaf, n_grp=args.n_grp, quad=not args.mono)
+    ps.set(pos, vel, mass, eps)
+    rows = (np.arange(min(args.n_sample, n), dtype=np.int64) * n) // min(args.n_sample, n)
+    t0 = time.perf_counter()
+    ad, _ = ps.direct(rows)
+    t_direct = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    theta, med = tree.choose_theta(ps, args.theta_target, args.n_sample)
+    t_choose = time.perf_counter() - t0
+    _, _, acc, _ = ps.get()
+    err = np.linalg.norm(acc[rows] - ad, axis=1) / np.linalg.norm(ad, axis=1)
+    st = tree.stats()
+    line = {"metric": "opening angle for a median force-error target",
+            "workload": workload_name(args), "target_median": args.theta_target,
+            "theta": theta, "median": med, "rms": float(np.sqrt(np.mean(err ** 2))),
+            "p99": float(np.quantile(err, 0.99)), "n_sample": int(len(rows)),
+            "direct_sample_s": t_direct, "direct_interactions_per_s": len(rows) * (n - 1) / t_direct,
+            "choose_theta_s": t_choose, "force_ms_at_choice": st["ms_force"],
+            "interactions_at_choice": st["interactions_epj"] + st["interactions_spj"]}
+    print(json.dumps(line), flush=True)
+    tree.close()
+    ps.close()
+    ctx.close()
+
+
 def run_suite(args):
     import torch
     import ics
@@ -609,6 +651,10 @@ def main():
     if args.suite:
         if rank == 0:
             run_suite(args)
+        return
+    if args.theta_target is not None:
+        if rank == 0:
+            run_theta_target(args)
         return
     if world > 1:
         import torch
