@@ -90,6 +90,11 @@ def lib():
         L.orc_tree_walk.restype = C.c_int64
         L.orc_tree_force.argtypes = [C.c_void_p, _i64, C.c_int64, _d, _d, _i64]
         L.orc_direct.argtypes = [C.c_int64, _d, _d, _d, _i64, C.c_int64, _d, _d]
+        L.orc_wendland_c6.argtypes = [C.c_double, C.c_double]
+        L.orc_wendland_c6.restype = C.c_double
+        L.orc_wendland_c6_array.argtypes = [C.c_int64, _d, C.c_double, _d]
+        L.orc_neighbors.argtypes = [C.c_int64, _d, _d, _d, C.c_int32, C.c_double, _i64, C.c_int64,
+                                    _i64, _d]
         L.orc_kick.argtypes = [C.c_int64, _d, _d, C.c_double]
         L.orc_drift.argtypes = [C.c_int64, _d, _d, C.c_double]
         L.orc_energy.argtypes = [C.c_int64, _d, _d, _d, _d]
@@ -199,6 +204,38 @@ def direct(pos, mass, eps, idx=None):
     lib().orc_direct(n, _p(pos, C.c_double), _p(mass, C.c_double), _p(eps, C.c_double),
                      ip, ni, _p(acc, C.c_double), _p(pot, C.c_double))
     return acc, pot
+
+
+# cutoff types of the short-range interaction
+FIXED, GATHER, SCATTER, SYMMETRIC = 0, 1, 2, 3
+
+
+def wendland_c6(r, H):
+    """Wendland C6 kernel in 3D with support radius H (Sect. 4.3's SPH kernel)."""
+    r = np.ascontiguousarray(np.atleast_1d(r), dtype=np.float64)
+    out = np.zeros_like(r)
+    lib().orc_wendland_c6_array(len(r), _p(r, C.c_double), float(H), _p(out, C.c_double))
+    return out
+
+
+def neighbors(pos, mass, h, mode, r_fixed=0.0, idx=None):
+    """Short-range mode, brute force: (neighbour counts, SPH density) of the
+    rows idx (all if None) for cutoff type mode (FIXED, GATHER, SCATTER,
+    SYMMETRIC); a particle is its own neighbour."""
+    pos = _f64(pos, (-1, 3))
+    mass = _f64(mass)
+    h = _f64(h) if h is not None else np.zeros(len(pos))
+    n = len(pos)
+    if idx is None:
+        ni, ip = n, None
+    else:
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        ni, ip = len(idx), _p(idx, C.c_int64)
+    cnt = np.zeros(ni, np.int64)
+    rho = np.zeros(ni)
+    lib().orc_neighbors(n, _p(pos, C.c_double), _p(mass, C.c_double), _p(h, C.c_double), int(mode),
+                        float(r_fixed), ip, ni, _p(cnt, C.c_int64), _p(rho, C.c_double))
+    return cnt, rho
 
 
 def kick(vel, acc, dt_half):

@@ -17,7 +17,8 @@
  *   ParticleSuperparticleNbody, Sect. 2.2) -> leapfrog kick/drift (Sect. 2.2,
  *   the predict/correct member functions of the N-body example).
  * Plus the exact reference: an O(N^2) FP64 direct sum of the same softened
- * pair force.
+ * pair force; and the short-range mode's brute-force neighbour counts and
+ * SPH density (Wendland C6) for the paper's four cutoff types.
  *
  * The paper fixes the force law and the Barnes-Hut structure but not the key
  * scheme, the tree rules, the opening criterion, the quadrupole convention,
@@ -671,6 +672,64 @@ void orc_direct(int64_t n, const double* pos, const double* mass,
         }
         for (int a = 0; a < 3; ++a) acc[3 * k + a] = ai[a];
         pot[k] = phi;
+    }
+}
+
+/* ------------------------------------------------- short-range mode (S) */
+/*
+ * The short-range interaction (Sect. 2.1.2, 3.2): particle j is a neighbour
+ * of particle i (j = i included, at zero separation) iff r^2 < c^2, with
+ * r^2 = (dx*dx + dy*dy) + dz*dz, dx = x_j - x_i, each operation rounded on
+ * its own, and the cutoff c of the paper's four types:
+ *   mode 0 fixed:        c = r_fixed
+ *   mode 1 i-dependent:  c = h_i         (gather)
+ *   mode 2 j-dependent:  c = h_j         (scatter)
+ *   mode 3 symmetric:    c = max(h_i, h_j)
+ * The workload on the neighbours is the SPH density with the Wendland C6
+ * kernel the paper uses for its SPH runs (Sect. 4.3): rho_i = sum_j m_j
+ * W(r, H) with H = r_fixed, h_i, h_j respectively, and for the symmetric
+ * type the mean of W(r, h_i) and W(r, h_j).  Brute force over all pairs.
+ */
+double orc_wendland_c6(double r, double H) {
+    if (!(H > 0.0)) return 0.0;
+    double q = r / H;
+    if (q >= 1.0) return 0.0;
+    double u = 1.0 - q, u2 = u * u, u4 = u2 * u2, u8 = u4 * u4;
+    double poly = 1.0 + q * (8.0 + q * (25.0 + q * 32.0));
+    const double pi = 3.14159265358979323846;
+    return 1365.0 / (64.0 * pi * H * H * H) * u8 * poly;
+}
+
+void orc_wendland_c6_array(int64_t n, const double* r, double H, double* out) {
+    for (int64_t k = 0; k < n; ++k) out[k] = orc_wendland_c6(r[k], H);
+}
+
+void orc_neighbors(int64_t n, const double* pos, const double* mass, const double* h,
+                   int32_t mode, double r_fixed, const int64_t* idx, int64_t ni,
+                   int64_t* count, double* rho) {
+    int64_t m_i = idx ? ni : n;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t k = 0; k < m_i; ++k) {
+        int64_t i = idx ? idx[k] : k;
+        int64_t cnt = 0;
+        double sum = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            double dx = pos[3 * j] - pos[3 * i];
+            double dy = pos[3 * j + 1] - pos[3 * i + 1];
+            double dz = pos[3 * j + 2] - pos[3 * i + 2];
+            double r2 = dx * dx + dy * dy + dz * dz;
+            double c = mode == 0 ? r_fixed : mode == 1 ? h[i] : mode == 2 ? h[j] : (h[i] > h[j] ? h[i] : h[j]);
+            if (!(r2 < c * c)) continue;
+            ++cnt;
+            double r = sqrt(r2);
+            double w = mode == 0 ? orc_wendland_c6(r, r_fixed)
+                     : mode == 1 ? orc_wendland_c6(r, h[i])
+                     : mode == 2 ? orc_wendland_c6(r, h[j])
+                                 : 0.5 * (orc_wendland_c6(r, h[i]) + orc_wendland_c6(r, h[j]));
+            sum += mass[j] * w;
+        }
+        count[k] = cnt;
+        rho[k] = sum;
     }
 }
 

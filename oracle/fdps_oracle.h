@@ -50,6 +50,14 @@ void orc_tree_force(const orc_tree* t, const int64_t* gidx, int64_t ng,
 void orc_direct(int64_t n, const double* pos, const double* mass,
                 const double* eps, const int64_t* idx, int64_t ni,
                 double* acc, double* pot);
+/* short-range mode: Wendland C6 kernel (3D, support radius H) and the
+   brute-force neighbour counts and SPH density of rows idx (all if NULL);
+   mode 0 fixed r_fixed, 1 h_i, 2 h_j, 3 max(h_i, h_j) */
+double orc_wendland_c6(double r, double H);
+void orc_wendland_c6_array(int64_t n, const double* r, double H, double* out);
+void orc_neighbors(int64_t n, const double* pos, const double* mass, const double* h,
+                   int32_t mode, double r_fixed, const int64_t* idx, int64_t ni,
+                   int64_t* count, double* rho);
 void orc_kick(int64_t n, double* vel, const double* acc, double dt_half);
 void orc_drift(int64_t n, double* pos, const double* vel, double dt);
 void orc_energy(int64_t n, const double* vel, const double* mass,
