@@ -274,6 +274,37 @@ int fdps_tree_get_groups(const fdps_tree* tree, int64_t cap, int64_t* n_out,
 int fdps_tree_get_lists(const fdps_tree* tree, int64_t g0, int64_t g1,
                         int64_t* offsets, uint32_t* entries, int64_t cap);
 
+/* ---------------------------------------------- short-range mode
+   Neighbour search over the same tree (Sect. 2.1.2, 3.2) for FDPS's four
+   cutoff types, with the SPH density of the paper's SPH runs (Wendland C6
+   kernel, Sect. 4.3) as the work on the neighbours.  Particle j is a
+   neighbour of i (i itself included) iff r^2 < c^2, r^2 evaluated in FP64
+   as (dx*dx + dy*dy) + dz*dz with each operation rounded on its own, and
+     FDPS_CUTOFF_FIXED      c = r_fixed
+     FDPS_CUTOFF_I          c = h_i            (gather)
+     FDPS_CUTOFF_J          c = h_j            (scatter)
+     FDPS_CUTOFF_SYMMETRIC  c = max(h_i, h_j)
+   rho_i = sum over the neighbours of m_j W(r, H), W the 3D Wendland C6
+   kernel with support H = r_fixed, h_i or h_j (symmetric: the mean of
+   W(r, h_i) and W(r, h_j)), evaluated in FP32.
+     h        [n] cutoff radii in the caller's order (host, or device with
+              h_on_device = 1); ignored (may be NULL) for the fixed type
+     counts   [n] neighbour counts, rho [n] densities, in the caller's order
+              (host, or device with out_on_device = 1); either may be NULL
+     info3    optional host [3]: neighbour pairs, candidate pairs tested,
+              pairs decided by the FP64 sequence
+   The tree's n_leaf and n_grp apply; the tree's lists afterwards hold the
+   neighbour candidates (opened leaves), not gravity lists.  Synchronous.
+   Errors: FDPS_EINVAL (type, radius, NULL radii, non-positive radii),
+   FDPS_ESTATE, FDPS_ENOMEM, FDPS_EOVERFLOW, FDPS_ECUDA. */
+#define FDPS_CUTOFF_FIXED 0
+#define FDPS_CUTOFF_I 1
+#define FDPS_CUTOFF_J 2
+#define FDPS_CUTOFF_SYMMETRIC 3
+int fdps_tree_neighbors(fdps_tree* tree, fdps_psys* ps, int32_t mode, double r_fixed,
+                        const double* h, int h_on_device, uint32_t* counts, double* rho,
+                        int out_on_device, int64_t* info3);
+
 /* ------------------------------------------ accuracy diagnostics
    fdps_direct_sample: the exact reference of the force law (Eq.
    ParticleParticleNbody summed over every other particle of the same

@@ -112,6 +112,7 @@ _PROTOS = {
     "fdps_tree_build_lists": (C.c_int, [_vp, _vp]),
     "fdps_tree_get_view": (C.c_int, [_vp, _vp, C.POINTER(fdps_tree_view)]),
     "fdps_direct_sample": (C.c_int, [_vp, _i64, _vp, _vp, _vp]),
+    "fdps_tree_neighbors": (C.c_int, [_vp, _vp, _i32, _d, _vp, C.c_int, _vp, _vp, C.c_int, _vp]),
     "fdps_tree_choose_theta": (C.c_int, [_vp, _vp, _d, _i64, _vp, _i32, C.POINTER(_d), C.POINTER(_d)]),
     "fdps_user_law_compile": (C.c_int, [_vp, C.c_char_p, C.POINTER(_vp), C.c_char_p, _i64]),
     "fdps_user_law_force_size": (_i64, [_vp]),
@@ -387,6 +388,23 @@ def fdps_tree_get_view(ctx, tree, ps) -> dict:
             for k, v in v.as_dict().items()}
 
 
+FDPS_CUTOFF_FIXED, FDPS_CUTOFF_I, FDPS_CUTOFF_J, FDPS_CUTOFF_SYMMETRIC = 0, 1, 2, 3
+
+
+def fdps_tree_neighbors(ctx, tree, ps, n, mode, r_fixed=0.0, h=None):
+    """(counts [n] uint32, rho [n], info: neighbour pairs, candidates, FP64
+    decisions) of the short-range mode, in the caller's order; h on the host
+    or as a CUDA tensor."""
+    counts = np.zeros(n, np.uint32)
+    rho = np.zeros(n)
+    info = np.zeros(3, np.int64)
+    hp, hdev = _ptr(None if h is None else (h if hasattr(h, "data_ptr") else np.ascontiguousarray(h, np.float64)))
+    _check(lib().fdps_tree_neighbors(tree, ps, int(mode), float(r_fixed), hp, 1 if hdev else 0,
+                                     C.c_void_p(counts.ctypes.data), C.c_void_p(rho.ctypes.data), 0,
+                                     C.c_void_p(info.ctypes.data)), ctx)
+    return counts, rho, info
+
+
 def fdps_direct_sample(ctx, ps, rows):
     """(acc [k][3], pot [k]) of the direct sum for the caller's rows."""
     r = np.ascontiguousarray(rows, dtype=np.int64)
@@ -590,6 +608,10 @@ class Tree:
 
     def lists(self, g0, g1):
         return fdps_tree_get_lists(self.ctx.h, self.h, g0, g1)
+
+    def neighbors(self, psys: ParticleSystem, mode: int, h=None, r_fixed: float = 0.0):
+        """Short-range mode: (neighbour counts, SPH density, info) per particle."""
+        return fdps_tree_neighbors(self.ctx.h, self.h, psys.h, psys.n, mode, r_fixed, h)
 
     def choose_theta(self, psys: ParticleSystem, target: float, n_sample: int = 4096, candidates=None):
         return fdps_tree_choose_theta(self.ctx.h, self.h, psys.h, target, n_sample, candidates)

@@ -228,7 +228,7 @@ int launch_force_pipeline(fdps_tree* t, fdps_psys* ps, int k_spj) {
     return compute_forces(t, ps, k_spj);
 }
 
-int run_force(fdps_tree* t, fdps_psys* ps, int k_spj, bool lists_only = false) {
+int run_tree_stages(fdps_tree* t, fdps_psys* ps) {
     fdps_ctx* ctx = t->ctx;
     const int64_t n = ps->n;
     int rc;
@@ -272,6 +272,14 @@ int run_force(fdps_tree* t, fdps_psys* ps, int k_spj, bool lists_only = false) {
         k_reset_counters<<<1, 32, 0, s>>>(t->st, 4);
         FDPS_LAUNCH_CHECK(ctx);
     }
+    return FDPS_OK;
+}
+
+int run_force(fdps_tree* t, fdps_psys* ps, int k_spj, bool lists_only = false) {
+    fdps_ctx* ctx = t->ctx;
+    int rc;
+    if ((rc = run_tree_stages(t, ps))) return rc;
+    cudaStream_t s = ctx->stream;
     const int wblocks = (int)(t->n_walk_warps / walk_warps_per_block());
     for (int attempt = 0;; ++attempt) {
         k_reset_counters<<<1, 32, 0, s>>>(t->st, 1);
@@ -319,6 +327,11 @@ bool valid_params(const fdps_tree_params* p) {
 }
 
 }  // namespace
+
+namespace fdps {
+int run_tree(fdps_tree* t, fdps_psys* ps) { return run_tree_stages(t, ps); }
+int read_device_state(fdps_tree* t) { return read_state(t); }
+}  // namespace fdps
 
 extern "C" {
 
@@ -576,6 +589,9 @@ int fdps_tree_destroy(fdps_tree* t) {
     dev_free(t->grp_scan);
     dev_free(t->sort_dtot);
     dev_free(t->sys_box);
+    dev_free(t->sr_h);
+    dev_free(t->nd_hmax);
+    dev_free(t->g_hmax);
     for (int k = 0; k < 10; ++k)
         if (t->ev[k]) cudaEventDestroy(t->ev[k]);
     delete t;
@@ -704,6 +720,108 @@ int fdps_tree_choose_theta(fdps_tree* t, fdps_psys* ps, double target, int64_t n
     if ((rc = run_force(t, ps, k_spj))) return rc;  // leave the forces of the chosen angle
     if (theta_out) *theta_out = best;
     if (median_out) *median_out = best_med;
+    return FDPS_OK;
+}
+
+int fdps_tree_neighbors(fdps_tree* t, fdps_psys* ps, int32_t mode, double r_fixed, const double* h,
+                        int h_on_device, uint32_t* counts, double* rho, int out_on_device, int64_t* info3) {
+    if (!t || !ps) return FDPS_EINVAL;
+    fdps_ctx* ctx = t->ctx;
+    if (ps->ctx != ctx) return set_error(ctx, FDPS_EINVAL, "tree and particle system belong to different contexts");
+    if (mode < FDPS_CUTOFF_FIXED || mode > FDPS_CUTOFF_SYMMETRIC)
+        return set_error(ctx, FDPS_EINVAL, "unknown cutoff type %d", (int)mode);
+    if (mode == FDPS_CUTOFF_FIXED && !(r_fixed > 0.0 && r_fixed < 1e300))
+        return set_error(ctx, FDPS_EINVAL, "the fixed cutoff needs a positive finite radius");
+    if (mode != FDPS_CUTOFF_FIXED && !h) return set_error(ctx, FDPS_EINVAL, "this cutoff type needs radii");
+    if (!ps->has_data) return set_error(ctx, FDPS_ESTATE, "particle data not set");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = ctx->stream;
+    const int64_t n = ps->n;
+    int rc;
+    if ((rc = run_tree_stages(t, ps))) return rc;
+    t->lists_of = nullptr;  // the pool will hold neighbour lists, not gravity lists
+    double* d_h = nullptr;
+    uint32_t* d_cnt = nullptr;
+    double* d_rho = nullptr;
+    unsigned long long* d_info = nullptr;
+    auto cleanup = [&]() {
+        if (d_h && !h_on_device) cudaFree(d_h);
+        if (d_cnt && !out_on_device) cudaFree(d_cnt);
+        if (d_rho && !out_on_device) cudaFree(d_rho);
+        cudaFree(d_info);
+    };
+    if (mode != FDPS_CUTOFF_FIXED) {
+        if (h_on_device) {
+            d_h = const_cast<double*>(h);
+        } else if (cudaMalloc(&d_h, sizeof(double) * n) != cudaSuccess ||
+                   cudaMemcpyAsync(d_h, h, sizeof(double) * n, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+            cudaGetLastError();
+            cleanup();
+            return set_error(ctx, FDPS_ENOMEM, "radii transfer failed");
+        }
+    }
+    if ((rc = short_prepare(t, ps, mode, d_h))) {
+        cleanup();
+        return rc;
+    }
+    const int wblocks = (int)(t->n_walk_warps / walk_warps_per_block());
+    for (int attempt = 0;; ++attempt) {
+        k_reset_counters<<<1, 32, 0, s>>>(t->st, 1);
+        FDPS_LAUNCH_CHECK(ctx);
+        if ((rc = launch_short_walk(t, ps, mode, r_fixed, wblocks)) || (rc = read_state(t))) {
+            cleanup();
+            return rc;
+        }
+        const uint32_t ov = t->h_st.overflow;
+        if (!(ov & (kOvfPool | kOvfFrontier))) break;
+        if (attempt > 8) {
+            cleanup();
+            return set_error(ctx, FDPS_EOVERFLOW, "neighbour lists did not fit after %d resizes", attempt);
+        }
+        ++t->retries;
+        if ((ov & kOvfFrontier) && (rc = ensure_frontier(t, 2 * t->cap_frontier))) {
+            cleanup();
+            return rc;
+        }
+        if (ov & kOvfPool) {
+            const int64_t need = (int64_t)(t->h_st.pool_needed * 3 / 2) +
+                                 2 * t->n_walk_warps * (int64_t)walk_chunk();
+            if ((rc = ensure_pool(t, std::max<int64_t>(need, 2 * t->cap_pool)))) {
+                cleanup();
+                return rc;
+            }
+        }
+    }
+    if (out_on_device) {
+        d_cnt = counts;
+        d_rho = rho;
+    }
+    if ((!d_cnt && cudaMalloc(&d_cnt, sizeof(uint32_t) * n) != cudaSuccess) ||
+        (!d_rho && cudaMalloc(&d_rho, sizeof(double) * n) != cudaSuccess) ||
+        cudaMalloc(&d_info, sizeof(unsigned long long) * 3) != cudaSuccess ||
+        cudaMemsetAsync(d_info, 0, sizeof(unsigned long long) * 3, s) != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        return set_error(ctx, FDPS_ENOMEM, "neighbour output allocation failed");
+    }
+    k_reset_counters<<<1, 32, 0, s>>>(t->st, 2);
+    FDPS_LAUNCH_CHECK(ctx);
+    if ((rc = launch_short_pairs(t, ps, mode, r_fixed, d_cnt, d_rho, d_info))) {
+        cleanup();
+        return rc;
+    }
+    unsigned long long hinfo[3] = {0, 0, 0};
+    cudaError_t e = cudaMemcpyAsync(hinfo, d_info, sizeof(hinfo), cudaMemcpyDeviceToHost, s);
+    if (!out_on_device) {
+        if (!e && counts) e = cudaMemcpyAsync(counts, d_cnt, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, s);
+        if (!e && rho) e = cudaMemcpyAsync(rho, d_rho, sizeof(double) * n, cudaMemcpyDeviceToHost, s);
+    }
+    const cudaError_t e2 = cudaStreamSynchronize(s);
+    cleanup();
+    if (e || e2) return set_error(ctx, FDPS_ECUDA, "neighbour results copy failed");
+    if (info3)
+        for (int k = 0; k < 3; ++k) info3[k] = (int64_t)hinfo[k];
+    t->valid = true;
     return FDPS_OK;
 }
 

@@ -146,6 +146,14 @@ struct fdps_tree {
     uint32_t* perm = nullptr;      // result of the sort (points into vals_*)
     uint64_t* keys_sorted = nullptr;
     const fdps_psys* lists_of = nullptr;  // particle system of the current lists
+    // short-range mode: cutoff radii in key order, per-node and per-group
+    // maxima of the radii
+    double* sr_h = nullptr;
+    int64_t cap_sr_h = 0;
+    double* nd_hmax = nullptr;
+    int64_t cap_nd_hmax = 0;
+    double* g_hmax = nullptr;
+    int64_t cap_g_hmax = 0;
     uint32_t* sort_hist = nullptr; // [256][tiles]
     uint32_t* sort_dtot = nullptr; // [4096]: digit totals / bases of every pass, tile counters
     int64_t cap_tiles = 0;
@@ -265,6 +273,10 @@ inline int grid_for(int64_t n, int block, int max_blocks) {
 // --------------------------------------------------------- stage entry points
 // (host functions, one per .cu file; all issue work on ctx->stream)
 
+// S0-S6 of a force calculation (root box to i-groups, resizing on
+// overflow) and a synchronous read of the device state word (api.cu)
+int run_tree(fdps_tree* t, fdps_psys* ps);
+int read_device_state(fdps_tree* t);
 int keys_and_sort(fdps_tree* t, fdps_psys* ps);        // keys_sort.cu
 int launch_sys_index(fdps_psys* ps);                   // integrate.cu
 int launch_energy_systems(fdps_psys* ps, double* kin, double* pot);  // integrate.cu
@@ -277,6 +289,13 @@ int compute_forces(fdps_tree* t, fdps_psys* ps, int spj_kind);  // force.cu
 // sampled rows (caller rows, device array): FP32-compensated direct sums
 // and the last tree results, each as (ax, ay, az, phi) per row in d_out4
 int direct_sample_device(fdps_psys* ps, int64_t ns, const int64_t* d_rows, double* d_out4);  // direct.cu
+// short-range mode (short.cu): cutoff radii into key order (h_user: device,
+// caller order) and their node and group maxima; the neighbour walk; the
+// pair pass writing counts and densities in the caller's order.
+int short_prepare(fdps_tree* t, fdps_psys* ps, int mode, const double* h_user);
+int launch_short_walk(fdps_tree* t, fdps_psys* ps, int mode, double r_fixed, int blocks);
+int launch_short_pairs(fdps_tree* t, fdps_psys* ps, int mode, double r_fixed, uint32_t* count,
+                       double* rho, unsigned long long* info3);
 int gather_rows_device(fdps_psys* ps, int64_t ns, const int64_t* d_rows, double* d_out4);    // direct.cu
 int launch_kick(fdps_psys* ps, double dt_half);        // integrate.cu
 int launch_kick_guarded(fdps_psys* ps, double dt_half, const uint32_t* flags, uint32_t mask);
