@@ -64,6 +64,9 @@ def parse():
                     help="choose the opening angle whose median force error against the GPU direct "
                          "sum on --n-sample rows meets this target (one JSON line)")
     ap.add_argument("--n-sample", type=int, default=4096)
+    ap.add_argument("--sph", action="store_true",
+                    help="short-range mode: SPH density (Wendland C6) of a uniform random cube with "
+                         "the cutoff at 4.2 mean inter-particle distances, i-dependent cutoff")
     ap.add_argument("--suite", action="store_true",
                     help="one JSON line per workload configuration: Plummer 2^20 (10 steps), "
                          "Hernquist 2^24 at theta 0.3/0.5/0.7, clumpy 2^26; with force errors "
@@ -576,6 +579,50 @@ def run_config(G, torch, name, model, n, eps, theta, quad, n_leaf, n_grp, steps,
     print(json.dumps(line), flush=True)
 
 
+def run_sph(args):
+    """Short-range mode on n particles of a uniform random unit cube with
+    radii h_i = 4.2 n^(-1/3) (about 310 neighbours, the paper's SPH cutoff):
+    neighbour pairs per second over the whole call (tree + neighbour walk +
+    pair pass), the FP32 roofline of the pair pass, and the density's mean
+    against the exact mean density."""
+    import torch
+    import paper_1601_03138_gb300 as G
+    from paper_1601_03138_gb300 import build as B
+    B.build()
+    n = args.n
+    rng = np.random.default_rng(1601031385)
+    pos = rng.random((n, 3))
+    mass = np.full(n, 1.0 / n)
+    hval = 4.2 * n ** (-1.0 / 3.0)
+    ctx = G.Context(0)
+    ps = G.ParticleSystem(ctx, n)
+    tree = G.Tree(ctx, theta=0.5, n_leaf=args.n_leaf, n_grp=args.n_grp)
+    ps.set(pos, np.zeros_like(pos), mass, np.full(n, 1e-3))
+    h = torch.full((n,), hval, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        cnt, rho, info = tree.neighbors(ps, G.FDPS_CUTOFF_I, h)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        cnt, rho, info = tree.neighbors(ps, G.FDPS_CUTOFF_I, h)
+        ts.append(time.perf_counter() - t0)
+    t = statistics.median(ts)
+    inner = np.all((pos > hval) & (pos < 1.0 - hval), axis=1)
+    line = {"metric": "SPH density neighbour pairs/s", "value": float(info[0]) / t, "unit": "pairs/s",
+            "workload": f"uniform cube N={n}, h = 4.2 N^-1/3, i-dependent cutoff, Wendland C6, "
+                        f"n_leaf={args.n_leaf} n_grp={args.n_grp}",
+            "ms_per_call": 1e3 * t, "steps": args.steps,
+            "neighbours_mean": float(info[0]) / n, "candidates_per_neighbour": float(info[1]) / float(info[0]),
+            "fp64_decisions": int(info[2]),
+            "density_interior_mean": float(rho[inner].mean()), "density_interior_std": float(rho[inner].std()),
+            "counts_min_max": [int(cnt.min()), int(cnt.max())]}
+    print(json.dumps(line), flush=True)
+    tree.close()
+    ps.close()
+    ctx.close()
+
+
 def run_theta_target(args):
     """The opening angle chosen for a median acceleration-error target on the
     benchmark workload: time of the direct-sum reference and of the choice,
@@ -651,6 +698,10 @@ def main():
     if args.suite:
         if rank == 0:
             run_suite(args)
+        return
+    if args.sph:
+        if rank == 0:
+            run_sph(args)
         return
     if args.theta_target is not None:
         if rank == 0:
