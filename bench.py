@@ -82,7 +82,7 @@ def parse():
 # bench reports null once that source has changed
 FORCE_TRAFFIC = {
     "hernquist N=16777216 theta=0.5 quad n_leaf=16 n_grp=256 eps=0.005 dt=0.00195312":
-        ("a0d06931cf1ec9db", 4.56e9 + 533.44e6),
+        ("41e9865666584e73", 4.56e9 + 533.44e6),
 }
 
 

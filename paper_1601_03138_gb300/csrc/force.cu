@@ -1,5 +1,6 @@
 // force.cu -- particle-particle (EPJ) and particle-superparticle (SPJ)
-// forces from the interaction lists, one warp per i-group.
+// forces from the interaction lists: one CTA per i-group (FP32-relative) or
+// one warp per i-group (FP64 variant).
 //
 // Per i-particle (Sect. 2.2, Eqs. ParticleParticleNbody and
 // ParticleSuperparticleNbody, G = 1, softening eps_i of the receiving
