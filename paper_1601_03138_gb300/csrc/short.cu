@@ -284,9 +284,14 @@ __global__ void __launch_bounds__(kSBlock) k_short_pairs(ShortPairArgs A) {
         const uint32_t len = A.g_len[g];
         const float L = (float)A.box[A.sys ? A.sys[gf] : 0u].L;
         const float Eabs = 1e-13f * L;  // error of the FP64 -> FP32 hi/lo parts
-        for (uint32_t ib = 0; ib < ni; ib += 32) {
-            const uint32_t i = ib + lane;
-            const bool act = i < ni;
+        // lanes: P i-slots x nsl slices of the candidates, so that small
+        // groups keep the whole warp busy
+        const uint32_t P = ni <= 16u ? ni : 32u;
+        const uint32_t nsl = 32u / P;
+        const uint32_t ip = lane % P, sl = lane / P;
+        for (uint32_t ib = 0; ib < ni; ib += P) {
+            const uint32_t i = ib + ip;
+            const bool act = sl < nsl && i < ni;
             const uint32_t pi = gf + (act ? i : 0u);
             const float4 ih = A.pf_hi[pi], il = A.pf_lo[pi];
             const double hi64 = A.h ? A.h[pi] : A.r_fixed;
@@ -326,8 +331,9 @@ __global__ void __launch_bounds__(kSBlock) k_short_pairs(ShortPairArgs A) {
                     }
                     __syncwarp();
                     if (act) {
-                        cands += m;
-                        for (uint32_t k = 0; k < m; ++k) {
+#pragma unroll 4
+                        for (uint32_t k = sl; k < m; k += nsl) {
+                            ++cands;
                             const float4 jh = s_h[w][k], jl = s_l[w][k];
                             const float dx = (jh.x - ih.x) + (jl.x - il.x);
                             const float dy = (jh.y - ih.y) + (jl.y - il.y);
@@ -377,10 +383,18 @@ __global__ void __launch_bounds__(kSBlock) k_short_pairs(ShortPairArgs A) {
                     }
                 }
             }
-            if (act) {
+            // the slices' partial counts and sums, into the first slice
+            uint32_t cnt_all = cnt;
+            float sum_all = sum;
+            for (uint32_t q = 1; q < nsl; ++q) {
+                const int src = (int)((ip + q * P) & 31u);
+                cnt_all += __shfl_sync(0xFFFFFFFFu, cnt, src);
+                sum_all += __shfl_sync(0xFFFFFFFFu, sum, src);
+            }
+            if (act && sl == 0) {
                 const uint32_t row = A.id[pi];
-                A.count[row] = cnt;
-                A.rho[row] = (double)sum;
+                A.count[row] = cnt_all;
+                A.rho[row] = (double)sum_all;
             }
             n_pairs += act ? cnt : 0u;
             n_cand += act ? cands : 0u;
