@@ -106,3 +106,24 @@ def test_choose_theta_meets_target(G, ctx):
     finally:
         tree.close()
         ps.close()
+
+
+def test_direct_sample_degenerate(G, ctx):
+    # a single particle feels nothing; two particles: the closed form
+    ps = G.ParticleSystem(ctx, 1)
+    try:
+        ps.set(np.array([[0.3, 0.1, -0.2]]), np.zeros((1, 3)), np.ones(1), np.full(1, 0.1))
+        acc, pot = ps.direct([0])
+        assert np.all(acc == 0.0) and pot[0] == 0.0
+    finally:
+        ps.close()
+    r, e, m1, m2 = 0.75, 0.1, 0.3, 1.7
+    ps = G.ParticleSystem(ctx, 2)
+    try:
+        ps.set(np.array([[0.0, 0.0, 0.0], [r, 0.0, 0.0]]), np.zeros((2, 3)), np.array([m1, m2]), np.full(2, e))
+        acc, pot = ps.direct([0, 1])
+        f = (r * r + e * e) ** -1.5
+        np.testing.assert_allclose(acc[:, 0], [m2 * r * f, -m1 * r * f], rtol=1e-6)
+        np.testing.assert_allclose(pot, [-m2 / np.hypot(r, e), -m1 / np.hypot(r, e)], rtol=1e-6)
+    finally:
+        ps.close()

@@ -96,3 +96,25 @@ def test_invalid_radii(G, ctx):
         with pytest.raises(G.FdpsError) as e:
             _run(G, ctx, pos, np.ones(100), h, mode, r_fixed=rf)
         assert e.value.code == G.FDPS_EINVAL
+
+
+def test_degenerate_sets(G, ctx):
+    # one particle: its own neighbour only; two particles exactly at the
+    # cutoff apart (not neighbours: strict r < c); many duplicates
+    cnt, rho, _ = _run(G, ctx, np.array([[0.1, 0.2, 0.3]]), np.array([2.0]), np.array([0.5]), 1)
+    assert cnt[0] == 1 and rho[0] == pytest.approx(2.0 * oracle.wendland_c6(0.0, 0.5)[0], rel=1e-6)
+    pos = np.array([[0.0, 0.0, 0.0], [0.5, 0.0, 0.0]])
+    for mode, h, rf in ((0, None, 0.5), (1, np.array([0.5, 0.5]), 0.0), (3, np.array([0.25, 0.5]), 0.0)):
+        cnt, rho, _ = _run(G, ctx, pos, np.ones(2), h, mode, r_fixed=rf)
+        cr, rr = oracle.neighbors(pos, np.ones(2), h, mode, r_fixed=rf)
+        np.testing.assert_array_equal(cnt.astype(np.int64), cr)
+        assert np.all(cnt == 1)
+    rng = np.random.default_rng(4)
+    pos = rng.random((3000, 3))
+    pos[:400] = pos[0]  # a level-21 leaf far above n_leaf
+    h = rng.uniform(0.05, 0.1, 3000)
+    for mode in (1, 2):
+        cnt, rho, _ = _run(G, ctx, pos, np.ones(3000), h, mode)
+        cr, rr = oracle.neighbors(pos, np.ones(3000), h, mode)
+        np.testing.assert_array_equal(cnt.astype(np.int64), cr)
+        np.testing.assert_allclose(rho, rr, rtol=1e-5)
