@@ -24,6 +24,7 @@ using namespace fdps;
 namespace {
 
 constexpr int kSortTile = 2048;
+static_assert(kSortTile == kBuildTile, "one tile count sizes the sort and build scratch");
 
 void free_particles(fdps_tree* t) {
     dev_free(t->keys_in);
@@ -35,6 +36,7 @@ void free_particles(fdps_tree* t) {
     dev_free(t->pf_lo);
     dev_free(t->head);
     dev_free(t->sort_hist);
+    dev_free(t->bt_count);
     t->cap_n = 0;
     t->cap_tiles = 0;
 }
@@ -47,7 +49,8 @@ int ensure_particles(fdps_tree* t, int64_t n) {
               dev_alloc(&t->keys_b, n) == cudaSuccess && dev_alloc(&t->vals_a, n) == cudaSuccess &&
               dev_alloc(&t->vals_b, n) == cudaSuccess && dev_alloc(&t->pf_hi, n) == cudaSuccess &&
               dev_alloc(&t->pf_lo, n) == cudaSuccess && dev_alloc(&t->head, n) == cudaSuccess &&
-              dev_alloc(&t->sort_hist, 256 * tiles) == cudaSuccess;
+              dev_alloc(&t->sort_hist, 2 * 256 * tiles) == cudaSuccess &&
+              dev_alloc(&t->bt_count, kMaxLevel * (kBuildWarps + 1) * (tiles + 1) + 32) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_particles(t);
@@ -66,7 +69,6 @@ void free_nodes(fdps_tree* t) {
     dev_free(t->nd_meta);
     dev_free(t->nd_parent);
     dev_free(t->nd_qlo);
-    dev_free(t->nd_prefix);
     dev_free(t->nd_sx);
     dev_free(t->nd_sy);
     dev_free(t->nd_sz);
@@ -76,7 +78,6 @@ void free_nodes(fdps_tree* t) {
     dev_free(t->nd_walk);
     dev_free(t->nd_fq0);
     dev_free(t->nd_fq1);
-    dev_free(t->lvl_scratch);
     t->cap_nodes = 0;
 }
 
@@ -87,12 +88,11 @@ int ensure_nodes(fdps_tree* t, int64_t cap) {
               dev_alloc(&t->nd_child, cap) == cudaSuccess && dev_alloc(&t->nd_meta, cap) == cudaSuccess &&
               dev_alloc(&t->nd_parent, cap) == cudaSuccess &&
               dev_alloc(&t->nd_qlo, cap) == cudaSuccess &&
-              dev_alloc(&t->nd_prefix, cap) == cudaSuccess && dev_alloc(&t->nd_sx, cap) == cudaSuccess &&
+              dev_alloc(&t->nd_sx, cap) == cudaSuccess &&
               dev_alloc(&t->nd_sy, cap) == cudaSuccess && dev_alloc(&t->nd_sz, cap) == cudaSuccess &&
               dev_alloc(&t->nd_com, cap) == cudaSuccess && dev_alloc(&t->nd_quad, 6 * cap) == cudaSuccess &&
               dev_alloc(&t->nd_f, 2 * cap) == cudaSuccess && dev_alloc(&t->nd_walk, cap) == cudaSuccess &&
-              dev_alloc(&t->nd_fq0, cap) == cudaSuccess && dev_alloc(&t->nd_fq1, cap) == cudaSuccess &&
-              dev_alloc(&t->lvl_scratch, 16 * cap) == cudaSuccess;
+              dev_alloc(&t->nd_fq0, cap) == cudaSuccess && dev_alloc(&t->nd_fq1, cap) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_nodes(t);
@@ -559,7 +559,6 @@ int fdps_tree_create(fdps_ctx* ctx, const fdps_tree_params* params, fdps_tree** 
     t->box_blocks = std::min(1024, ctx->sm_count * 4);
     t->n_walk_warps = (int64_t)walk_blocks(ctx) * walk_warps_per_block();
     bool ok = dev_alloc(&t->st, 1) == cudaSuccess && dev_alloc(&t->box_part, t->box_blocks) == cudaSuccess &&
-              dev_alloc(&t->lvl_scan, t->box_blocks) == cudaSuccess &&
               dev_alloc(&t->grp_scan, t->box_blocks) == cudaSuccess &&
               dev_alloc(&t->sort_dtot, 4096) == cudaSuccess;
     if (!ok) {
@@ -585,7 +584,6 @@ int fdps_tree_destroy(fdps_tree* t) {
     dev_free(t->frontier);
     dev_free(t->st);
     dev_free(t->box_part);
-    dev_free(t->lvl_scan);
     dev_free(t->grp_scan);
     dev_free(t->sort_dtot);
     dev_free(t->sys_box);

@@ -107,10 +107,10 @@ __device__ __forceinline__ bool meta_leaf(uint32_t m) { return (m >> 16) & 1u; }
 
 // Level 0: one root per system (node k = root of system k, owning
 // positions off[k] .. off[k+1]; a single root over all n if off is null).
-__global__ void k_roots(DevState* st, int n_roots, const int64_t* __restrict__ off, int64_t n,
-                        int n_leaf, uint32_t* nd_first, uint32_t* nd_count, uint32_t* nd_child,
-                        uint32_t* nd_meta, uint32_t* nd_parent, uint64_t* nd_qlo,
-                        uint64_t* nd_prefix) {
+// The other levels' nodes come from the particle-parallel kernels below.
+__global__ void k_roots(int n_roots, const int64_t* __restrict__ off, int64_t n, int n_leaf,
+                        uint32_t* nd_first, uint32_t* nd_count, uint32_t* nd_child, uint32_t* nd_meta,
+                        uint32_t* nd_parent, uint64_t* nd_qlo) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_roots; k += gridDim.x * blockDim.x) {
         const int64_t a = off ? off[k] : 0, b = off ? off[k + 1] : n;
         nd_first[k] = (uint32_t)a;
@@ -119,129 +119,283 @@ __global__ void k_roots(DevState* st, int n_roots, const int64_t* __restrict__ o
         nd_meta[k] = (b - a <= n_leaf ? 1u : 0u) << 16;
         nd_parent[k] = 0xFFFFFFFFu;
         nd_qlo[k] = 0;
-        nd_prefix[k] = 0;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        st->lvl_start[0] = 0;
-        for (int l = 1; l < kMaxLevel + 3; ++l) st->lvl_start[l] = n_roots;
-        st->n_nodes = n_roots;
-        st->max_level = 0;
     }
 }
 
-// Slot s = 8 * (parent - first parent of the level) + octant.
-__global__ void __launch_bounds__(kB) k_level_count(int l, const DevState* __restrict__ st,
-                                                    const uint64_t* __restrict__ keys,
-                                                    const uint32_t* __restrict__ nd_first,
-                                                    const uint32_t* __restrict__ nd_count,
-                                                    const uint32_t* __restrict__ nd_meta,
-                                                    uint32_t* __restrict__ slot_lb,
-                                                    uint32_t* __restrict__ slot_cnt,
-                                                    uint32_t* __restrict__ part) {
-    const int64_t P0 = st->lvl_start[l - 1], P1 = st->lvl_start[l];
-    const int64_t nslots = 8 * (P1 - P0);
-    int64_t t0, t1;
-    block_tiles(nslots, &t0, &t1);
-    const int shift = 63 - 3 * l;
-    uint32_t nonempty = 0;
-    for (int64_t t = t0; t < t1; ++t) {
-        const int64_t s = t * kB + threadIdx.x;
-        const int d = (int)(s & 7);
-        uint32_t lb = 0, end = 0;
-        bool internal = false;
-        if (s < nslots) {
-            const int64_t p = P0 + (s >> 3);
-            internal = !meta_leaf(nd_meta[p]);
-            const uint32_t f = nd_first[p];
-            end = f + nd_count[p];
-            if (internal) {
-                if (d == 0) {
-                    lb = f;
-                } else {  // first index in [f, end) whose digit at level l is >= d
-                    uint32_t lo = f, hi = end;
-                    while (lo < hi) {
-                        uint32_t mid = lo + ((hi - lo) >> 1);
-                        if ((uint32_t)((keys[mid] >> shift) & 7u) < (uint32_t)d)
-                            lo = mid + 1;
-                        else
-                            hi = mid;
+// ------------------------------------------------ particle-parallel build
+//
+// All levels at once from the sorted keys.  D_j, the first level at which
+// the keys of positions j-1 and j differ (0 where a system starts, 22 for
+// equal keys), marks cell boundaries: the level-l cell holding position i
+// runs from the last j <= i with D_j <= l to before the next j > i with
+// D_j <= l (positions outside [0, n) count as D = 0).  Cells shrink with
+// the level, so the leaf holding i is at LL_i, the first level whose cell
+// holds <= n_leaf particles (21 if none), and every coarser cell holding i
+// is an internal node.  Hence the nodes starting at i are levels
+// max(D_i, 1) .. LL_i, and the nodes ending at j (holding j - 1, not j) are
+// levels max(D_j, 1) .. LL_{j-1}.  Whether a cell holds <= n_leaf particles
+// is decided within n_leaf <= 16 positions either side.  Node ids stay
+// breadth-first (level-major, first particle ascending): id = start of the
+// level + number of the level's nodes starting before i, from per-tile
+// counts scanned per level and per-warp counts within the tile.
+
+constexpr int kBT = 256;                    // threads per tile
+constexpr int kBWarps = kBT / 32;
+constexpr int kBRows = 8;                   // rows of 32 positions per warp
+constexpr int kBSpan = 32 * kBRows;         // positions per warp
+constexpr int kBTile = kBT * kBRows;        // positions per tile
+constexpr int kHalo = kMaxLeaf;             // window either side of a row
+static_assert(kBTile == kBuildTile && kBWarps == kBuildWarps, "tile shape shared with the allocation");
+static_assert(kHalo == 16, "a row's window is 64 positions: 16 before, 32 own, 16 after");
+
+__device__ __forceinline__ uint32_t first_diff_level(int64_t j, int64_t n, const uint64_t* __restrict__ keys,
+                                                     const uint32_t* __restrict__ sys) {
+    if (j <= 0 || j >= n) return 0u;
+    if (sys && sys[j] != sys[j - 1]) return 0u;
+    const uint64_t x = keys[j - 1] ^ keys[j];
+    // keys have 63 bits: bit 62 is the top bit of the level-1 digit
+    return x ? ((uint32_t)__clzll((long long)x) - 1u) / 3u + 1u : 22u;
+}
+
+// Does the cell holding window position c hold <= n_leaf particles, given
+// the window's boundaries M (bit k: D of window position k <= the level)?
+// A boundary missing on either side means more than 16 particles.
+__device__ __forceinline__ bool cell_fits(unsigned long long M, int c, int n_leaf) {
+    const unsigned long long back = M & ((2ull << c) - 1ull);
+    const unsigned long long fwd = M >> (c + 1);
+    if (!back || !fwd) return false;
+    const int s = 63 - __clzll((long long)back);
+    const int e = c + __ffsll((long long)fwd);
+    return e - s <= n_leaf;
+}
+
+// Per tile: D and LL of every position (pk = D | LL << 8) and the number of
+// nodes of each level starting in each warp's positions, per warp
+// (wcount[(l - 1) * nw + warp]) and per tile (tcount[(l - 1) * ntiles +
+// tile]).  A warp takes 32 consecutive positions at a time: 22 ballots give
+// each level's boundaries in the 64-position window around them, and each
+// lane bisects the levels for its LL.
+__global__ void __launch_bounds__(kBT) k_tree_count(int64_t n, int n_leaf, const uint64_t* __restrict__ keys,
+                                                    const uint32_t* __restrict__ sys, uint32_t* __restrict__ pk,
+                                                    uint32_t* __restrict__ wcount, uint32_t* __restrict__ tcount,
+                                                    int64_t nw, int64_t ntiles) {
+    __shared__ uint8_t sD[kBTile + 2 * kHalo];
+    __shared__ unsigned long long s_m[kBWarps][kMaxLevel + 1];
+    __shared__ uint32_t s_wc[kMaxLevel][kBWarps];
+    const int64_t t0 = (int64_t)blockIdx.x * kBTile;
+    for (int q = threadIdx.x; q < kBTile + 2 * kHalo; q += kBT)
+        sD[q] = (uint8_t)first_diff_level(t0 - kHalo + q, n, keys, sys);
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = kHalo + lane;  // own window position
+    uint32_t cnt[kMaxLevel];
+#pragma unroll
+    for (int l = 0; l < kMaxLevel; ++l) cnt[l] = 0u;
+    for (int r = 0; r < kBRows; ++r) {
+        const int rb = w * kBSpan + r * 32;  // tile position of the row's first position
+        const int64_t i = t0 + rb + lane;
+        const uint32_t dA = sD[rb + lane];       // window 0..31
+        const uint32_t dB = sD[rb + 32 + lane];  // window 32..63
+        const uint32_t d = sD[rb + kHalo + lane];
+#pragma unroll
+        for (int l = 0; l <= kMaxLevel; ++l) {
+            const uint32_t a = __ballot_sync(0xFFFFFFFFu, dA <= (uint32_t)l);
+            const uint32_t b = __ballot_sync(0xFFFFFFFFu, dB <= (uint32_t)l);
+            if (lane == 0) s_m[w][l] = (unsigned long long)a | ((unsigned long long)b << 32);
+        }
+        __syncwarp();
+        int lo = 0, hi = kMaxLevel;  // first fitting level in [lo, hi], or 21
+#pragma unroll
+        for (int it = 0; it < 5; ++it) {
+            const int mid = (lo + hi) >> 1;
+            if (lo < hi) {
+                if (cell_fits(s_m[w][mid], c, n_leaf))
+                    hi = mid;
+                else
+                    lo = mid + 1;
+            }
+        }
+        const uint32_t LL = (uint32_t)lo;
+        __syncwarp();  // s_m is rewritten by the next row
+        if (i < n) pk[i] = d | (LL << 8);
+        const uint32_t l0 = max(d, 1u);
+        const uint32_t mask = (i < n && l0 <= LL) ? ((2u << LL) - (1u << l0)) : 0u;
+#pragma unroll
+        for (int l = 1; l <= kMaxLevel; ++l) cnt[l - 1] += __popc(__ballot_sync(0xFFFFFFFFu, (mask >> l) & 1u));
+    }
+    uint32_t mine = 0u;
+#pragma unroll
+    for (int l = 0; l < kMaxLevel; ++l)
+        if (lane == l) mine = cnt[l];
+    if (lane < kMaxLevel) {
+        wcount[(int64_t)lane * nw + (int64_t)blockIdx.x * kBWarps + w] = mine;
+        s_wc[lane][w] = mine;
+    }
+    __syncthreads();
+    if (threadIdx.x < kMaxLevel) {
+        uint32_t t = 0u;
+#pragma unroll
+        for (int k = 0; k < kBWarps; ++k) t += s_wc[threadIdx.x][k];
+        tcount[(int64_t)threadIdx.x * ntiles + blockIdx.x] = t;
+    }
+}
+
+// Exclusive scan of one level's per-tile counts (block l - 1 takes level
+// l); the level's total goes to ltot[l - 1].
+__global__ void __launch_bounds__(1024) k_tree_scan(uint32_t* tcount, int64_t ntiles, uint32_t* ltot) {
+    uint32_t tot;
+    scan_partials(tcount + (int64_t)blockIdx.x * ntiles, (int)ntiles, &tot);
+    if (threadIdx.x == 0) ltot[blockIdx.x] = tot;
+}
+
+__device__ __forceinline__ uint32_t compact3(uint64_t v) {
+    v &= 0x1249249249249249ull;
+    v = (v | (v >> 2)) & 0x10C30C30C30C30C3ull;
+    v = (v | (v >> 4)) & 0x100F00F00F00F00Full;
+    v = (v | (v >> 8)) & 0x001F0000FF0000FFull;
+    v = (v | (v >> 16)) & 0x001F00000000FFFFull;
+    v = (v | (v >> 32)) & 0x1FFFFFull;
+    return (uint32_t)v;
+}
+
+// Writes every node of levels >= 1: first particle, level and leaf flag,
+// parent, first child, grid origin, and (in nd_count, turned into the
+// count by k_tree_finish) the position after its last particle.  The
+// level-l node holding j - 1 is the last level-l node that starts before j,
+// so a position's exclusive rank at each level names both the nodes it
+// starts and those it ends.  The blocks cover positions 0 .. n (every open
+// node ends at n).  Each block derives the level starts from the totals
+// (levels from the first that does not fit in the node arrays on are left
+// empty, with the overflow flag set); block 0 also publishes them.
+__global__ void __launch_bounds__(kBT) k_tree_nodes(
+    int64_t n, int n_roots, int64_t cap_nodes, const uint64_t* __restrict__ keys,
+    const uint32_t* __restrict__ sys, const uint32_t* __restrict__ pk, const uint32_t* __restrict__ wcount,
+    const uint32_t* __restrict__ tcount, int64_t nw, int64_t ntiles, const uint32_t* __restrict__ ltot,
+    DevState* st, uint32_t* __restrict__ nd_first, uint32_t* __restrict__ nd_end, uint32_t* __restrict__ nd_child,
+    uint32_t* __restrict__ nd_meta, uint32_t* __restrict__ nd_parent, uint64_t* __restrict__ nd_qlo) {
+    __shared__ int64_t s_lvl[kMaxLevel + 3];
+    __shared__ int s_cut;
+    __shared__ uint32_t s_wc[kMaxLevel][kBWarps];
+    __shared__ uint32_t sP[1 + kBTile];  // pk of positions t0 - 1 .. t0 + kBTile - 1
+    if (threadIdx.x == 0) {
+        int64_t s = n_roots;
+        int cut = kMaxLevel + 1, top = 0;
+        s_lvl[0] = 0;
+        for (int l = 1; l <= kMaxLevel; ++l) {
+            s_lvl[l] = s;
+            if (cut > kMaxLevel && s + ltot[l - 1] > cap_nodes) cut = l;
+            if (cut > kMaxLevel) {
+                s += ltot[l - 1];
+                if (ltot[l - 1]) top = l;
+            }
+        }
+        for (int l = cut; l <= kMaxLevel + 2; ++l) s_lvl[l] = s;
+        s_cut = cut;
+        if (blockIdx.x == 0) {
+            for (int l = 0; l < kMaxLevel + 3; ++l) st->lvl_start[l] = (int32_t)s_lvl[l];
+            st->n_nodes = (int32_t)s;
+            st->max_level = top;
+            if (cut <= kMaxLevel) st->overflow |= kOvfNodes;
+        }
+    }
+    const int64_t tile = blockIdx.x;
+    const int64_t t0 = tile * kBTile;
+    // positions at or past n: D = 0, no nodes
+    for (int q = threadIdx.x; q < 1 + kBTile; q += kBT) {
+        const int64_t j = t0 - 1 + q;
+        sP[q] = (j >= 0 && j < n) ? pk[j] : 0u;
+    }
+    if (threadIdx.x < kMaxLevel * kBWarps) {
+        const int l = threadIdx.x / kBWarps, k = threadIdx.x % kBWarps;
+        s_wc[l][k] = tile < ntiles ? wcount[(int64_t)l * nw + tile * kBWarps + k] : 0u;
+    }
+    __syncthreads();
+    const int cut = s_cut;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    // next id of each level for this warp: level start + nodes of earlier
+    // tiles + nodes of earlier warps of this tile (a tile past the counted
+    // ones holds only position n: all of the level's nodes come before)
+    uint32_t nxt = 0u;
+    if (lane >= 1 && lane <= kMaxLevel) {
+        nxt = (uint32_t)s_lvl[lane] + (tile < ntiles ? tcount[(int64_t)(lane - 1) * ntiles + tile] : ltot[lane - 1]);
+        for (int k = 0; k < w; ++k) nxt += s_wc[lane - 1][k];
+    }
+    uint32_t run[kMaxLevel];
+#pragma unroll
+    for (int l = 1; l <= kMaxLevel; ++l) run[l - 1] = __shfl_sync(0xFFFFFFFFu, nxt, l);
+    for (int r = 0; r < kBRows; ++r) {
+        const int p = w * kBSpan + r * 32 + lane;
+        const int64_t j = t0 + p;
+        const uint32_t v = sP[1 + p], u = sP[p];
+        const uint32_t d = v & 0xFFu, LL = (v >> 8) & 0xFFu;
+        const uint32_t lo = max(d, 1u), hi = LL;
+        const bool any = j < n && lo <= hi;
+        // levels of the nodes that end here
+        uint32_t elo = 32u, ehi = 0u;
+        if (j >= 1 && j <= n && d <= (uint32_t)kMaxLevel) {
+            elo = max(d, 1u);
+            ehi = (u >> 8) & 0xFFu;
+        }
+        uint64_t key = 0;
+        uint32_t qx = 0, qy = 0, qz = 0, root = 0;
+        if (any) {
+            key = keys[j];
+            qx = compact3(key >> 2);
+            qy = compact3(key >> 1);
+            qz = compact3(key);
+            if (sys) root = sys[j];
+        }
+        uint32_t prev_id = 0u, prev_excl = 0u;
+#pragma unroll
+        for (int l = 1; l <= kMaxLevel; ++l) {
+            const bool h = any && lo <= (uint32_t)l && (uint32_t)l <= hi;
+            const uint32_t bm = __ballot_sync(0xFFFFFFFFu, h);
+            const uint32_t excl = run[l - 1] + __popc(bm & lt);
+            run[l - 1] += __popc(bm);
+            if (l < cut) {
+                if (elo <= (uint32_t)l && (uint32_t)l <= ehi) nd_end[excl - 1u] = (uint32_t)j;
+                if (h) {
+                    const uint32_t id = excl;
+                    uint32_t parent;
+                    if ((uint32_t)l > lo) {
+                        parent = prev_id;
+                        nd_child[prev_id] = id;  // first child of this position's previous node
+                    } else if (l == 1) {
+                        parent = root;
+                        if (d == 0u) nd_child[root] = id;  // a system's first position
+                    } else {
+                        parent = prev_excl - 1u;  // last node of level l - 1 starting before j
                     }
-                    lb = lo;
+                    const uint32_t cm = ~((1u << (kMaxLevel - l)) - 1u) & kQMax;
+                    nd_first[id] = (uint32_t)j;
+                    nd_child[id] = 0xFFFFFFFFu;
+                    nd_meta[id] = (uint32_t)l | (((uint32_t)l == hi ? 1u : 0u) << 16);
+                    nd_parent[id] = parent;
+                    nd_qlo[id] = ((uint64_t)(qx & cm) << 42) | ((uint64_t)(qy & cm) << 21) | (uint64_t)(qz & cm);
+                    prev_id = id;
                 }
             }
+            prev_excl = excl;
         }
-        uint32_t nxt = __shfl_down_sync(0xFFFFFFFFu, lb, 1, 8);
-        if (d == 7) nxt = end;
-        uint32_t cnt = internal ? nxt - lb : 0u;
-        if (s < nslots) {
-            slot_lb[s] = lb;
-            slot_cnt[s] = cnt;
-        }
-        nonempty += cnt > 0 ? 1u : 0u;
-    }
-    uint32_t tot = block_sum(nonempty);
-    if (threadIdx.x == 0) part[blockIdx.x] = tot;
-}
-
-__global__ void __launch_bounds__(1024) k_level_scan(int l, DevState* st, uint32_t* part, int np,
-                                                     int64_t cap_nodes) {
-    uint32_t tot;
-    scan_partials(part, np, &tot);
-    if (threadIdx.x == 0) {
-        int64_t start = st->lvl_start[l];
-        int64_t end = start + tot;
-        if (end > cap_nodes) {
-            st->overflow |= kOvfNodes;
-            end = start;  // write no node of this level; later levels stay empty
-        }
-        for (int k = l + 1; k < kMaxLevel + 3; ++k) st->lvl_start[k] = (int32_t)end;
-        st->n_nodes = (int32_t)end;
-        if (end > start) st->max_level = l;
     }
 }
 
-__global__ void __launch_bounds__(kB) k_level_write(
-    int l, int n_leaf, const DevState* __restrict__ st, const uint32_t* __restrict__ slot_lb,
-    const uint32_t* __restrict__ slot_cnt, const uint32_t* __restrict__ part,
-    uint32_t* __restrict__ nd_first, uint32_t* __restrict__ nd_count, uint32_t* __restrict__ nd_child,
-    uint32_t* __restrict__ nd_meta, uint32_t* __restrict__ nd_parent, uint64_t* __restrict__ nd_qlo,
-    uint64_t* __restrict__ nd_prefix) {
-    const int64_t P0 = st->lvl_start[l - 1], P1 = st->lvl_start[l];
-    const int64_t C0 = st->lvl_start[l], C1 = st->lvl_start[l + 1];
-    if (C1 == C0) return;  // empty level (or capacity exceeded): uniform exit
-    const int64_t nslots = 8 * (P1 - P0);
-    int64_t t0, t1;
-    block_tiles(nslots, &t0, &t1);
-    uint32_t running = part[blockIdx.x];
-    const int lane = threadIdx.x & 31;
-    const int sh = kMaxLevel - l;
-    for (int64_t t = t0; t < t1; ++t) {
-        const int64_t s = t * kB + threadIdx.x;
-        const uint32_t cnt = s < nslots ? slot_cnt[s] : 0u;
-        const uint32_t flag = cnt > 0 ? 1u : 0u;
-        uint32_t tile_tot;
-        const uint32_t rank = block_excl(flag, &tile_tot);
-        const uint32_t gm = (__ballot_sync(0xFFFFFFFFu, flag) >> (lane & ~7)) & 0xFFu;
-        if (flag) {
-            const int d = (int)(s & 7);
-            const int64_t p = P0 + (s >> 3);
-            const int64_t id = C0 + running + rank;
-            nd_first[id] = slot_lb[s];
-            nd_count[id] = cnt;
-            nd_child[id] = 0xFFFFFFFFu;
-            nd_meta[id] = (uint32_t)l | ((cnt <= (uint32_t)n_leaf || l == kMaxLevel) ? 1u : 0u) << 16;
-            nd_parent[id] = (uint32_t)p;
-            const uint64_t pq = nd_qlo[p];
-            const uint64_t add = ((uint64_t)((d >> 2) & 1) << (42 + sh)) |
-                                 ((uint64_t)((d >> 1) & 1) << (21 + sh)) | ((uint64_t)(d & 1) << sh);
-            nd_qlo[id] = pq | add;
-            nd_prefix[id] = (nd_prefix[p] << 3) | (uint64_t)d;
-            if (d == __ffs(gm) - 1) {  // first non-empty octant: parent's child range
-                nd_child[p] = (uint32_t)id;
-                nd_meta[p] = (uint32_t)(l - 1) | ((uint32_t)__popc(gm) << 8);
-            }
-        }
-        running += tile_tot;
+// Counts (end - first) and children counts: node c is the last child of
+// its parent P iff the next node has another parent; it then stores c -
+// first child of P + 1 in P's meta (one writer per parent).
+__global__ void __launch_bounds__(256) k_tree_finish(const DevState* __restrict__ st, int n_roots,
+                                                     const uint32_t* __restrict__ nd_first,
+                                                     uint32_t* __restrict__ nd_count,
+                                                     const uint32_t* __restrict__ nd_parent,
+                                                     const uint32_t* __restrict__ nd_child,
+                                                     uint32_t* __restrict__ nd_meta) {
+    const int64_t nn = st->n_nodes;
+    for (int64_t c = n_roots + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nn;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        nd_count[c] -= nd_first[c];
+        const uint32_t P = nd_parent[c];
+        if (c + 1 == nn || nd_parent[c + 1] != P) nd_meta[P] |= ((uint32_t)c - nd_child[P] + 1u) << 8;
     }
 }
 
@@ -600,24 +754,30 @@ __global__ void __launch_bounds__(256) k_group_data(
 int build_tree(fdps_tree* t, fdps_psys* ps) {
     fdps_ctx* ctx = t->ctx;
     cudaStream_t s = ctx->stream;
-    const int G = t->box_blocks;  // partition width of the level kernels
-    k_roots<<<grid_for(ps->n_sys, 256, 64), 256, 0, s>>>(
-        t->st, ps->n_sys, ps->d_off, ps->n, t->p.n_leaf, t->nd_first, t->nd_count, t->nd_child,
-        t->nd_meta, t->nd_parent, t->nd_qlo, t->nd_prefix);
+    const int64_t n = ps->n;
+    const int64_t ntiles = n > 0 ? (n + kBTile - 1) / kBTile : 1;
+    const int64_t nw = ntiles * kBWarps;
+    uint32_t* wcount = t->bt_count;                 // [21][nw] per warp
+    uint32_t* tcount = wcount + kMaxLevel * nw;     // [21][ntiles] per tile, then scanned
+    uint32_t* ltot = tcount + kMaxLevel * ntiles;   // [21]
+    k_roots<<<grid_for(ps->n_sys, 256, 64), 256, 0, s>>>(ps->n_sys, ps->d_off, n, t->p.n_leaf, t->nd_first,
+                                                         t->nd_count, t->nd_child, t->nd_meta, t->nd_parent,
+                                                         t->nd_qlo);
     FDPS_LAUNCH_CHECK(ctx);
-    uint32_t* slot_lb = t->lvl_scratch;
-    uint32_t* slot_cnt = t->lvl_scratch + 8 * t->cap_nodes;
-    for (int l = 1; l <= kMaxLevel; ++l) {
-        k_level_count<<<G, kB, 0, s>>>(l, t->st, t->keys_sorted, t->nd_first, t->nd_count,
-                                       t->nd_meta, slot_lb, slot_cnt, t->lvl_scan);
-        FDPS_LAUNCH_CHECK(ctx);
-        k_level_scan<<<1, 1024, 0, s>>>(l, t->st, t->lvl_scan, G, t->cap_nodes);
-        FDPS_LAUNCH_CHECK(ctx);
-        k_level_write<<<G, kB, 0, s>>>(l, t->p.n_leaf, t->st, slot_lb, slot_cnt, t->lvl_scan,
-                                       t->nd_first, t->nd_count, t->nd_child, t->nd_meta,
-                                       t->nd_parent, t->nd_qlo, t->nd_prefix);
-        FDPS_LAUNCH_CHECK(ctx);
-    }
+    // per-position scratch: t->head, rewritten by the group selection
+    k_tree_count<<<(unsigned)ntiles, kBT, 0, s>>>(n, t->p.n_leaf, t->keys_sorted, ps->d_sys, t->head, wcount,
+                                                  tcount, nw, ntiles);
+    FDPS_LAUNCH_CHECK(ctx);
+    k_tree_scan<<<kMaxLevel, 1024, 0, s>>>(tcount, ntiles, ltot);
+    FDPS_LAUNCH_CHECK(ctx);
+    const unsigned grid_nodes = (unsigned)(n / kBTile + 1);  // positions 0 .. n
+    k_tree_nodes<<<grid_nodes, kBT, 0, s>>>(n, ps->n_sys, t->cap_nodes, t->keys_sorted, ps->d_sys, t->head,
+                                            wcount, tcount, nw, ntiles, ltot, t->st, t->nd_first, t->nd_count,
+                                            t->nd_child, t->nd_meta, t->nd_parent, t->nd_qlo);
+    FDPS_LAUNCH_CHECK(ctx);
+    k_tree_finish<<<ctx->sm_count * 4, 256, 0, s>>>(t->st, ps->n_sys, t->nd_first, t->nd_count, t->nd_parent,
+                                                    t->nd_child, t->nd_meta);
+    FDPS_LAUNCH_CHECK(ctx);
     return FDPS_OK;
 }
 

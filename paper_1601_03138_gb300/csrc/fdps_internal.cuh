@@ -37,6 +37,8 @@ constexpr uint32_t kQMax = (1u << 21) - 1u;
 constexpr uint32_t kLeafTag = 0x80000000u;  // list entry: opened leaf (EPJ)
 constexpr int kMaxLeaf = 16;
 constexpr int kMaxGrp = 4096;
+constexpr int kBuildTile = 2048;  // positions per tile of the tree build
+constexpr int kBuildWarps = 8;    // warps per tile of the tree build
 
 // overflow bits of DevState::overflow
 constexpr uint32_t kOvfNodes = 1u;
@@ -154,12 +156,13 @@ struct fdps_tree {
     int64_t cap_nd_hmax = 0;
     double* g_hmax = nullptr;
     int64_t cap_g_hmax = 0;
-    uint32_t* sort_hist = nullptr; // [256][tiles]
+    uint32_t* sort_hist = nullptr; // 2 x [tiles][256]: look-back words of the sort passes
     uint32_t* sort_dtot = nullptr; // [4096]: digit totals / bases of every pass, tile counters
     int64_t cap_tiles = 0;
     float4* pf_hi = nullptr;       // (x_hi, y_hi, z_hi, m) relative to c0
     float4* pf_lo = nullptr;       // (x_lo, y_lo, z_lo, eps^2)
-    uint32_t* head = nullptr;      // per particle: group node starting here
+    uint32_t* head = nullptr;      // per particle: group node starting here (tree build scratch before)
+    uint32_t* bt_count = nullptr;  // tree build: per-warp node counts of each level, level totals
     // nodes
     int64_t cap_nodes = 0;
     uint32_t* nd_first = nullptr;
@@ -168,7 +171,6 @@ struct fdps_tree {
     uint32_t* nd_meta = nullptr;    // level | nchild << 8 | leaf << 16
     uint32_t* nd_parent = nullptr;
     uint64_t* nd_qlo = nullptr;     // packed grid origin x<<42 | y<<21 | z
-    uint64_t* nd_prefix = nullptr;  // key prefix (debug / tests)
     double* nd_sx = nullptr;        // FP64 sums of m x (bottom-up)
     double* nd_sy = nullptr;
     double* nd_sz = nullptr;
@@ -179,8 +181,6 @@ struct fdps_tree {
                                     // first child, meta
     float4* nd_fq0 = nullptr;       // FP32 (Qxx, Qyy, Qzz, Qxy)
     float2* nd_fq1 = nullptr;       // FP32 (Qxz, Qyz)
-    uint32_t* lvl_scratch = nullptr;  // child-count slots of one level
-    uint32_t* lvl_scan = nullptr;     // per-block partial sums
     // groups
     int64_t cap_groups = 0;
     uint32_t* g_first = nullptr;

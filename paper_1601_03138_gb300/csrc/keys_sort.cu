@@ -471,9 +471,9 @@ template <bool SYSKEY, bool FULL>
 __device__ __forceinline__ void onesweep_tile(
     const int n, const int tile, const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
     uint64_t* __restrict__ kout, uint32_t* __restrict__ vout, const int shift,
-    const uint32_t* __restrict__ dbase, volatile uint32_t* st, const uint32_t* __restrict__ sys,
-    uint32_t* err, uint64_t* sk, uint32_t* sv, uint8_t* sd, uint32_t (*wcnt)[kRadix], uint32_t* tstart,
-    uint32_t* gdelta) {
+    const uint32_t* __restrict__ dbase, volatile uint32_t* st, uint32_t* __restrict__ st_next,
+    const uint32_t* __restrict__ sys, uint32_t* err, uint64_t* sk, uint32_t* sv, uint8_t* sd,
+    uint32_t (*wcnt)[kRadix], uint32_t* tstart, uint32_t* gdelta) {
     constexpr int kWarps = kOsBlock / 32;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lt_mask = (1u << lane) - 1u;
@@ -545,6 +545,8 @@ __device__ __forceinline__ void onesweep_tile(
         }
         // publish this tile's count at once, so later tiles can look past it
         st[(size_t)tile * kRadix + d] = (tile == 0 ? kFlagInc : kFlagAgg) | run;
+        // the next pass looks back in the other buffer: clear this tile's row
+        st_next[(size_t)tile * kRadix + d] = 0u;
     }
     const uint32_t ts = block_excl_scan(run, nullptr);
     if (d < kRadix) tstart[d] = ts;
@@ -623,7 +625,7 @@ template <bool SYSKEY>
 __global__ void __launch_bounds__(kOsBlock, kOsMinBlocks) k_onesweep(
     int64_t n, const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
     uint64_t* __restrict__ kout, uint32_t* __restrict__ vout, int shift,
-    const uint32_t* __restrict__ dbase, uint32_t* status, uint32_t* tile_ctr,
+    const uint32_t* __restrict__ dbase, uint32_t* status, uint32_t* status_next, uint32_t* tile_ctr,
     const uint32_t* __restrict__ sys, uint32_t* err) {
     constexpr int kWarps = kOsBlock / 32;
     __shared__ uint64_t sk[kOsTile];
@@ -638,11 +640,11 @@ __global__ void __launch_bounds__(kOsBlock, kOsMinBlocks) k_onesweep(
     __syncthreads();
     const int tile = (int)s_tile;
     if ((int64_t)(tile + 1) * kOsTile <= n)
-        onesweep_tile<SYSKEY, true>((int)n, tile, kin, vin, kout, vout, shift, dbase, status, sys, err, sk, sv,
-                                    sd, wcnt, tstart, gdelta);
+        onesweep_tile<SYSKEY, true>((int)n, tile, kin, vin, kout, vout, shift, dbase, status, status_next,
+                                    sys, err, sk, sv, sd, wcnt, tstart, gdelta);
     else
-        onesweep_tile<SYSKEY, false>((int)n, tile, kin, vin, kout, vout, shift, dbase, status, sys, err, sk,
-                                     sv, sd, wcnt, tstart, gdelta);
+        onesweep_tile<SYSKEY, false>((int)n, tile, kin, vin, kout, vout, shift, dbase, status, status_next,
+                                     sys, err, sk, sv, sd, wcnt, tstart, gdelta);
 }
 
 // Reorder the particle system into key order and write the FP32 hi/lo
@@ -714,20 +716,24 @@ int keys_and_sort(fdps_tree* t, fdps_psys* ps) {
     const uint32_t* vin = nullptr;
     uint64_t* kb[2] = {t->keys_a, t->keys_b};
     uint32_t* vb[2] = {t->vals_a, t->vals_b};
-    uint32_t* status = t->sort_hist;  // [tile][256] look-back words of the pass
+    // [tile][256] look-back words, two buffers: a pass looks back in one and
+    // clears the other for the next pass, so only the first needs a memset
+    uint32_t* status[2] = {t->sort_hist, t->sort_hist + (size_t)kRadix * ntiles};
+    FDPS_CUDA_TRY(ctx, cudaMemsetAsync(status[0], 0, sizeof(uint32_t) * kRadix * (size_t)ntiles, s));
     for (int pass = 0; pass < npass; ++pass) {
         const bool by_sys = pass >= 8;
         const int shift = by_sys ? 8 * (pass - 8) : 8 * pass;
-        FDPS_CUDA_TRY(ctx, cudaMemsetAsync(status, 0, sizeof(uint32_t) * kRadix * (size_t)ntiles, s));
         uint64_t* ko = kb[pass & 1];
         uint32_t* vo = vb[pass & 1];
+        uint32_t* st_cur = status[pass & 1];
+        uint32_t* st_nxt = status[(pass + 1) & 1];
         if (by_sys)
             k_onesweep<true><<<ntiles, kOsBlock, 0, s>>>(n, kin, vin, ko, vo, shift, hist + pass * kRadix,
-                                                           status, tile_ctr + pass, ps->d_sys,
+                                                           st_cur, st_nxt, tile_ctr + pass, ps->d_sys,
                                                            &t->st->overflow);
         else
             k_onesweep<false><<<ntiles, kOsBlock, 0, s>>>(n, kin, vin, ko, vo, shift, hist + pass * kRadix,
-                                                            status, tile_ctr + pass, nullptr,
+                                                            st_cur, st_nxt, tile_ctr + pass, nullptr,
                                                             &t->st->overflow);
         FDPS_LAUNCH_CHECK(ctx);
         kin = ko;
@@ -745,7 +751,7 @@ int selftest_lookback_timeout(fdps_ctx* ctx, uint32_t* flags_out) {
     const int64_t n = 2 * kOsTile;
     uint64_t* keys = nullptr;
     unsigned char* raw = nullptr;
-    const size_t bytes = sizeof(uint64_t) * 2 * n + sizeof(uint32_t) * (2 * n + 2 * kRadix + kRadix + 2);
+    const size_t bytes = sizeof(uint64_t) * 2 * n + sizeof(uint32_t) * (2 * n + 4 * kRadix + kRadix + 2);
     if (cudaMalloc(&raw, bytes) != cudaSuccess) {
         cudaGetLastError();
         return set_error(ctx, FDPS_ENOMEM, "self-test allocation failed");
@@ -754,7 +760,8 @@ int selftest_lookback_timeout(fdps_ctx* ctx, uint32_t* flags_out) {
     uint64_t* kout = keys + n;
     uint32_t* vout = reinterpret_cast<uint32_t*>(kout + n);
     uint32_t* status = vout + n;            // 2 tiles x 256
-    uint32_t* dbase = status + 2 * kRadix;  // 256
+    uint32_t* status_next = status + 2 * kRadix;
+    uint32_t* dbase = status_next + 2 * kRadix;  // 256
     uint32_t* ctr = dbase + kRadix;
     uint32_t* err = ctr + 1;
     cudaStream_t s = ctx->stream;
@@ -764,8 +771,8 @@ int selftest_lookback_timeout(fdps_ctx* ctx, uint32_t* flags_out) {
         cudaMemcpyAsync(ctr, &one, sizeof(one), cudaMemcpyHostToDevice, s) != cudaSuccess)
         rc = set_error(ctx, FDPS_ECUDA, "self-test set-up failed");
     if (!rc) {
-        k_onesweep<false><<<1, kOsBlock, 0, s>>>(n, keys, nullptr, kout, vout, 0, dbase, status, ctr,
-                                                   nullptr, err);
+        k_onesweep<false><<<1, kOsBlock, 0, s>>>(n, keys, nullptr, kout, vout, 0, dbase, status,
+                                                   status_next, ctr, nullptr, err);
         if (cudaGetLastError() != cudaSuccess) rc = set_error(ctx, FDPS_ECUDA, "self-test launch failed");
     }
     uint32_t h = 0;
