@@ -341,25 +341,25 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
                 const float R2 = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, e2[0])));
                 const float Ri = rsqrtf(R2);
                 const float Ri2 = Ri * Ri;
-                const float nMRi = a.w * Ri;
-                const float nMRi3 = nMRi * Ri2;
+                const float Ri3 = Ri * Ri2;
                 if (QUAD) {
                     const float Qrx = fmaf(q0.x, rx, fmaf(q0.w, ry, q1.x * rz));
                     const float Qry = fmaf(q0.w, rx, fmaf(q0.y, ry, q1.y * rz));
                     const float Qrz = fmaf(q1.x, rx, fmaf(q1.y, ry, q0.z * rz));
                     const float rQr = fmaf(rx, Qrx, fmaf(ry, Qry, rz * Qrz));
-                    const float Ri5 = Ri2 * Ri2 * Ri;
-                    const float u = rQr * Ri5;
-                    const float nc = fmaf(-2.5f * u, Ri2, nMRi3);
-                    sax[0] = fmaf(Qrx, Ri5, fmaf(nc, rx, sax[0]));
-                    say[0] = fmaf(Qry, Ri5, fmaf(nc, ry, say[0]));
-                    saz[0] = fmaf(Qrz, Ri5, fmaf(nc, rz, saz[0]));
-                    spp[0] = fmaf(-0.5f, u, spp[0] + nMRi);
+                    const float Ri5 = Ri3 * Ri2;
+                    const float u = rQr * Ri5;                            // r.Q.r / R^5
+                    const float g = fmaf(-2.5f * u, Ri2, a.w * Ri3);      // -(M/R^3 + 5/2 r.Q.r / R^7)
+                    sax[0] = fmaf(Qrx, Ri5, fmaf(g, rx, sax[0]));
+                    say[0] = fmaf(Qry, Ri5, fmaf(g, ry, say[0]));
+                    saz[0] = fmaf(Qrz, Ri5, fmaf(g, rz, saz[0]));
+                    spp[0] = fmaf(-0.5f, u, fmaf(a.w, Ri, spp[0]));
                 } else {
+                    const float nMRi3 = a.w * Ri3;
                     sax[0] = fmaf(nMRi3, rx, sax[0]);
                     say[0] = fmaf(nMRi3, ry, say[0]);
                     saz[0] = fmaf(nMRi3, rz, saz[0]);
-                    spp[0] += nMRi;
+                    spp[0] = fmaf(a.w, Ri, spp[0]);
                 }
             } else {
                 const f2 jx = f2_bc(a.x), jy = f2_bc(a.y), jz = f2_bc(a.z), nM = f2_bc(a.w);
@@ -378,25 +378,26 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
                     const f2 R2 = f2_fma(rx, rx, f2_fma(ry, ry, f2_fma(rz, rz, ep[h])));
                     const f2 Ri = f2_rsqrt(R2);
                     const f2 Ri2 = f2_mul(Ri, Ri);
-                    const f2 nMRi = f2_mul(nM, Ri);      // -M/R
-                    const f2 nMRi3 = f2_mul(nMRi, Ri2);  // -M/R^3
+                    const f2 Ri3 = f2_mul(Ri, Ri2);
                     if (QUAD) {
                         const f2 Qrx = f2_fma(qxx, rx, f2_fma(qxy, ry, f2_mul(qxz, rz)));
                         const f2 Qry = f2_fma(qxy, rx, f2_fma(qyy, ry, f2_mul(qyz, rz)));
                         const f2 Qrz = f2_fma(qxz, rx, f2_fma(qyz, ry, f2_mul(qzz, rz)));
                         const f2 rQr = f2_fma(rx, Qrx, f2_fma(ry, Qry, f2_mul(rz, Qrz)));
-                        const f2 Ri5 = f2_mul(f2_mul(Ri2, Ri2), Ri);
-                        const f2 u = f2_mul(rQr, Ri5);                      // r.Q.r / R^5
-                        const f2 nc = f2_fma(f2_mul(cm25, u), Ri2, nMRi3);  // -(M/R^3 + 5/2 r.Q.r / R^7)
-                        pax[h] = f2_fma(Qrx, Ri5, f2_fma(nc, rx, pax[h]));
-                        pay[h] = f2_fma(Qry, Ri5, f2_fma(nc, ry, pay[h]));
-                        paz[h] = f2_fma(Qrz, Ri5, f2_fma(nc, rz, paz[h]));
-                        pp[h] = f2_fma(cm05, u, f2_add(pp[h], nMRi));
+                        const f2 Ri5 = f2_mul(Ri3, Ri2);
+                        const f2 u = f2_mul(rQr, Ri5);  // r.Q.r / R^5
+                        // -(M/R^3 + 5/2 r.Q.r / R^7)
+                        const f2 g = f2_fma(f2_mul(cm25, u), Ri2, f2_mul(nM, Ri3));
+                        pax[h] = f2_fma(Qrx, Ri5, f2_fma(g, rx, pax[h]));
+                        pay[h] = f2_fma(Qry, Ri5, f2_fma(g, ry, pay[h]));
+                        paz[h] = f2_fma(Qrz, Ri5, f2_fma(g, rz, paz[h]));
+                        pp[h] = f2_fma(cm05, u, f2_fma(nM, Ri, pp[h]));
                     } else {
+                        const f2 nMRi3 = f2_mul(nM, Ri3);  // -M/R^3
                         pax[h] = f2_fma(nMRi3, rx, pax[h]);
                         pay[h] = f2_fma(nMRi3, ry, pay[h]);
                         paz[h] = f2_fma(nMRi3, rz, paz[h]);
-                        pp[h] = f2_add(pp[h], nMRi);
+                        pp[h] = f2_fma(nM, Ri, pp[h]);
                     }
                 }
             }
