@@ -235,21 +235,24 @@ __global__ void __launch_bounds__(kWalkBlock, 8) k_walk(WalkArgs A) {
                     cursor += k;
                 }
                 nspj += __popc(__ballot_sync(0xFFFFFFFFu, action == 1));
-                // ---- push children of opened internal cells
-                uint32_t inc = nch;
+                // ---- push children of opened internal cells (deep in the
+                // tree most batches open none)
+                if (__ballot_sync(0xFFFFFFFFu, nch > 0u)) {
+                    uint32_t inc = nch;
 #pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    uint32_t tv = __shfl_up_sync(0xFFFFFFFFu, inc, off);
-                    if (lane >= off) inc += tv;
-                }
-                const uint32_t tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
-                if (nsize + tot > F) {
-                    if (lane == 0) atomicOr(&st->overflow, kOvfFrontier);
-                    ovf = true;
-                } else {
-                    const uint32_t o = nsize + inc - nch;
-                    for (uint32_t c = 0; c < nch; ++c) fb[o + c] = child + c;
-                    nsize += tot;
+                    for (int off = 1; off < 32; off <<= 1) {
+                        uint32_t tv = __shfl_up_sync(0xFFFFFFFFu, inc, off);
+                        if (lane >= off) inc += tv;
+                    }
+                    const uint32_t tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
+                    if (nsize + tot > F) {
+                        if (lane == 0) atomicOr(&st->overflow, kOvfFrontier);
+                        ovf = true;
+                    } else {
+                        const uint32_t o = nsize + inc - nch;
+                        for (uint32_t c = 0; c < nch; ++c) fb[o + c] = child + c;
+                        nsize += tot;
+                    }
                 }
             }
             __syncwarp();
