@@ -174,3 +174,35 @@ def test_invalid_system_offsets(G, ctx):
     ps.set_systems([0, 4, 10])
     assert G.fdps_psys_num_systems(ps.h) == 2
     ps.close()
+
+
+def test_ensemble_tiny_systems_between_large_ones(G, ctx):
+    # systems at or below n_leaf (a root that is a leaf) next to large ones,
+    # and system boundaries on and off the build's 2048-position tiles
+    sizes = [2000, 3, 48, 1, 2047, 5, 4096, 2, 6]
+    pos, vel, mass, eps, off = _ensemble(sizes, 11)
+    n = len(pos)
+    ps = G.ParticleSystem(ctx, n)
+    tree = G.Tree(ctx, theta=0.5, n_leaf=6, n_grp=48, quad=True)
+    try:
+        ps.set_systems(off)
+        ps.set(pos, vel, mass, eps)
+        tree.calc_force_all_and_write_back(ps)
+        nodes = tree.nodes()
+        node_sys = np.searchsorted(off, nodes["first"], side="right") - 1
+        # roots first, one per system, then deeper levels
+        assert np.array_equal(nodes["level"][: len(sizes)], np.zeros(len(sizes)))
+        for k in range(len(sizes)):
+            a, b = off[k], off[k + 1]
+            ref = oracle.Tree(pos[a:b], mass[a:b], eps[a:b], theta=0.5, n_leaf=6, n_grp=48, quad=True)
+            nr = ref.nodes()
+            gsel = np.nonzero(node_sys == k)[0]
+            # the system's nodes are the oracle's, in order
+            assert len(gsel) == ref.n_nodes
+            for key in ("level", "count", "nchild"):
+                np.testing.assert_array_equal(nodes[key][gsel], nr[key], err_msg=f"{key} of system {k}")
+            np.testing.assert_array_equal(nodes["first"][gsel] - a, nr["first"])
+            np.testing.assert_array_equal(nodes["com"][gsel], nr["com"])
+    finally:
+        tree.close()
+        ps.close()

@@ -110,6 +110,12 @@ CASES = [
     # theta = 0 with one particle per leaf: every list holds ~70000 leaves,
     # longer than one 2^16-entry pool chunk
     ("plummer-theta0-long-lists", "plummer", 70000, 0.0, 1, 512, False),
+    # leaf sizes that are not powers of two, tile-aligned and ragged sizes:
+    # the build decides leaves within n_leaf positions either side
+    ("hernquist-nleaf3", "hernquist", 6144, 0.5, 3, 24, False),
+    ("clumpy-nleaf5", "clumpy", 10241, 0.5, 5, 40, True),
+    ("plummer-nleaf11", "plummer", 8192, 0.5, 11, 77, False),
+    ("hernquist-nleaf13", "hernquist", 12289, 0.6, 13, 100, True),
 ]
 
 
