@@ -279,7 +279,10 @@ __global__ void __launch_bounds__(kBT) k_tree_nodes(
     __shared__ uint32_t sP[1 + kBTile];  // pk of positions t0 - 1 .. t0 + kBTile - 1
     if (threadIdx.x == 0) {
         int64_t s = n_roots;
-        int cut = kMaxLevel + 1, top = 0;
+        // keys left unsorted by a sort that gave up: roots only, so that
+        // every later stage stays within its buffers until the retry
+        const bool stalled = st->overflow & kSortStall;
+        int cut = stalled ? 1 : kMaxLevel + 1, top = 0;
         s_lvl[0] = 0;
         for (int l = 1; l <= kMaxLevel; ++l) {
             s_lvl[l] = s;
@@ -295,7 +298,7 @@ __global__ void __launch_bounds__(kBT) k_tree_nodes(
             for (int l = 0; l < kMaxLevel + 3; ++l) st->lvl_start[l] = (int32_t)s_lvl[l];
             st->n_nodes = (int32_t)s;
             st->max_level = top;
-            if (cut <= kMaxLevel) st->overflow |= kOvfNodes;
+            if (cut <= kMaxLevel && !stalled) st->overflow |= kOvfNodes;
         }
     }
     const int64_t tile = blockIdx.x;

@@ -48,6 +48,9 @@ constexpr uint32_t kOvfGroups = 8u;
 constexpr uint32_t kBadInput = 16u;
 constexpr uint32_t kOvfChunk = 32u;
 constexpr uint32_t kSortStall = 64u;  // a radix-sort look-back wait gave up
+// Any of these leaves the step's lists or particle order invalid: the
+// kernels downstream skip their work (the host redoes the step).
+constexpr uint32_t kStepInvalid = kOvfNodes | kOvfPool | kOvfFrontier | kOvfGroups | kOvfChunk | kSortStall;
 
 // Per-tree device-resident state written by the kernels of one force call.
 struct DevState {

@@ -517,6 +517,9 @@ __global__ void __launch_bounds__(kCB, (QUAD ? 4 : 1)) k_force_f32(ForceArgs A) 
     sb.s2 = reinterpret_cast<float2*>(s_union + kCE * 32);
     double* s_red = reinterpret_cast<double*>(s_union);
     DevState* st = A.st;
+    // lists cut short by a buffer overflow may point past the pool: no work
+    // (a step replayed from a graph is redone by the host)
+    if (st->overflow & kStepInvalid) return;
     const uint32_t ngroups = (uint32_t)st->n_groups;
     for (;;) {
         if (threadIdx.x == 0) s_g = atomicAdd(&st->force_counter, 1u);
@@ -552,6 +555,7 @@ __global__ void __launch_bounds__(kFBlock) k_force_f64(ForceArgs A) {
     __shared__ double s_red[kFWarps][4][32];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     DevState* st = A.st;
+    if (st->overflow & kStepInvalid) return;  // as in the FP32 kernel
     const uint32_t ngroups = (uint32_t)st->n_groups;
     for (;;) {
         uint32_t g = 0;

@@ -649,8 +649,11 @@ __global__ void __launch_bounds__(kOsBlock, kOsMinBlocks) k_onesweep(
 
 // Reorder the particle system into key order and write the FP32 hi/lo
 // copies relative to the root centre used by the walk and force kernels.
+// If the sort gave up (a look-back wait ran out), the permutation may be
+// incomplete: the particles are copied in their current order instead, so
+// the system stays whole for the caller's retry.
 __global__ void __launch_bounds__(256) k_reorder(
-    int64_t n, const uint32_t* __restrict__ perm, const SysBox* __restrict__ box,
+    const DevState* __restrict__ st, int64_t n, const uint32_t* __restrict__ perm, const SysBox* __restrict__ box,
     const uint32_t* __restrict__ sys,
     const double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ z,
     const double* __restrict__ vx, const double* __restrict__ vy, const double* __restrict__ vz,
@@ -659,11 +662,12 @@ __global__ void __launch_bounds__(256) k_reorder(
     double* __restrict__ vx2, double* __restrict__ vy2, double* __restrict__ vz2,
     double* __restrict__ m2, double* __restrict__ eps2, uint32_t* __restrict__ id2,
     float4* __restrict__ pf_hi, float4* __restrict__ pf_lo) {
+    const bool sorted = !(st->overflow & kSortStall);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const SysBox& b = box[sys ? sys[i] : 0];
         const double c0 = b.c0[0], c1 = b.c0[1], c2 = b.c0[2];
-        uint32_t s = perm[i];
+        const uint32_t s = sorted ? perm[i] : (uint32_t)i;
         double px = x[s], py = y[s], pz = z[s], pm = m[s], pe = eps[s];
         x2[i] = px;
         y2[i] = py;
@@ -790,7 +794,7 @@ int reorder_particles(fdps_tree* t, fdps_psys* ps) {
     const int64_t n = ps->n;
     int grid = grid_for(n, 256, ctx->sm_count * 16);
     k_reorder<<<grid, 256, 0, ctx->stream>>>(
-        n, t->perm, t->sys_box, ps->d_sys, ps->x[c], ps->y[c], ps->z[c], ps->vx[c], ps->vy[c], ps->vz[c],
+        t->st, n, t->perm, t->sys_box, ps->d_sys, ps->x[c], ps->y[c], ps->z[c], ps->vx[c], ps->vy[c], ps->vz[c],
         ps->m[c], ps->eps[c], ps->id[c], ps->x[o], ps->y[o], ps->z[o], ps->vx[o], ps->vy[o],
         ps->vz[o], ps->m[o], ps->eps[o], ps->id[o], t->pf_hi, t->pf_lo);
     FDPS_LAUNCH_CHECK(ctx);
