@@ -1,13 +1,12 @@
-// build.cu -- level-parallel octree build, bottom-up moments and i-groups.
+// build.cu -- octree build, bottom-up moments and i-groups.
 //
 // Octree (the Barnes-Hut tree of Sect. 3.2; its rules are this library's
 // reading): a node is a (level l, key prefix) pair holding >= 1 particle; it
 // is a leaf iff it holds <= n_leaf particles or l = 21; an internal node's
 // children are its non-empty octants in digit order.  Node ids are BFS
-// order: level-major, prefix ascending.  Level l+1 is produced from level l
-// in three launches: per (parent, octant) slot a binary search of the
-// sorted keys for the octant's first particle, a scan of non-empty slots,
-// and the writes.
+// order: level-major, prefix ascending.  All levels are built at once from
+// the sorted keys, one thread per position (see the particle-parallel build
+// below).
 //
 // Moments: M and S = sum m x are accumulated in FP64 with explicitly
 // rounded adds and multiplies (no FMA), leaves sequentially over their
