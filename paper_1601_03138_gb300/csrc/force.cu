@@ -498,24 +498,53 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
     __syncthreads();
 }
 
+// Shared memory of the FP32 kernels (one CTA per group at a time).
+template <bool QUAD, int EPT>
+struct F32Shared {
+    static constexpr int kCE = kCB * EPT;
+    static constexpr int kSpjBytes = kCE * (QUAD ? 40 : 16);
+    static constexpr int kRedBytes = 4 * kRed * 8;
+    static constexpr int kUnion = kSpjBytes > kRedBytes ? kSpjBytes : kRedBytes;
+    __align__(16) unsigned char u[kUnion];  // superparticles of a chunk, or the slice reduction
+    __align__(16) float4 j[kCJ];
+    uint32_t ef[kCE];
+    uint32_t es[kCE];
+    uint32_t w[2 * kCW];
+    float k[4 * 8 * kCB];  // Kahan sums and compensations
+};
+
+// Forces on the particles of group g, with the whole CTA.
+template <bool QUAD, int EPT>
+__device__ __forceinline__ void force_group(const ForceArgs& A, uint32_t g, F32Shared<QUAD, EPT>& sm) {
+    constexpr int kCE = F32Shared<QUAD, EPT>::kCE;
+    SpjBuf<QUAD> sb;
+    sb.s0 = reinterpret_cast<float4*>(sm.u);
+    sb.s1 = reinterpret_cast<float4*>(sm.u + kCE * 16);
+    sb.s2 = reinterpret_cast<float2*>(sm.u + kCE * 32);
+    double* s_red = reinterpret_cast<double*>(sm.u);
+    const uint32_t ni = A.g_count[g], gf = A.g_first[g];
+    const unsigned long long off = A.g_off[g];
+    const uint32_t len = A.g_len[g];
+    const float4 gch = A.g_ch[g], gcl = A.g_cl[g];
+    for (uint32_t ib = 0; ib < ni;) {
+        const GroupPlan pl = plan_group(ni - ib);
+        if (pl.K == 1)
+            force_round_f32<QUAD, 1, EPT>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, sm.j, sb, sm.ef,
+                                          sm.es, sm.w, s_red, sm.k);
+        else if (pl.K == 2)
+            force_round_f32<QUAD, 2, EPT>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, sm.j, sb, sm.ef,
+                                          sm.es, sm.w, s_red, sm.k);
+        else
+            force_round_f32<QUAD, 4, EPT>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, sm.j, sb, sm.ef,
+                                          sm.es, sm.w, s_red, sm.k);
+        ib += (uint32_t)(pl.P * pl.K);
+    }
+}
+
 template <bool QUAD, int EPT>
 __global__ void __launch_bounds__(kCB, (QUAD ? 4 : 1)) k_force_f32(ForceArgs A) {
-    constexpr int kCE = kCB * EPT;
-    constexpr int kSpjBytes = kCE * (QUAD ? 40 : 16);
-    constexpr int kRedBytes = 4 * kRed * 8;
-    constexpr int kUnion = kSpjBytes > kRedBytes ? kSpjBytes : kRedBytes;
-    __shared__ __align__(16) unsigned char s_union[kUnion];
-    __shared__ __align__(16) float4 s_j[kCJ];
-    __shared__ uint32_t s_ef[kCE];
-    __shared__ uint32_t s_es[kCE];
-    __shared__ uint32_t s_w[2 * kCW];
+    __shared__ F32Shared<QUAD, EPT> sm;
     __shared__ uint32_t s_g;
-    __shared__ float s_k[4 * 8 * kCB];  // Kahan sums and compensations
-    SpjBuf<QUAD> sb;
-    sb.s0 = reinterpret_cast<float4*>(s_union);
-    sb.s1 = reinterpret_cast<float4*>(s_union + kCE * 16);
-    sb.s2 = reinterpret_cast<float2*>(s_union + kCE * 32);
-    double* s_red = reinterpret_cast<double*>(s_union);
     DevState* st = A.st;
     // lists cut short by a buffer overflow may point past the pool: no work
     // (a step replayed from a graph is redone by the host)
@@ -527,23 +556,7 @@ __global__ void __launch_bounds__(kCB, (QUAD ? 4 : 1)) k_force_f32(ForceArgs A) 
         const uint32_t g = s_g;
         __syncthreads();
         if (g >= ngroups) break;
-        const uint32_t ni = A.g_count[g], gf = A.g_first[g];
-        const unsigned long long off = A.g_off[g];
-        const uint32_t len = A.g_len[g];
-        const float4 gch = A.g_ch[g], gcl = A.g_cl[g];
-        for (uint32_t ib = 0; ib < ni;) {
-            const GroupPlan pl = plan_group(ni - ib);
-            if (pl.K == 1)
-                force_round_f32<QUAD, 1, EPT>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, s_j, sb,
-                                         s_ef, s_es, s_w, s_red, s_k);
-            else if (pl.K == 2)
-                force_round_f32<QUAD, 2, EPT>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, s_j, sb,
-                                         s_ef, s_es, s_w, s_red, s_k);
-            else
-                force_round_f32<QUAD, 4, EPT>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, s_j, sb,
-                                         s_ef, s_es, s_w, s_red, s_k);
-            ib += (uint32_t)(pl.P * pl.K);
-        }
+        force_group<QUAD, EPT>(A, g, sm);
     }
 }
 
@@ -692,8 +705,7 @@ int force_blocks(fdps_ctx* ctx, int precision, int quad) {
     return per_sm * ctx->sm_count;
 }
 
-int compute_forces(fdps_tree* t, fdps_psys* ps, int spj_kind) {
-    fdps_ctx* ctx = t->ctx;
+ForceArgs force_args(fdps_tree* t, fdps_psys* ps) {
     const int c = ps->cur;
     ForceArgs A;
     A.st = t->st;
@@ -722,6 +734,12 @@ int compute_forces(fdps_tree* t, fdps_psys* ps, int spj_kind) {
     A.ay = ps->ay;
     A.az = ps->az;
     A.pot = ps->pot;
+    return A;
+}
+
+int compute_forces(fdps_tree* t, fdps_psys* ps, int spj_kind) {
+    fdps_ctx* ctx = t->ctx;
+    const ForceArgs A = force_args(t, ps);
     const bool quad = spj_kind == FDPS_GRAV_SPJ_QUAD;
     const int blocks = force_blocks(ctx, t->p.precision, quad);
     cudaStream_t s = ctx->stream;

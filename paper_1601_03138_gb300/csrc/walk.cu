@@ -57,7 +57,6 @@ struct WalkArgs {
 
 namespace {
 
-constexpr int kWalkBlock = 128;
 constexpr unsigned long long kChunk = 1ull << 16;
 constexpr float kU32 = 5.9604645e-08f;  // 2^-24, unit roundoff of FP32
 
@@ -81,211 +80,244 @@ __device__ __forceinline__ bool open_fp64(double L, int level, double theta2, co
     return __dmul_rn(ell, ell) >= __dmul_rn(theta2, d2);
 }
 
-__global__ void __launch_bounds__(kWalkBlock, 8) k_walk(WalkArgs A) {
+// What a warp carries from one group's walk to the next: its pool chunk
+// and its totals for the device state word.  Every field is the same in
+// all lanes.
+struct WalkState {
+    unsigned long long cursor, chunk_end;
+    bool ovf;
+    unsigned long long acc_entries, acc_epj, acc_spj, acc_iepj, acc_ispj, acc_fb;
+    uint32_t max_front;
+};
+
+__device__ __forceinline__ WalkState walk_state_init() {
+    WalkState S;
+    S.cursor = S.chunk_end = 0;
+    S.ovf = false;
+    S.acc_entries = S.acc_epj = S.acc_spj = S.acc_iepj = S.acc_ispj = S.acc_fb = 0;
+    S.max_front = 0;
+    return S;
+}
+
+// The list of group g, walked by the calling warp (all 32 lanes), with its
+// two frontier buffers fa and fb.
+__device__ __forceinline__ void walk_group(const WalkArgs& A, uint32_t g, uint32_t* fa, uint32_t* fb,
+                                           WalkState& S) {
     DevState* st = A.st;
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
+    const uint32_t F = A.cap_frontier;
+    // the group's system: its root node (node id = system index) and box
+    const uint32_t sysid = A.sys ? A.sys[A.g_first[g]] : 0u;
+    const double L = A.box[sysid].L;
+    const float Lf = __double2float_rn(L);
+    // the FP32 filter's bound holds while the squares of cell sizes stay
+    // normal FP32 numbers (with or without flushing of subnormals): outside
+    // this range of root boxes every test takes the exact FP64 sequence
+    const bool filt = Lf >= 0x1p-40f && Lf <= 0x1p60f;
+    const uint32_t* qb = A.g_qbox + 6 * (int64_t)g;
+    const uint32_t qmin0 = qb[0], qmin1 = qb[1], qmin2 = qb[2];
+    const uint32_t qmax0 = qb[3], qmax1 = qb[4], qmax2 = qb[5];
+    const float4 gch = A.g_ch[g], gcl = A.g_cl[g];
+    const float4 blo = A.g_blo[g], bhi = A.g_bhi[g];
+    const float hb = fmaxf(fmaxf(fmaxf(-blo.x, -blo.y), fmaxf(-blo.z, bhi.x)), fmaxf(bhi.y, bhi.z));
+    const double* box64 = A.g_box + 6 * (int64_t)g;
+
+    unsigned long long gstart = S.cursor;
+    uint32_t nspj = 0, nepj_lane = 0;
+    uint32_t fsize = 1;
+    if (lane == 0) fa[0] = sysid;
+    __syncwarp();
+    while (fsize > 0) {
+        uint32_t nsize = 0;
+        S.max_front = fsize > S.max_front ? fsize : S.max_front;
+        // the first batch's frontier entries, node records and COM pairs;
+        // every batch then fetches the next one's before testing its own
+        // (frontier ids two batches ahead, records one batch ahead, so
+        // no batch waits on a load that depends on another load)
+        uint32_t node_nx = lane < fsize ? fa[lane] : 0u;
+        uint32_t node_nx2 = lane + 32 < fsize ? fa[lane + 32] : 0u;
+        uint4 rec_nx = make_uint4(0, 0, 0, 0);
+        float4 fh_nx = make_float4(0.f, 0.f, 0.f, 0.f), fl_nx = fh_nx;
+        if (lane < fsize) {
+            rec_nx = A.nd_walk[node_nx];
+            fh_nx = A.nd_f[2 * node_nx];
+            fl_nx = A.nd_f[2 * node_nx + 1];
+        }
+        for (uint32_t base = 0; base < fsize; base += 32) {
+            const uint32_t idx = base + lane;
+            const bool act = idx < fsize;
+            const uint32_t node = node_nx;
+            const uint4 rec = rec_nx;
+            const float4 fh = fh_nx, fl = fl_nx;
+            if (idx + 32 < fsize) {
+                node_nx = node_nx2;
+                rec_nx = A.nd_walk[node_nx];
+                fh_nx = A.nd_f[2 * node_nx];
+                fl_nx = A.nd_f[2 * node_nx + 1];
+            }
+            if (idx + 64 < fsize) node_nx2 = fa[idx + 64];
+            int action = 0;  // 1 SPJ, 2 EPJ leaf, 3 open internal
+            uint32_t nch = 0, child = 0;
+            bool fallback = false;
+            if (act) {
+                const int level = (int)((rec.x >> 21) & 31u);
+                const bool leaf = (rec.x >> 26) & 1u;
+                const uint32_t w = (1u << (kMaxLevel - level)) - 1u;
+                const uint32_t qx = rec.x & kQMax, qy = rec.y, qz = rec.z;
+                const bool meets = qx <= qmax0 && qx + w >= qmin0 && qy <= qmax1 &&
+                                   qy + w >= qmin1 && qz <= qmax2 && qz + w >= qmin2;
+                bool open = true;
+                if (!meets) {
+                    const float dx = (fh.x - gch.x) + (fl.x - gcl.x);
+                    const float dy = (fh.y - gch.y) + (fl.y - gcl.y);
+                    const float dz = (fh.z - gch.z) + (fl.z - gcl.z);
+                    const float tx = fmaxf(fmaxf(blo.x - dx, dx - bhi.x), 0.0f);
+                    const float ty = fmaxf(fmaxf(blo.y - dy, dy - bhi.y), 0.0f);
+                    const float tz = fmaxf(fmaxf(blo.z - dz, dz - bhi.z), 0.0f);
+                    const float d2 = tx * tx + ty * ty + tz * tz;
+                    // L 2^-level, exact: an exponent decrement of the normal FP32 L
+                    const float ell = __int_as_float(__float_as_int(Lf) - (level << 23));
+                    const float l2 = ell * ell;
+                    const float r2 = A.theta2f * d2;
+                    const float T = l2 - r2;
+                    // bound on |T - (ell^2 - theta^2 D^2)|, D the exact distance
+                    const float E = 4.0f * kU32 *
+                                        (fmaxf(fmaxf(fabsf(dx), fabsf(dy)), fabsf(dz)) + hb) +
+                                    1e-13f * Lf;
+                    const float S1 = tx + ty + tz;
+                    const float margin =
+                        8.0f * kU32 * (l2 + r2) + A.theta2f * (2.0f * E * S1 + 3.0f * E * E);
+                    if (filt && T > margin) {
+                        open = true;
+                    } else if (filt && T < -margin) {
+                        open = false;
+                    } else {
+                        fallback = true;
+                        open = open_fp64(L, level, A.theta2, A.nd_com[node], box64);
+                    }
+                }
+                if (!open) {
+                    action = 1;
+                } else if (leaf) {
+                    action = 2;
+                    nepj_lane += rec.w;  // the leaf's particle count
+                } else {
+                    action = 3;
+                    child = rec.w;
+                    nch = rec.x >> 27;
+                }
+            }
+            S.acc_fb += __popc(__ballot_sync(0xFFFFFFFFu, fallback));
+            // ---- append SPJ / EPJ entries
+            const bool emit = action == 1 || action == 2;
+            const uint32_t emask = __ballot_sync(0xFFFFFFFFu, emit);
+            const uint32_t k = __popc(emask);
+            if (k) {
+                if (S.cursor + k > S.chunk_end) {
+                    // new chunk: at least kChunk entries and twice the
+                    // group's list so far, so long lists move O(log) times
+                    const unsigned long long sofar = S.cursor - gstart;
+                    const unsigned long long want =
+                        2 * (sofar + k) > kChunk ? 2 * (sofar + k) : kChunk;
+                    unsigned long long nb = 0;
+                    if (lane == 0) nb = atomicAdd(&st->pool_cursor, want);
+                    nb = shfl_u64(nb, 0);
+                    if (!S.ovf && nb + want > A.cap_pool) {
+                        if (lane == 0) atomicOr(&st->overflow, kOvfPool);
+                        S.ovf = true;
+                    }
+                    if (!S.ovf) {
+                        for (unsigned long long j = lane; j < sofar; j += 32)
+                            A.pool[nb + j] = A.pool[gstart + j];
+                        __syncwarp();
+                        gstart = nb;
+                        S.cursor = nb + sofar;
+                        S.chunk_end = nb + want;
+                    } else {
+                        S.chunk_end = ~0ull;  // count only from here on
+                    }
+                }
+                if (emit && !S.ovf)
+                    A.pool[S.cursor + __popc(emask & lt)] = action == 2 ? (node | kLeafTag) : node;
+                S.cursor += k;
+            }
+            nspj += __popc(__ballot_sync(0xFFFFFFFFu, action == 1));
+            // ---- push children of opened internal cells (deep in the
+            // tree most batches open none)
+            if (__ballot_sync(0xFFFFFFFFu, nch > 0u)) {
+                uint32_t inc = nch;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    uint32_t tv = __shfl_up_sync(0xFFFFFFFFu, inc, off);
+                    if (lane >= off) inc += tv;
+                }
+                const uint32_t tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
+                if (nsize + tot > F) {
+                    if (lane == 0) atomicOr(&st->overflow, kOvfFrontier);
+                    S.ovf = true;
+                } else {
+                    const uint32_t o = nsize + inc - nch;
+                    for (uint32_t c = 0; c < nch; ++c) fb[o + c] = child + c;
+                    nsize += tot;
+                }
+            }
+        }
+        __syncwarp();
+        uint32_t* tmp = fa;
+        fa = fb;
+        fb = tmp;
+        fsize = nsize;
+    }
+    const uint32_t nepj = __reduce_add_sync(0xFFFFFFFFu, nepj_lane);
+    const unsigned long long len = S.cursor - gstart;
+    if (lane == 0) {
+        A.g_off[g] = gstart;
+        A.g_len[g] = (uint32_t)len;
+        A.g_nspj[g] = nspj;
+        A.g_nepj[g] = nepj;
+    }
+    const unsigned long long ni = A.g_count[g];
+    S.acc_entries += len;
+    S.acc_epj += nepj;
+    S.acc_spj += nspj;
+    S.acc_iepj += ni * nepj;
+    S.acc_ispj += ni * nspj;
+}
+
+// The warp's totals into the device state word (lane 0).
+__device__ __forceinline__ void walk_flush(const WalkArgs& A, const WalkState& S) {
+    DevState* st = A.st;
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&st->pool_needed, S.acc_entries);
+        atomicAdd(&st->list_entries, S.acc_entries);
+        atomicAdd(&st->n_epj, S.acc_epj);
+        atomicAdd(&st->n_spj, S.acc_spj);
+        atomicAdd(&st->int_epj, S.acc_iepj);
+        atomicAdd(&st->int_spj, S.acc_ispj);
+        atomicAdd(&st->fallbacks, S.acc_fb);
+        atomicMax(&st->max_frontier, S.max_front);
+    }
+}
+
+constexpr int kWalkBlock = 128;
+
+__global__ void __launch_bounds__(kWalkBlock, 8) k_walk(WalkArgs A) {
+    DevState* st = A.st;
+    const int lane = threadIdx.x & 31;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     uint32_t* fa = A.frontier + wid * 2 * (int64_t)A.cap_frontier;
     uint32_t* fb = fa + A.cap_frontier;
-    const uint32_t F = A.cap_frontier;
     const uint32_t ngroups = (uint32_t)st->n_groups;
-
-    unsigned long long cursor = 0, chunk_end = 0;
-    bool ovf = false;
-    unsigned long long acc_entries = 0, acc_epj = 0, acc_spj = 0, acc_iepj = 0, acc_ispj = 0,
-                       acc_fb = 0;
-    uint32_t max_front = 0;
-
+    WalkState S = walk_state_init();
     for (;;) {
         uint32_t g = 0;
         if (lane == 0) g = atomicAdd(&st->walk_counter, 1u);
         g = __shfl_sync(0xFFFFFFFFu, g, 0);
         if (g >= ngroups) break;
-
-        // the group's system: its root node (node id = system index) and box
-        const uint32_t sysid = A.sys ? A.sys[A.g_first[g]] : 0u;
-        const double L = A.box[sysid].L;
-        const float Lf = __double2float_rn(L);
-        const uint32_t* qb = A.g_qbox + 6 * (int64_t)g;
-        const uint32_t qmin0 = qb[0], qmin1 = qb[1], qmin2 = qb[2];
-        const uint32_t qmax0 = qb[3], qmax1 = qb[4], qmax2 = qb[5];
-        const float4 gch = A.g_ch[g], gcl = A.g_cl[g];
-        const float4 blo = A.g_blo[g], bhi = A.g_bhi[g];
-        const float hb = fmaxf(fmaxf(fmaxf(-blo.x, -blo.y), fmaxf(-blo.z, bhi.x)), fmaxf(bhi.y, bhi.z));
-        const double* box64 = A.g_box + 6 * (int64_t)g;
-
-        unsigned long long gstart = cursor;
-        uint32_t nspj = 0, nepj_lane = 0;
-        uint32_t fsize = 1;
-        if (lane == 0) fa[0] = sysid;
-        __syncwarp();
-        while (fsize > 0) {
-            uint32_t nsize = 0;
-            max_front = fsize > max_front ? fsize : max_front;
-            // the first batch's frontier entries, node records and COM pairs;
-            // every batch then fetches the next one's before testing its own
-            // (frontier ids two batches ahead, records one batch ahead, so
-            // no batch waits on a load that depends on another load)
-            uint32_t node_nx = lane < fsize ? fa[lane] : 0u;
-            uint32_t node_nx2 = lane + 32 < fsize ? fa[lane + 32] : 0u;
-            uint4 rec_nx = make_uint4(0, 0, 0, 0);
-            float4 fh_nx = make_float4(0.f, 0.f, 0.f, 0.f), fl_nx = fh_nx;
-            if (lane < fsize) {
-                rec_nx = A.nd_walk[node_nx];
-                fh_nx = A.nd_f[2 * node_nx];
-                fl_nx = A.nd_f[2 * node_nx + 1];
-            }
-            for (uint32_t base = 0; base < fsize; base += 32) {
-                const uint32_t idx = base + lane;
-                const bool act = idx < fsize;
-                const uint32_t node = node_nx;
-                const uint4 rec = rec_nx;
-                const float4 fh = fh_nx, fl = fl_nx;
-                if (idx + 32 < fsize) {
-                    node_nx = node_nx2;
-                    rec_nx = A.nd_walk[node_nx];
-                    fh_nx = A.nd_f[2 * node_nx];
-                    fl_nx = A.nd_f[2 * node_nx + 1];
-                }
-                if (idx + 64 < fsize) node_nx2 = fa[idx + 64];
-                int action = 0;  // 1 SPJ, 2 EPJ leaf, 3 open internal
-                uint32_t nch = 0, child = 0;
-                bool fallback = false;
-                if (act) {
-                    const int level = (int)((rec.x >> 21) & 31u);
-                    const bool leaf = (rec.x >> 26) & 1u;
-                    const uint32_t w = (1u << (kMaxLevel - level)) - 1u;
-                    const uint32_t qx = rec.x & kQMax, qy = rec.y, qz = rec.z;
-                    const bool meets = qx <= qmax0 && qx + w >= qmin0 && qy <= qmax1 &&
-                                       qy + w >= qmin1 && qz <= qmax2 && qz + w >= qmin2;
-                    bool open = true;
-                    if (!meets) {
-                        const float dx = (fh.x - gch.x) + (fl.x - gcl.x);
-                        const float dy = (fh.y - gch.y) + (fl.y - gcl.y);
-                        const float dz = (fh.z - gch.z) + (fl.z - gcl.z);
-                        const float tx = fmaxf(fmaxf(blo.x - dx, dx - bhi.x), 0.0f);
-                        const float ty = fmaxf(fmaxf(blo.y - dy, dy - bhi.y), 0.0f);
-                        const float tz = fmaxf(fmaxf(blo.z - dz, dz - bhi.z), 0.0f);
-                        const float d2 = tx * tx + ty * ty + tz * tz;
-                        // L 2^-level, exact: an exponent decrement of the normal FP32 L
-                        const float ell = __int_as_float(__float_as_int(Lf) - (level << 23));
-                        const float l2 = ell * ell;
-                        const float r2 = A.theta2f * d2;
-                        const float T = l2 - r2;
-                        // bound on |T - (ell^2 - theta^2 D^2)|, D the exact distance
-                        const float E = 4.0f * kU32 *
-                                            (fmaxf(fmaxf(fabsf(dx), fabsf(dy)), fabsf(dz)) + hb) +
-                                        1e-13f * Lf;
-                        const float S1 = tx + ty + tz;
-                        const float margin =
-                            8.0f * kU32 * (l2 + r2) + A.theta2f * (2.0f * E * S1 + 3.0f * E * E);
-                        if (T > margin) {
-                            open = true;
-                        } else if (T < -margin) {
-                            open = false;
-                        } else {
-                            fallback = true;
-                            open = open_fp64(L, level, A.theta2, A.nd_com[node], box64);
-                        }
-                    }
-                    if (!open) {
-                        action = 1;
-                    } else if (leaf) {
-                        action = 2;
-                        nepj_lane += rec.w;  // the leaf's particle count
-                    } else {
-                        action = 3;
-                        child = rec.w;
-                        nch = rec.x >> 27;
-                    }
-                }
-                acc_fb += __popc(__ballot_sync(0xFFFFFFFFu, fallback));
-                // ---- append SPJ / EPJ entries
-                const bool emit = action == 1 || action == 2;
-                const uint32_t emask = __ballot_sync(0xFFFFFFFFu, emit);
-                const uint32_t k = __popc(emask);
-                if (k) {
-                    if (cursor + k > chunk_end) {
-                        // new chunk: at least kChunk entries and twice the
-                        // group's list so far, so long lists move O(log) times
-                        const unsigned long long sofar = cursor - gstart;
-                        const unsigned long long want =
-                            2 * (sofar + k) > kChunk ? 2 * (sofar + k) : kChunk;
-                        unsigned long long nb = 0;
-                        if (lane == 0) nb = atomicAdd(&st->pool_cursor, want);
-                        nb = shfl_u64(nb, 0);
-                        if (!ovf && nb + want > A.cap_pool) {
-                            if (lane == 0) atomicOr(&st->overflow, kOvfPool);
-                            ovf = true;
-                        }
-                        if (!ovf) {
-                            for (unsigned long long j = lane; j < sofar; j += 32)
-                                A.pool[nb + j] = A.pool[gstart + j];
-                            __syncwarp();
-                            gstart = nb;
-                            cursor = nb + sofar;
-                            chunk_end = nb + want;
-                        } else {
-                            chunk_end = ~0ull;  // count only from here on
-                        }
-                    }
-                    if (emit && !ovf)
-                        A.pool[cursor + __popc(emask & lt)] = action == 2 ? (node | kLeafTag) : node;
-                    cursor += k;
-                }
-                nspj += __popc(__ballot_sync(0xFFFFFFFFu, action == 1));
-                // ---- push children of opened internal cells (deep in the
-                // tree most batches open none)
-                if (__ballot_sync(0xFFFFFFFFu, nch > 0u)) {
-                    uint32_t inc = nch;
-#pragma unroll
-                    for (int off = 1; off < 32; off <<= 1) {
-                        uint32_t tv = __shfl_up_sync(0xFFFFFFFFu, inc, off);
-                        if (lane >= off) inc += tv;
-                    }
-                    const uint32_t tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
-                    if (nsize + tot > F) {
-                        if (lane == 0) atomicOr(&st->overflow, kOvfFrontier);
-                        ovf = true;
-                    } else {
-                        const uint32_t o = nsize + inc - nch;
-                        for (uint32_t c = 0; c < nch; ++c) fb[o + c] = child + c;
-                        nsize += tot;
-                    }
-                }
-            }
-            __syncwarp();
-            uint32_t* tmp = fa;
-            fa = fb;
-            fb = tmp;
-            fsize = nsize;
-        }
-        const uint32_t nepj = __reduce_add_sync(0xFFFFFFFFu, nepj_lane);
-        const unsigned long long len = cursor - gstart;
-        if (lane == 0) {
-            A.g_off[g] = gstart;
-            A.g_len[g] = (uint32_t)len;
-            A.g_nspj[g] = nspj;
-            A.g_nepj[g] = nepj;
-        }
-        const unsigned long long ni = A.g_count[g];
-        acc_entries += len;
-        acc_epj += nepj;
-        acc_spj += nspj;
-        acc_iepj += ni * nepj;
-        acc_ispj += ni * nspj;
+        walk_group(A, g, fa, fb, S);
     }
-    if (lane == 0) {
-        atomicAdd(&st->pool_needed, acc_entries);
-        atomicAdd(&st->list_entries, acc_entries);
-        atomicAdd(&st->n_epj, acc_epj);
-        atomicAdd(&st->n_spj, acc_spj);
-        atomicAdd(&st->int_epj, acc_iepj);
-        atomicAdd(&st->int_spj, acc_ispj);
-        atomicAdd(&st->fallbacks, acc_fb);
-        atomicMax(&st->max_frontier, max_front);
-    }
+    walk_flush(A, S);
 }
 
 }  // namespace
@@ -302,8 +334,7 @@ int walk_warps_per_block() { return kWalkBlock / 32; }
 
 unsigned long long walk_chunk() { return kChunk; }
 
-int launch_walk(fdps_tree* t, const uint32_t* sys, int blocks) {
-    fdps_ctx* ctx = t->ctx;
+WalkArgs walk_args(fdps_tree* t, const uint32_t* sys) {
     WalkArgs A;
     A.st = t->st;
     A.nd_count = t->nd_count;
@@ -330,6 +361,12 @@ int launch_walk(fdps_tree* t, const uint32_t* sys, int blocks) {
     A.cap_frontier = (uint32_t)t->cap_frontier;
     A.theta2 = t->p.theta * t->p.theta;
     A.theta2f = (float)A.theta2;
+    return A;
+}
+
+int launch_walk(fdps_tree* t, const uint32_t* sys, int blocks) {
+    fdps_ctx* ctx = t->ctx;
+    const WalkArgs A = walk_args(t, sys);
     k_walk<<<blocks, kWalkBlock, 0, ctx->stream>>>(A);
     FDPS_LAUNCH_CHECK(ctx);
     return FDPS_OK;
