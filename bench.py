@@ -198,17 +198,22 @@ def workload_name(args):
             f"n_grp={args.n_grp} eps={args.eps} dt={args.dt:.6g}")
 
 
-def cpu_sample(pos, mass, eps, args, seconds):
+def cpu_sample(pos, mass, eps, args, seconds, built=None, seed=1):
     """The oracle as it stands on a bounded sample of the same workload:
     full tree build, then walk + force for a random subset of i-groups sized
-    to about `seconds` of CPU work.  Returns a cpu_baseline dict."""
+    to about `seconds` of CPU work, the build charged in proportion to the
+    particles sampled.  `built` = (tree, build seconds) reuses one build of
+    the same particle set.  Returns a cpu_baseline dict."""
     import oracle
-    t0 = time.perf_counter()
-    tree = oracle.Tree(pos, mass, eps, theta=args.theta, n_leaf=args.n_leaf, n_grp=args.n_grp,
-                       quad=not args.mono)
-    t_build = time.perf_counter() - t0
+    if built is None:
+        t0 = time.perf_counter()
+        tree = oracle.Tree(pos, mass, eps, theta=args.theta, n_leaf=args.n_leaf, n_grp=args.n_grp,
+                           quad=not args.mono)
+        t_build = time.perf_counter() - t0
+    else:
+        tree, t_build = built
     ng = tree.n_groups
-    rng = np.random.default_rng(1)
+    rng = np.random.default_rng(seed)
     order = rng.permutation(ng)
     done, inter, t_force, k = 0, 0, 0.0, 16
     gcount = tree.groups()["count"]
@@ -235,12 +240,18 @@ def run_reference(args, rank, world):
         return
     pos, vel, mass, eps = make_inputs(args)
     import oracle
-    for _ in range(args.warmup):
-        cpu_sample(pos, mass, eps, args, 1.0)
+    # one build of the particle set, timed once and charged pro rata to
+    # every sample; the samples take different random groups
+    t0 = time.perf_counter()
+    tree = oracle.Tree(pos, mass, eps, theta=args.theta, n_leaf=args.n_leaf, n_grp=args.n_grp,
+                       quad=not args.mono)
+    built = (tree, time.perf_counter() - t0)
+    for k in range(args.warmup):
+        cpu_sample(pos, mass, eps, args, 1.0, built, seed=1000 + k)
     vals = []
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        vals.append(cpu_sample(pos, mass, eps, args, args.cpu_seconds / max(args.steps, 1)))
+    for k in range(args.steps):
+        vals.append(cpu_sample(pos, mass, eps, args, args.cpu_seconds / max(args.steps, 1), built, seed=1 + k))
     wall = time.perf_counter() - t0
     v = statistics.median([c["value"] for c in vals])
     line = {"impl": "reference", "metric": "particle-interactions/s", "value": v,
