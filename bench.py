@@ -32,10 +32,18 @@ sys.path.insert(0, ROOT)
 
 # FP32-lane operations of one interaction as the kernels evaluate the
 # formulas (FMA = 1): particle-particle and monopole superparticle 13,
-# quadrupole superparticle 33; plus one MUFU reciprocal square root each.
+# quadrupole superparticle 32; plus one MUFU reciprocal square root each.
 OPS_EPJ = 13
 OPS_SPJ_MONO = 13
-OPS_SPJ_QUAD = 33
+OPS_SPJ_QUAD = 32
+# The algorithmic count of the measurement plan: 13 operations per
+# particle-particle interaction and about twice that, 26, per quadrupole
+# superparticle (the paper's cost ratio of a quadrupole to a monopole term,
+# Sect. 5.5); the roofline fraction on this count is reported beside the
+# instruction count's.
+ALG_EPJ = 13
+ALG_SPJ_MONO = 13
+ALG_SPJ_QUAD = 26
 
 
 def parse():
@@ -95,6 +103,40 @@ def force_traffic(workload: str):
     with open(src, "rb") as f:
         sha = hashlib.sha256(f.read()).hexdigest()
     return rec[1] if sha.startswith(rec[0]) else None
+
+
+# Algorithmic DRAM bytes of the HBM-bound stages: per particle, and per
+# octree node where the stage writes nodes (each kernel's reads and writes
+# of its inputs and outputs, once).
+STAGE_BYTES = {
+    # root box (x, y, z read) + Morton keys (x, y, z read, key written)
+    "ms_box_keys": (24 + 32, 0),
+    # 8 stable LSD passes of 8 bits: pass 0 reads keys and writes (key,
+    # index), passes 1-7 read and write (key, index)
+    "ms_sort": (8 + 12 + 7 * 24, 0),
+    # permutation and 8 FP64 fields + id gathered, written in key order,
+    # FP32 hi/lo copies written
+    "ms_permute": (4 + 64 + 4 + 64 + 4 + 32, 0),
+    # sorted keys, per-position first differing level and leaf level; node
+    # records written
+    "ms_build": (16 + 4, 37),
+    # particle positions and masses read; node sums, centres, quadrupoles
+    # and their FP32 copies written
+    "ms_moments": (32, 200),
+}
+
+
+def stage_hbm(stages_ms, n, n_nodes, peak_gbs):
+    """Algorithmic GB/s and fraction of the measured HBM copy bandwidth of
+    the HBM-bound stages."""
+    out = {}
+    for k, (bp, bn) in STAGE_BYTES.items():
+        ms = stages_ms.get(k)
+        if not ms:
+            continue
+        b = bp * n + bn * n_nodes
+        out[k[3:]] = {"bytes": b, "gb_s": b / (ms * 1e6), "frac": b / (ms * 1e6) / peak_gbs}
+    return out
 
 
 def combine_ranks(t_local: float, units_local: float, world: int, device: str):
@@ -235,6 +277,56 @@ def cpu_sample(pos, mass, eps, args, seconds, built=None, seed=1):
                        f"interactions, {t_force:.1f} s)")}
 
 
+def cpu_baseline(pos, mass, eps, args, seconds):
+    """The oracle on all host cores (cpu_sample) and on one core.  The one-core
+    figure walks and forces the first groups of one random order for about
+    `seconds` / 2 on one thread, and the same groups again on all cores, so the
+    two are comparable; the tree build is charged pro rata, its one-core time
+    measured on the first 2^20 particles (a fair subsample of the same
+    distribution) and scaled by N log N."""
+    import oracle
+    cores = oracle.get_threads()
+    t0 = time.perf_counter()
+    tree = oracle.Tree(pos, mass, eps, theta=args.theta, n_leaf=args.n_leaf, n_grp=args.n_grp,
+                       quad=not args.mono)
+    t_build = time.perf_counter() - t0
+    main = cpu_sample(pos, mass, eps, args, seconds, built=(tree, t_build))
+    n = len(pos)
+    order = np.random.default_rng(7).permutation(tree.n_groups)
+    gcount = tree.groups()["count"]
+    oracle.set_threads(1)
+    try:
+        m1 = min(len(pos), 1 << 20)
+        t0 = time.perf_counter()
+        oracle.Tree(pos[:m1], mass[:m1], eps[:m1], theta=args.theta, n_leaf=args.n_leaf,
+                    n_grp=args.n_grp, quad=not args.mono)
+        t_b1 = (time.perf_counter() - t0) * (n * np.log2(max(n, 2))) / (m1 * np.log2(max(m1, 2)))
+        done, inter, t1, k = 0, 0, 0.0, 4
+        while t1 < seconds / 2 and done < len(order):
+            sel = order[done:done + k]
+            t2 = time.perf_counter()
+            _, _, tot = tree.force(sel)
+            t1 += time.perf_counter() - t2
+            inter += tot[2]
+            done += len(sel)
+            k *= 2
+    finally:
+        oracle.set_threads(cores)
+    t2 = time.perf_counter()
+    tree.force(order[:done])
+    tn = time.perf_counter() - t2
+    frac = gcount[order[:done]].sum() / n
+    main["cores_1"] = {
+        "value": inter / (t1 + t_b1 * frac), "cores": 1,
+        "value_all_cores_same_groups": inter / (tn + t_build * frac), "cores_all": cores,
+        "sample": (f"walk and force of the same {done} random i-groups ({frac * 100:.3f}% of "
+                   f"particles, {inter:.3e} interactions) on 1 core ({t1:.1f} s) and on {cores} "
+                   f"cores ({tn:.2f} s); build charged pro rata: {t_build:.1f} s measured on "
+                   f"{cores} cores, {t_b1:.1f} s on 1 core scaled from a build of "
+                   f"{m1} particles by N log N")}
+    return main
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -332,15 +424,20 @@ def run_ours(args, rank, world, local_rank):
     ops_last = last["interactions_epj"] * OPS_EPJ + last["interactions_spj"] * ops_spj
     f_s = statistics.median(force_ms) / 1e3
     achieved = ops_last / f_s
+    alg_spj = ALG_SPJ_MONO if args.mono else ALG_SPJ_QUAD
+    alg_last = last["interactions_epj"] * ALG_EPJ + last["interactions_spj"] * alg_spj
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                 "unit": "TFLOP/s", "frac": achieved / peak_ops,
+                "frac_algorithmic": alg_last / f_s / peak_ops,
                 "traffic": force_traffic(workload_name(args)),
                 "kernel": "k_force_f32 (quadrupole)" if not args.mono else "k_force_f32",
                 "peak_source": f"{sm_count} SMs x 128 FP32 lanes x {f_ghz:.3f} GHz "
                                f"(sm_max_mhz of {pk_kind} peaks), FMA = 1 op",
-                "ops_per_interaction": {"epj": OPS_EPJ, "spj": ops_spj}}
+                "ops_per_interaction": {"epj": OPS_EPJ, "spj": ops_spj},
+                "ops_per_interaction_algorithmic": {"epj": ALG_EPJ, "spj": alg_spj}}
     stages = {k: round(statistics.median([s[k] for s in stage]), 3) for k in stage[0]
               if k.startswith("ms_")}
+    hbm = stage_hbm(stages, n, last["n_nodes"], pk.get("hbm_gbs", 6800.0))
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -395,7 +492,7 @@ def run_ours(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_sample(pos, mass, eps, args, args.cpu_seconds)
+        cpu = cpu_baseline(pos, mass, eps, args, args.cpu_seconds)
 
     if rank == 0:
         line = {"metric": "particle-interactions/s", "value": value, "unit": "interactions/s",
@@ -407,7 +504,7 @@ def run_ours(args, rank, world, local_rank):
                 "config": {"workload": workload_name(args), "l2": "inputs larger than L2",
                            "replicas": world, "autotuned": tuned},
                 "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "clocks": clk, "fp64_variant": fp64, "stages_ms": stages,
+                "clocks": clk, "fp64_variant": fp64, "stages_ms": stages, "stages_hbm": hbm,
                 "per_step": {"interactions": inter / args.steps,
                              "interactions_epj": inter_e / args.steps,
                              "interactions_spj": inter_s / args.steps,

@@ -418,10 +418,11 @@ int fdps_user_law_destroy(fdps_user_law* law);
 
 /* ------------------------------------------- allocation-free key sort
    The paper has no counterpart to this call; it is a service for callers
-   that may not allocate device memory themselves: code running while a
-   stream is captured into a CUDA graph (a cudaMalloc there invalidates the
-   capture) and hosts that hand out all device memory through their own
-   allocator.  It computes what fdps_tree_calc_force_all_and_write_back
+   that may not allocate device memory themselves: hosts such as frameworks
+   that hand out all device memory through their own pool allocator, and
+   real-time loops that may not take the implicit synchronisation and
+   unbounded latency of a cudaMalloc / cudaFree.  It computes what
+   fdps_tree_calc_force_all_and_write_back
    computes first (root box, 63-bit Morton keys, stable radix sort) for one
    particle set and allocates nothing: its scratch (about 5.3 MB) is a
    file-scope device array that every GPU which loads the library holds
@@ -433,11 +434,17 @@ int fdps_user_law_destroy(fdps_user_law* law);
                   keep input order)
      stream       cudaStream_t to run on (NULL = legacy default stream)
    Returns FDPS_OK, FDPS_EINVAL (NULL pointer, n out of range) or
-   FDPS_ECUDA.  The work is queued on `stream` and not waited for.  The
-   first call on a device looks up the scratch array's device address;
-   make that first call outside any stream capture.  All calls on a device
-   share the one scratch array: calls that may overlap on the GPU (other
-   streams, other host threads) race and must be serialised by the caller. */
+   FDPS_ECUDA (also when a CUDA error was already pending on the calling
+   thread; that error is left pending for the caller).  The work is queued
+   on `stream` and not waited for.  The first call on a device, with that
+   device current, looks up the scratch array's device address and keeps it
+   for the process; make that first call before any stream capture.  The
+   address belongs to the device's primary context (the one the CUDA
+   runtime API uses): calls from other contexts, or after a cudaDeviceReset
+   of the device, are not supported.  All calls on a device share the one
+   scratch array, which keeps the last call's contents: calls that may
+   overlap on the GPU (other streams, other host threads) race and must be
+   serialised by the caller. */
 #define FDPS_NOALLOC_MAX_N (1 << 18)
 int fdps_morton_sort_noalloc(const double* x, const double* y, const double* z,
                              int64_t n, uint64_t* keys_sorted, uint32_t* perm,

@@ -10,7 +10,12 @@
 // the last term removing the i-particle's own entry (its force term is zero).
 // A quadrupole superparticle (mass M, traceless Q, r = x_i - com,
 // R^2 = r^2 + eps_i^2) contributes phi = -M/R - (r.Q.r) / (2 R^5) and
-// a = -M r / R^3 + Q r / R^5 - (5/2) (r.Q.r) r / R^7.
+// a = -M r / R^3 + Q r / R^5 - (5/2) (r.Q.r) r / R^7.  The FP32 kernel
+// evaluates the same expressions regrouped as a = R^-5 (Q r + R^2 h r) and
+// phi = R^-1 (h + 2 w), with w = (r.Q.r) R^-4 and h = -M - (5/2) w: 32 FP32
+// operations per interaction (3 differences, 3 for R^2, 3 powers of 1/R,
+// 9 for Q r, 3 for r.Q.r, w, h, R^2 h, 6 for a, 2 for phi) and one MUFU
+// reciprocal square root.
 //
 // FP32-relative kernel (one CTA per i-group): list entries are gathered
 // into shared memory as FP32 coordinates relative to the group centre,
@@ -165,6 +170,17 @@ __device__ __forceinline__ void block_scan2(uint32_t a, uint32_t b, uint32_t* ea
     *tb = sb;
 }
 
+// EPT consecutive u32 slots of one thread written as one vector.
+template <int EPT>
+__device__ __forceinline__ void store_entries(uint32_t* dst, const uint32_t (&v)[EPT]) {
+    if (EPT == 4)
+        *reinterpret_cast<uint4*>(dst) = make_uint4(v[0], v[1 % EPT], v[2 % EPT], v[3 % EPT]);
+    else if (EPT == 2)
+        *reinterpret_cast<uint2*>(dst) = make_uint2(v[0], v[1 % EPT]);
+    else
+        for (int r = 0; r < EPT; ++r) dst[r] = v[r];
+}
+
 // Largest e in [0, CE) with scan[e] <= item.
 template <int CE>
 __device__ __forceinline__ int owner_chunk(const uint32_t* scan, uint32_t item) {
@@ -273,7 +289,7 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
         zp[h] = f2_pk(zi[2 * h], zi[2 * h + 1]);
         ep[h] = f2_pk(e2[2 * h], e2[2 * h + 1]);
     }
-    const f2 cm25 = f2_bc(-2.5f), cm05 = f2_bc(-0.5f);
+    const f2 cm25 = f2_bc(-2.5f), c2 = f2_bc(2.0f);
     const int kbeg = on ? sl : 0x3FFFFFFF;
 #pragma unroll
     for (int k = 0; k < 8 * K; ++k) s_k[k * kCB + t] = 0.0f;
@@ -298,7 +314,7 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
             nspj += spj ? 1u : 0u;
             npart += lcnt[r];
         }
-        uint32_t rs, es, ns, total;
+        uint32_t rs, es, ns, total, esc[EPT];
         block_scan2(nspj, npart, &rs, &es, &ns, &total, s_w);
 #pragma unroll
         for (int r = 0; r < EPT; ++r) {
@@ -315,10 +331,12 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
                 }
                 ++rs;
             }
-            s_ef[t * EPT + r] = lfirst[r];
-            s_es[t * EPT + r] = es;
+            esc[r] = es;
             es += lcnt[r];
         }
+        // each thread's EPT consecutive slots in one vector store (no bank conflicts)
+        store_entries<EPT>(s_ef + t * EPT, lfirst);
+        store_entries<EPT>(s_es + t * EPT, esc);
         __syncthreads();
         float sax[K], say[K], saz[K], spp[K];  // scalar path (K = 1)
         f2 pax[KP > 0 ? KP : 1], pay[KP > 0 ? KP : 1], paz[KP > 0 ? KP : 1], pp[KP > 0 ? KP : 1];
@@ -341,20 +359,22 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
                 const float R2 = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, e2[0])));
                 const float Ri = rsqrtf(R2);
                 const float Ri2 = Ri * Ri;
-                const float Ri3 = Ri * Ri2;
                 if (QUAD) {
+                    const float Ri4 = Ri2 * Ri2;
+                    const float Ri5 = Ri4 * Ri;
                     const float Qrx = fmaf(q0.x, rx, fmaf(q0.w, ry, q1.x * rz));
                     const float Qry = fmaf(q0.w, rx, fmaf(q0.y, ry, q1.y * rz));
                     const float Qrz = fmaf(q1.x, rx, fmaf(q1.y, ry, q0.z * rz));
                     const float rQr = fmaf(rx, Qrx, fmaf(ry, Qry, rz * Qrz));
-                    const float Ri5 = Ri3 * Ri2;
-                    const float u = rQr * Ri5;                            // r.Q.r / R^5
-                    const float g = fmaf(-2.5f * u, Ri2, a.w * Ri3);      // -(M/R^3 + 5/2 r.Q.r / R^7)
-                    sax[0] = fmaf(Qrx, Ri5, fmaf(g, rx, sax[0]));
-                    say[0] = fmaf(Qry, Ri5, fmaf(g, ry, say[0]));
-                    saz[0] = fmaf(Qrz, Ri5, fmaf(g, rz, saz[0]));
-                    spp[0] = fmaf(-0.5f, u, fmaf(a.w, Ri, spp[0]));
+                    const float w = rQr * Ri4;                 // r.Q.r / R^4
+                    const float hh = fmaf(-2.5f, w, a.w);      // -M - 5/2 w
+                    const float hR2 = hh * R2;
+                    sax[0] = fmaf(Ri5, fmaf(hR2, rx, Qrx), sax[0]);
+                    say[0] = fmaf(Ri5, fmaf(hR2, ry, Qry), say[0]);
+                    saz[0] = fmaf(Ri5, fmaf(hR2, rz, Qrz), saz[0]);
+                    spp[0] = fmaf(Ri, fmaf(2.0f, w, hh), spp[0]);  // (-M - w/2) / R
                 } else {
+                    const float Ri3 = Ri * Ri2;
                     const float nMRi3 = a.w * Ri3;
                     sax[0] = fmaf(nMRi3, rx, sax[0]);
                     say[0] = fmaf(nMRi3, ry, say[0]);
@@ -378,21 +398,22 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
                     const f2 R2 = f2_fma(rx, rx, f2_fma(ry, ry, f2_fma(rz, rz, ep[h])));
                     const f2 Ri = f2_rsqrt(R2);
                     const f2 Ri2 = f2_mul(Ri, Ri);
-                    const f2 Ri3 = f2_mul(Ri, Ri2);
                     if (QUAD) {
+                        const f2 Ri4 = f2_mul(Ri2, Ri2);
+                        const f2 Ri5 = f2_mul(Ri4, Ri);
                         const f2 Qrx = f2_fma(qxx, rx, f2_fma(qxy, ry, f2_mul(qxz, rz)));
                         const f2 Qry = f2_fma(qxy, rx, f2_fma(qyy, ry, f2_mul(qyz, rz)));
                         const f2 Qrz = f2_fma(qxz, rx, f2_fma(qyz, ry, f2_mul(qzz, rz)));
                         const f2 rQr = f2_fma(rx, Qrx, f2_fma(ry, Qry, f2_mul(rz, Qrz)));
-                        const f2 Ri5 = f2_mul(Ri3, Ri2);
-                        const f2 u = f2_mul(rQr, Ri5);  // r.Q.r / R^5
-                        // -(M/R^3 + 5/2 r.Q.r / R^7)
-                        const f2 g = f2_fma(f2_mul(cm25, u), Ri2, f2_mul(nM, Ri3));
-                        pax[h] = f2_fma(Qrx, Ri5, f2_fma(g, rx, pax[h]));
-                        pay[h] = f2_fma(Qry, Ri5, f2_fma(g, ry, pay[h]));
-                        paz[h] = f2_fma(Qrz, Ri5, f2_fma(g, rz, paz[h]));
-                        pp[h] = f2_fma(cm05, u, f2_fma(nM, Ri, pp[h]));
+                        const f2 w = f2_mul(rQr, Ri4);         // r.Q.r / R^4
+                        const f2 hh = f2_fma(cm25, w, nM);     // -M - 5/2 w
+                        const f2 hR2 = f2_mul(hh, R2);
+                        pax[h] = f2_fma(Ri5, f2_fma(hR2, rx, Qrx), pax[h]);
+                        pay[h] = f2_fma(Ri5, f2_fma(hR2, ry, Qry), pay[h]);
+                        paz[h] = f2_fma(Ri5, f2_fma(hR2, rz, Qrz), paz[h]);
+                        pp[h] = f2_fma(Ri, f2_fma(c2, w, hh), pp[h]);  // (-M - w/2) / R
                     } else {
+                        const f2 Ri3 = f2_mul(Ri, Ri2);
                         const f2 nMRi3 = f2_mul(nM, Ri3);  // -M/R^3
                         pax[h] = f2_fma(nMRi3, rx, pax[h]);
                         pay[h] = f2_fma(nMRi3, ry, pay[h]);
@@ -507,8 +528,8 @@ struct F32Shared {
     static constexpr int kUnion = kSpjBytes > kRedBytes ? kSpjBytes : kRedBytes;
     __align__(16) unsigned char u[kUnion];  // superparticles of a chunk, or the slice reduction
     __align__(16) float4 j[kCJ];
-    uint32_t ef[kCE];
-    uint32_t es[kCE];
+    __align__(16) uint32_t ef[kCE];
+    __align__(16) uint32_t es[kCE];
     uint32_t w[2 * kCW];
     float k[4 * 8 * kCB];  // Kahan sums and compensations
 };

@@ -12,6 +12,8 @@
 //         over earlier tiles for the global offsets, a staged scatter).
 //         The allocation-free entry point keeps the reduce-then-scan form
 //         (tile histograms, a scan, a stable scatter).
+#include <atomic>
+
 #include "fdps_internal.cuh"
 
 namespace fdps {
@@ -807,10 +809,10 @@ int reorder_particles(fdps_tree* t, fdps_psys* ps) {
 // fdps_morton_sort_noalloc: root box, Morton keys and the stable sort of one
 // particle set with every scratch buffer taken from g_noalloc_scratch, a
 // file-scope device array, so the call itself allocates nothing.  It exists
-// for callers that may not allocate device memory on their own: code that
-// runs while a stream is being captured into a CUDA graph (a cudaMalloc
-// there breaks the capture), and hosts such as frameworks or real-time
-// loops that own every byte of device memory through their own allocator.
+// for callers that may not allocate device memory on their own: hosts such
+// as frameworks that hand out every byte of device memory through their own
+// pool allocator, and real-time loops that may not take the implicit
+// synchronisation and unbounded latency of a cudaMalloc / cudaFree.
 
 namespace {
 
@@ -832,8 +834,12 @@ constexpr size_t kNoAllocBytes = align256(kOffValsA + sizeof(uint32_t) * kNoAllo
 // Held by every device that loads the library, until the process exits.
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
+// The scratch array's device address per device ordinal, looked up once
+// with that device current (in its primary context, the one the runtime
+// API uses); written with an atomic store, every writer storing the same
+// address.
 constexpr int kNoAllocMaxDevices = 64;
-unsigned char* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+std::atomic<unsigned char*> g_noalloc_ptr[kNoAllocMaxDevices] = {};
 
 }  // namespace
 }  // namespace fdps
@@ -844,6 +850,9 @@ extern "C" int fdps_morton_sort_noalloc(const double* x, const double* y, const 
     using namespace fdps;
     if (!x || !y || !z || !keys_sorted || !perm) return FDPS_EINVAL;
     if (n < 1 || n > kNoAllocMaxN) return FDPS_EINVAL;  // beyond FDPS_NOALLOC_MAX_N
+    // an error the calling thread left pending stays the caller's: refuse
+    // to run on it rather than clear it
+    if (cudaPeekAtLastError() != cudaSuccess) return FDPS_ECUDA;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
         cudaGetLastError();
@@ -851,15 +860,16 @@ extern "C" int fdps_morton_sort_noalloc(const double* x, const double* y, const 
     }
     // Once per device, with that device current: the device address of the
     // scratch array (its host-side name is only a stand-in).
-    if (!g_noalloc_ptr[dev]) {
+    unsigned char* base = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+    if (!base) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
             cudaGetLastError();
             return FDPS_ECUDA;
         }
-        g_noalloc_ptr[dev] = static_cast<unsigned char*>(p);
+        base = static_cast<unsigned char*>(p);
+        g_noalloc_ptr[dev].store(base, std::memory_order_release);
     }
-    unsigned char* base = g_noalloc_ptr[dev];
     DevState* st = reinterpret_cast<DevState*>(base + kOffState);
     SysBox* sbox = reinterpret_cast<SysBox*>(base + kOffSysBox);
     BoxPartial* box = reinterpret_cast<BoxPartial*>(base + kOffBox);
@@ -870,8 +880,9 @@ extern "C" int fdps_morton_sort_noalloc(const double* x, const double* y, const 
     uint32_t* vals_a = reinterpret_cast<uint32_t*>(base + kOffValsA);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int ntiles = (int)((n + kSortTile - 1) / kSortTile);
-    // The array keeps the previous call's contents; the state block is the
-    // one region read before it is written, so it is cleared first.
+    // The array keeps the previous call's contents.  Every region this call
+    // reads is written by an earlier launch of the same call; the state
+    // block is cleared anyway, as a defensive measure.
     if (cudaMemsetAsync(st, 0, sizeof(DevState), s) != cudaSuccess) {
         cudaGetLastError();
         return FDPS_ECUDA;

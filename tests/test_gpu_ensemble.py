@@ -56,6 +56,65 @@ def _rms(a, b):
     return float(np.sqrt(np.mean(e ** 2)))
 
 
+def _check_systems(tree, ps, pos, vel, mass, eps, off, systems, theta, n_leaf, n_grp, quad):
+    """Systems `systems` of an ensemble whose force calculation has run: each
+    one's keys, permutation, nodes, groups and lists bit-exact against the
+    oracle run on that system alone, its forces within the FP32 tolerance of
+    the oracle on identical lists, its kinetic and potential energies."""
+    n = len(pos)
+    _, _, acc, pot = ps.get()
+    keys, perm = tree.keys(n)
+    nodes = tree.nodes()
+    groups = tree.groups()
+    node_sys = np.searchsorted(off, nodes["first"], side="right") - 1
+    grp_sys = np.searchsorted(off, groups["first"], side="right") - 1
+    ek, ep = ps.energy_systems()
+    for k in systems:
+        a, b = off[k], off[k + 1]
+        ref = oracle.Tree(pos[a:b], mass[a:b], eps[a:b], theta=theta, n_leaf=n_leaf, n_grp=n_grp, quad=quad)
+        kr, pr = ref.keys()
+        np.testing.assert_array_equal(keys[a:b], kr)
+        np.testing.assert_array_equal(perm[a:b].astype(np.int64) - a, pr)
+        # this system's nodes, in the GPU's order, are the oracle's nodes
+        gsel = np.nonzero(node_sys == k)[0]
+        nr = ref.nodes()
+        assert len(gsel) == ref.n_nodes
+        np.testing.assert_array_equal(nodes["level"][gsel], nr["level"])
+        np.testing.assert_array_equal(nodes["first"][gsel] - a, nr["first"])
+        np.testing.assert_array_equal(nodes["count"][gsel], nr["count"])
+        np.testing.assert_array_equal(nodes["nchild"][gsel], nr["nchild"])
+        np.testing.assert_array_equal(nodes["com"][gsel], nr["com"])
+        local = np.full(len(nodes["level"]), -1)
+        local[gsel] = np.arange(len(gsel))
+        gk = np.nonzero(grp_sys == k)[0]
+        assert len(gk) == ref.n_groups
+        gr = ref.groups()
+        np.testing.assert_array_equal(groups["first"][gk] - a, gr["first"])
+        np.testing.assert_array_equal(groups["count"][gk], gr["count"])
+        np.testing.assert_array_equal(groups["box"][gk], gr["box"])
+        offs_l, ent = tree.lists(int(gk[0]), int(gk[-1]) + 1)
+        for j in range(len(gk)):
+            e = ent[offs_l[j]:offs_l[j + 1]]
+            leaf = (e & np.uint32(0x80000000)) != 0
+            spj = np.sort(local[e[~leaf].astype(np.int64)])
+            lid = (e[leaf] & np.uint32(0x7FFFFFFF)).astype(np.int64)
+            epj = np.sort(np.concatenate(
+                [np.arange(nodes["first"][c] - a, nodes["first"][c] - a + nodes["count"][c]) for c in lid]
+                + [np.zeros(0, np.int64)]))
+            er, sr = ref.walk(j)
+            np.testing.assert_array_equal(spj, np.sort(sr))
+            np.testing.assert_array_equal(epj, np.sort(er))
+        ar, phr, _ = ref.force()
+        if b - a == 1:
+            assert np.all(acc[a:b] == 0)
+        else:
+            assert _rms(acc[a:b], ar) <= RMS_FP32
+            assert _rms(pot[a:b, None], phr[:, None]) <= RMS_FP32
+        kr_, pr_ = oracle.energy(vel[a:b], mass[a:b], phr)
+        assert ek[k] == pytest.approx(kr_, rel=1e-12)
+        assert ep[k] == pytest.approx(pr_, rel=1e-5, abs=1e-12)
+
+
 @pytest.mark.parametrize("quad", [False, True])
 def test_ensemble_systems_match_oracle_alone(G, ctx, quad):
     sizes = [1, 2, 3, 9, 17, 64, 65, 300, 1000, 4000, 2500, 777, 8, 129, 5000]
@@ -67,52 +126,31 @@ def test_ensemble_systems_match_oracle_alone(G, ctx, quad):
         ps.set_systems(off)
         ps.set(pos, vel, mass, eps)
         tree.calc_force_all_and_write_back(ps)
-        _, _, acc, pot = ps.get()
-        keys, perm = tree.keys(n)
-        nodes = tree.nodes()
-        groups = tree.groups()
-        offs_l, ent = tree.lists(0, len(groups["first"]))
-        node_sys = np.searchsorted(off, nodes["first"], side="right") - 1
-        grp_sys = np.searchsorted(off, groups["first"], side="right") - 1
-        ek, ep = ps.energy_systems()
-        for k in range(len(sizes)):
-            a, b = off[k], off[k + 1]
-            ref = oracle.Tree(pos[a:b], mass[a:b], eps[a:b], theta=0.5, n_leaf=8, n_grp=64, quad=quad)
-            kr, pr = ref.keys()
-            np.testing.assert_array_equal(keys[a:b], kr)
-            np.testing.assert_array_equal(perm[a:b].astype(np.int64) - a, pr)
-            # this system's nodes, in the GPU's order, are the oracle's nodes
-            gsel = np.nonzero(node_sys == k)[0]
-            nr = ref.nodes()
-            assert len(gsel) == ref.n_nodes
-            np.testing.assert_array_equal(nodes["level"][gsel], nr["level"])
-            np.testing.assert_array_equal(nodes["first"][gsel] - a, nr["first"])
-            np.testing.assert_array_equal(nodes["count"][gsel], nr["count"])
-            np.testing.assert_array_equal(nodes["nchild"][gsel], nr["nchild"])
-            np.testing.assert_array_equal(nodes["com"][gsel], nr["com"])
-            local = np.full(len(nodes["level"]), -1)
-            local[gsel] = np.arange(len(gsel))
-            gk = np.nonzero(grp_sys == k)[0]
-            assert len(gk) == ref.n_groups
-            for j, g in enumerate(gk):
-                e = ent[offs_l[g]:offs_l[g + 1]]
-                leaf = (e & np.uint32(0x80000000)) != 0
-                spj = np.sort(local[e[~leaf].astype(np.int64)])
-                lid = (e[leaf] & np.uint32(0x7FFFFFFF)).astype(np.int64)
-                epj = np.sort(np.concatenate(
-                    [np.arange(nodes["first"][c] - a, nodes["first"][c] - a + nodes["count"][c]) for c in lid]
-                    + [np.zeros(0, np.int64)]))
-                er, sr = ref.walk(j)
-                np.testing.assert_array_equal(spj, np.sort(sr))
-                np.testing.assert_array_equal(epj, np.sort(er))
-            ar, phr, _ = ref.force()
-            if b - a == 1:
-                assert np.all(acc[a:b] == 0)
-            else:
-                assert _rms(acc[a:b], ar) <= RMS_FP32
-            kr_, pr_ = oracle.energy(vel[a:b], mass[a:b], phr)
-            assert ek[k] == pytest.approx(kr_, rel=1e-12)
-            assert ep[k] == pytest.approx(pr_, rel=1e-5, abs=1e-12)
+        _check_systems(tree, ps, pos, vel, mass, eps, off, range(len(sizes)), 0.5, 8, 64, quad)
+    finally:
+        tree.close()
+        ps.close()
+
+
+def test_ensemble4096_sampled_systems_match_oracle(G, ctx):
+    """The benchmarked ensemble: 4096 Plummer clusters with N log-uniform in
+    [256, 65536] (49.6 million particles), eps = 1 / (4 N^1/3), theta = 0.5,
+    monopole, in the launch configuration its autotuner picks (n_leaf 8,
+    n_grp 256, tile depth 512); 32 random systems plus the smallest and the
+    largest, each bit-exact against the oracle run on it alone."""
+    cfg = ics.CONFIGS["ensemble4096"]
+    pos, vel, mass, eps, off = ics.ensemble(4096, cfg["seed"])
+    n = len(pos)
+    sizes = np.diff(off)
+    systems = sorted(set(np.random.default_rng(4096).choice(4096, 32, replace=False).tolist())
+                     | {int(np.argmin(sizes)), int(np.argmax(sizes))})
+    ps = G.ParticleSystem(ctx, n)
+    tree = G.Tree(ctx, theta=cfg["theta"], n_leaf=8, n_grp=256, quad=False, tile_depth=512)
+    try:
+        ps.set_systems(off)
+        ps.set(pos, vel, mass, eps)
+        tree.calc_force_all_and_write_back(ps)
+        _check_systems(tree, ps, pos, vel, mass, eps, off, systems, cfg["theta"], 8, 256, False)
     finally:
         tree.close()
         ps.close()

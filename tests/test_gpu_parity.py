@@ -321,9 +321,12 @@ def test_leapfrog_matches_oracle_integration(G, ctx):
 
 
 def _sampled_parity(G, ctx, pos, vel, mass, eps, theta, n_leaf, n_grp, quad, n_sample, n_direct,
-                    direct_tol):
+                    direct_tol, tile_depth=0):
+    """Structure bit-exact, lists and forces of n_sample random groups against
+    the oracle; the median force error of n_direct random particles against
+    the FP64 direct sum, returned (asserted <= direct_tol unless None)."""
     n = len(pos)
-    ps, tree = run_gpu(G, ctx, pos, vel, mass, eps, theta, n_leaf, n_grp, quad)
+    ps, tree = run_gpu(G, ctx, pos, vel, mass, eps, theta, n_leaf, n_grp, quad, tile_depth=tile_depth)
     try:
         ref = oracle.Tree(pos, mass, eps, theta=theta, n_leaf=n_leaf, n_grp=n_grp, quad=quad)
         sample = np.random.default_rng(n).choice(ref.n_groups, n_sample, replace=False)
@@ -337,7 +340,9 @@ def _sampled_parity(G, ctx, pos, vel, mass, eps, theta, n_leaf, n_grp, quad, n_s
         idx = np.random.default_rng(n + 1).choice(n, n_direct, replace=False)
         ad, pd = oracle.direct(pos, mass, eps, idx)
         err = np.linalg.norm(acc[idx] - ad, axis=1) / np.linalg.norm(ad, axis=1)
-        assert np.median(err) <= direct_tol
+        if direct_tol is not None:
+            assert np.median(err) <= direct_tol
+        return float(np.median(err))
     finally:
         tree.close()
         ps.close()
@@ -350,13 +355,42 @@ def test_parity_three_million_ragged(G, ctx):
 
 
 def test_parity_at_full_bench_size(G, ctx):
-    """The benchmark's workload and launch configuration: Hernquist N = 2^24,
-    theta = 0.5, quadrupole, n_leaf = 16, n_grp = 128; every key, the
-    permutation, every node and group bit-exact; lists and forces of 64
-    sampled groups against the oracle; 256 sampled particles against the
-    FP64 direct sum."""
+    """The benchmark's workload in the launch configuration its autotuner
+    picks: Hernquist N = 2^24, theta = 0.5, quadrupole, n_leaf = 16,
+    n_grp = 256, tile depth 512; every key, the permutation, every node and
+    group bit-exact; lists and forces of 1024 sampled groups against the
+    oracle; 256 sampled particles against the FP64 direct sum (median
+    <= 5e-4)."""
     pos, vel, mass, eps = ics.make("hernquist", 1 << 24, ics.SEED_BASE + 3, 0.005)
-    _sampled_parity(G, ctx, pos, vel, mass, eps, 0.5, 16, 128, True, 64, 256, 5e-4)
+    _sampled_parity(G, ctx, pos, vel, mass, eps, 0.5, 16, 256, True, 1024, 256, 5e-4, tile_depth=512)
+
+
+def test_parity_clumpy_2_26(G, ctx):
+    """The clumpy workload at its benchmarked size: 1000 Plummer clumps plus
+    a uniform background, N = 2^26, eps = 0.002, theta = 0.5, quadrupole,
+    n_leaf = 16, n_grp = 256; every key, the permutation, every node and
+    group bit-exact; lists and forces of 128 sampled groups against the
+    oracle (the parity bar).  Accuracy against the FP64 direct sum on 256
+    sampled particles: this strongly clustered set sits at a median of
+    5.2e-4 at theta = 0.5, just above the 5e-4 that the quadrupole tree
+    meets on the Hernquist benchmark (a property of the opening test on
+    cells whose centre of mass lies far from their centre, shared with the
+    oracle), so the bound checked here is 1.5 times that, and the error-
+    controlled opening angle (fdps_tree_choose_theta, checked against the
+    oracle in test_gpu_accuracy.py) must find an angle of at most 0.5 that
+    meets 5e-4 on this set."""
+    pos, vel, mass, eps = ics.make("clumpy", 1 << 26, ics.SEED_BASE + 4, 0.002)
+    med = _sampled_parity(G, ctx, pos, vel, mass, eps, 0.5, 16, 256, True, 128, 256, None, tile_depth=512)
+    assert med <= 7.5e-4
+    ps = G.ParticleSystem(ctx, len(pos))
+    tree = G.Tree(ctx, theta=0.5, n_leaf=16, n_grp=256, quad=True)
+    try:
+        ps.set(pos, vel, mass, eps)
+        theta, med_t = tree.choose_theta(ps, 5e-4, 1024)
+        assert theta <= 0.5 and med_t <= 5e-4
+    finally:
+        tree.close()
+        ps.close()
 
 
 @pytest.mark.parametrize("quad", [False, True])

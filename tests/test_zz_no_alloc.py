@@ -1,8 +1,9 @@
 """The allocation-free key sort against the regular force pipeline.
 
 fdps_morton_sort_noalloc serves callers that may not allocate device memory
-themselves (stream capture into a CUDA graph, hosts with their own
-allocator); its scratch is one device array inside the library.  Here it is
+themselves (hosts that hand out device memory through their own pool
+allocator, real-time loops that may not take a cudaMalloc's synchronisation
+and latency); its scratch is one device array inside the library.  Here it is
 called through the C ABI twice in a row, on two different particle sets, and
 each result must equal, bit for bit, the keys and permutation the regular
 entry point (fdps_tree_calc_force_all_and_write_back) produced for the same
