@@ -81,7 +81,14 @@ typedef enum {
      moment     enum fdps_moment
      precision  enum fdps_precision
      tile_depth list entries staged in shared memory per force-kernel chunk:
-                0 (default, = 512), 256 or 512                            */
+                0 (default, = 512), 256 or 512
+     block      threads per CTA of the FP32 force kernel: 0 (default, =
+                128), 64, 128 or 256
+     i_per_thread  at most this many i-particles per thread of the FP32
+                force kernel: 0 (default, = 4), 2 or 4; block 256 takes 2
+                at most (its Kahan sums would not fit shared memory)
+     (block and i_per_thread, the "block shape", change only the speed;
+     the FP64 variant ignores them)                                      */
 typedef struct {
     double theta;
     int32_t n_leaf;
@@ -89,7 +96,9 @@ typedef struct {
     int32_t moment;
     int32_t precision;
     int32_t tile_depth;
-    int32_t reserved[3];
+    int32_t block;
+    int32_t i_per_thread;
+    int32_t reserved;
 } fdps_tree_params;
 
 /* Per-call counters and stage times (milliseconds, CUDA events, valid when
@@ -229,19 +238,24 @@ int fdps_psys_energy_systems(fdps_psys* ps, double* kinetic, double* potential);
    (FDPS_ESTATE); synchronises the stream once per step. */
 int fdps_run(fdps_tree* tree, fdps_psys* ps, double dt, int64_t n_steps);
 
-/* Autotuner: time the full force calculation (CUDA events, best of
+/* Autotuner (the paper's n_grp trade-off, Sect. 5.5-5.6, measured instead
+   of modelled): time the full force calculation (CUDA events, best of
    `repeats` after one untimed sizing run) for every combination of the
-   candidate n_leaf, n_grp and tile_depth values (tile_depth may be NULL:
-   default only), keep the fastest in the tree's parameters, and leave the
-   forces of that choice in ps.  Combinations the parameter rules reject
-   (n_grp < n_leaf) are skipped.  *best and *best_ms (either may be NULL)
-   receive the winning parameters and its time in milliseconds.  Theta,
-   moment and precision are not tuned: they set the accuracy.
+   candidate n_leaf, n_grp and tile_depth values at the tree's block shape
+   (tile_depth may be NULL: default only); then, at the fastest of those,
+   every combination of the candidate block and i_per_thread values of the
+   FP32 force kernel (either may be NULL: the winner's own).  Keeps the
+   fastest in the tree's parameters and leaves the forces of that choice in
+   ps.  Combinations the parameter rules reject (n_grp < n_leaf, block 256
+   with 4 i-particles) are skipped.  *best and *best_ms (either may be
+   NULL) receive the winning parameters and its time in milliseconds.
+   Theta, moment and precision are not tuned: they set the accuracy.
    Errors: FDPS_EINVAL, FDPS_ESTATE, and those of the force calculation. */
 int fdps_tree_autotune(fdps_tree* tree, fdps_psys* ps, const int32_t* n_leaf, int32_t n_nl,
                        const int32_t* n_grp, int32_t n_ng, const int32_t* tile_depth,
-                       int32_t n_td, int32_t repeats, fdps_tree_params* best,
-                       double* best_ms);
+                       int32_t n_td, const int32_t* block, int32_t n_block,
+                       const int32_t* i_per_thread, int32_t n_ipt, int32_t repeats,
+                       fdps_tree_params* best, double* best_ms);
 
 /* --------------------------------------------------- introspection
    Test and diagnostic access to the last force calculation's

@@ -51,7 +51,7 @@ class FdpsError(RuntimeError):
 class fdps_tree_params(C.Structure):
     _fields_ = [("theta", C.c_double), ("n_leaf", C.c_int32), ("n_grp", C.c_int32),
                 ("moment", C.c_int32), ("precision", C.c_int32), ("tile_depth", C.c_int32),
-                ("reserved", C.c_int32 * 3)]
+                ("block", C.c_int32), ("i_per_thread", C.c_int32), ("reserved", C.c_int32)]
 
 
 class fdps_tree_stats(C.Structure):
@@ -123,7 +123,7 @@ _PROTOS = {
     "fdps_psys_num_systems": (_i32, [_vp]),
     "fdps_psys_energy_systems": (C.c_int, [_vp, _vp, _vp]),
     "fdps_run": (C.c_int, [_vp, _vp, _d, _i64]),
-    "fdps_tree_autotune": (C.c_int, [_vp, _vp, _vp, _i32, _vp, _i32, _vp, _i32, _i32,
+    "fdps_tree_autotune": (C.c_int, [_vp, _vp, _vp, _i32, _vp, _i32, _vp, _i32, _vp, _i32, _vp, _i32, _i32,
                                      C.POINTER(fdps_tree_params), C.POINTER(_d)]),
 }
 
@@ -246,9 +246,9 @@ def fdps_psys_get(ctx, ps, pos=None, vel=None, acc=None, pot=None):
 
 
 def fdps_tree_create(ctx, theta=0.5, n_leaf=8, n_grp=64, moment=FDPS_MONOPOLE,
-                     precision=FDPS_FP32REL, tile_depth=0):
+                     precision=FDPS_FP32REL, tile_depth=0, block=0, i_per_thread=0):
     p = fdps_tree_params(float(theta), int(n_leaf), int(n_grp), int(moment), int(precision),
-                         int(tile_depth))
+                         int(tile_depth), int(block), int(i_per_thread))
     h = C.c_void_p()
     _check(lib().fdps_tree_create(ctx, C.byref(p), C.byref(h)), ctx)
     return h
@@ -298,18 +298,27 @@ def fdps_run(ctx, tree, ps, dt, n_steps):
 
 
 def fdps_tree_autotune(ctx, tree, ps, n_leaf=(8, 16), n_grp=(64, 128, 256, 512),
-                       tile_depth=(256, 512), repeats=2):
-    """Pick the fastest (n_leaf, n_grp, tile_depth); returns (params dict, ms)."""
+                       tile_depth=(256, 512), block=None, i_per_thread=None, repeats=2):
+    """Pick the fastest (n_leaf, n_grp, tile_depth), then the fastest block
+    shape (block, i_per_thread) of the force kernel at that choice (None:
+    not searched); returns (params dict, ms)."""
     nl = np.ascontiguousarray(n_leaf, dtype=np.int32)
     ng = np.ascontiguousarray(n_grp, dtype=np.int32)
     td = np.ascontiguousarray(tile_depth, dtype=np.int32)
+    bl = None if block is None else np.ascontiguousarray(block, dtype=np.int32)
+    ip = None if i_per_thread is None else np.ascontiguousarray(i_per_thread, dtype=np.int32)
     best = fdps_tree_params()
     ms = C.c_double()
     _check(lib().fdps_tree_autotune(tree, ps, C.c_void_p(nl.ctypes.data), len(nl),
                                     C.c_void_p(ng.ctypes.data), len(ng), C.c_void_p(td.ctypes.data),
-                                    len(td), int(repeats), C.byref(best), C.byref(ms)), ctx)
+                                    len(td), None if bl is None else C.c_void_p(bl.ctypes.data),
+                                    0 if bl is None else len(bl),
+                                    None if ip is None else C.c_void_p(ip.ctypes.data),
+                                    0 if ip is None else len(ip), int(repeats), C.byref(best),
+                                    C.byref(ms)), ctx)
     return ({"theta": best.theta, "n_leaf": best.n_leaf, "n_grp": best.n_grp,
-             "tile_depth": best.tile_depth}, ms.value)
+             "tile_depth": best.tile_depth, "block": best.block or 128,
+             "i_per_thread": best.i_per_thread or 4}, ms.value)
 
 
 def fdps_psys_energy(ctx, ps):
@@ -565,12 +574,12 @@ class Tree:
     """TreeForForceLong (monopole or quadrupole) with theta, n_leaf, n_grp."""
 
     def __init__(self, ctx: Context, theta=0.5, n_leaf=8, n_grp=64, quad=False, fp64=False,
-                 tile_depth=0):
+                 tile_depth=0, block=0, i_per_thread=0):
         self.ctx = ctx
         self.quad = bool(quad)
         self.h = fdps_tree_create(ctx.h, theta, n_leaf, n_grp,
                                   FDPS_QUADRUPOLE if quad else FDPS_MONOPOLE,
-                                  FDPS_FP64 if fp64 else FDPS_FP32REL, tile_depth)
+                                  FDPS_FP64 if fp64 else FDPS_FP32REL, tile_depth, block, i_per_thread)
 
     def close(self):
         if getattr(self, "h", None):

@@ -323,7 +323,10 @@ bool valid_params(const fdps_tree_params* p) {
            p->n_leaf <= kMaxLeaf && p->n_grp >= p->n_leaf && p->n_grp <= kMaxGrp &&
            (p->moment == FDPS_MONOPOLE || p->moment == FDPS_QUADRUPOLE) &&
            (p->precision == FDPS_FP32REL || p->precision == FDPS_FP64) &&
-           (p->tile_depth == 0 || p->tile_depth == 256 || p->tile_depth == 512);
+           (p->tile_depth == 0 || p->tile_depth == 256 || p->tile_depth == 512) &&
+           (p->block == 0 || p->block == 64 || p->block == 128 || p->block == 256) &&
+           (p->i_per_thread == 0 || p->i_per_thread == 2 || p->i_per_thread == 4) &&
+           !(p->block == 256 && p->i_per_thread != 2);
 }
 
 }  // namespace
@@ -549,7 +552,9 @@ int fdps_tree_create(fdps_ctx* ctx, const fdps_tree_params* params, fdps_tree** 
     *out = nullptr;
     if (!valid_params(params))
         return set_error(ctx, FDPS_EINVAL,
-                         "invalid tree parameters (theta >= 0, 1 <= n_leaf <= %d, n_leaf <= n_grp <= %d)",
+                         "invalid tree parameters (theta >= 0, 1 <= n_leaf <= %d, n_leaf <= n_grp <= %d, "
+                         "tile_depth 0/256/512, block 0/64/128/256, i_per_thread 0/2/4, block 256 with "
+                         "i_per_thread 2)",
                          kMaxLeaf, kMaxGrp);
     cudaSetDevice(ctx->device);
     fdps_tree* t = new (std::nothrow) fdps_tree();
@@ -1108,6 +1113,7 @@ int fdps_tree_get_lists(const fdps_tree* tc, int64_t g0, int64_t g1, int64_t* of
 
 int fdps_tree_autotune(fdps_tree* t, fdps_psys* ps, const int32_t* n_leaf, int32_t n_nl,
                        const int32_t* n_grp, int32_t n_ng, const int32_t* tile_depth, int32_t n_td,
+                       const int32_t* block, int32_t n_block, const int32_t* i_per_thread, int32_t n_ipt,
                        int32_t repeats, fdps_tree_params* best, double* best_ms) {
     if (!t || !ps || !n_leaf || !n_grp || n_nl < 1 || n_ng < 1 || repeats < 1) return FDPS_EINVAL;
     fdps_ctx* ctx = t->ctx;
@@ -1126,6 +1132,27 @@ int fdps_tree_autotune(fdps_tree* t, fdps_psys* ps, const int32_t* n_leaf, int32
     fdps_tree_params win = orig;
     float win_ms = -1.f;
     int rc = FDPS_OK;
+    // time one candidate: an untimed run (sizes the buffers) unless only the
+    // force kernel's block shape changed, then the best of `repeats`
+    auto trial = [&](const fdps_tree_params& cand, bool sizing) {
+        t->p = cand;
+        if (sizing && (rc = run_force(t, ps, k_spj))) return;
+        float best_here = -1.f;
+        for (int32_t r = 0; r < repeats && !rc; ++r) {
+            cudaEventRecord(e0, ctx->stream);
+            rc = run_force(t, ps, k_spj);
+            cudaEventRecord(e1, ctx->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (best_here < 0.f || ms < best_here) best_here = ms;
+        }
+        if (!rc && (win_ms < 0.f || best_here < win_ms)) {
+            win_ms = best_here;
+            win = cand;
+        }
+    };
+    // stage 1: tree parameters at the tree's block shape
     for (int32_t a = 0; a < n_nl && !rc; ++a)
         for (int32_t b = 0; b < n_ng && !rc; ++b)
             for (int32_t c = 0; c < n_td && !rc; ++c) {
@@ -1134,23 +1161,23 @@ int fdps_tree_autotune(fdps_tree* t, fdps_psys* ps, const int32_t* n_leaf, int32
                 cand.n_grp = n_grp[b];
                 cand.tile_depth = tile_depth[c];
                 if (!valid_params(&cand)) continue;  // e.g. n_grp < n_leaf
-                t->p = cand;
-                if ((rc = run_force(t, ps, k_spj))) break;  // sizes the buffers
-                float best_here = -1.f;
-                for (int32_t r = 0; r < repeats && !rc; ++r) {
-                    cudaEventRecord(e0, ctx->stream);
-                    rc = run_force(t, ps, k_spj);
-                    cudaEventRecord(e1, ctx->stream);
-                    cudaEventSynchronize(e1);
-                    float ms = 0.f;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    if (best_here < 0.f || ms < best_here) best_here = ms;
-                }
-                if (!rc && (win_ms < 0.f || best_here < win_ms)) {
-                    win_ms = best_here;
-                    win = cand;
-                }
+                trial(cand, true);
             }
+    // stage 2: the force kernel's block shape at stage 1's choice
+    if (!rc && win_ms >= 0.f && t->p.precision == FDPS_FP32REL && ((block && n_block > 0) || (i_per_thread && n_ipt > 0))) {
+        const fdps_tree_params base = win;
+        const int32_t nb = (block && n_block > 0) ? n_block : 1;
+        const int32_t ni = (i_per_thread && n_ipt > 0) ? n_ipt : 1;
+        for (int32_t a = 0; a < nb && !rc; ++a)
+            for (int32_t b = 0; b < ni && !rc; ++b) {
+                fdps_tree_params cand = base;
+                if (block && n_block > 0) cand.block = block[a];
+                if (i_per_thread && n_ipt > 0) cand.i_per_thread = i_per_thread[b];
+                if (!valid_params(&cand)) continue;  // e.g. block 256 with 4 i-particles
+                if (cand.block == base.block && cand.i_per_thread == base.i_per_thread) continue;
+                trial(cand, false);
+            }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) {

@@ -96,45 +96,45 @@ __device__ __forceinline__ int owner(const uint32_t* scan, uint32_t item) {
 }
 
 // ---------------------------------------------------------------- FP32
-// One 128-thread CTA per i-group.  Thread t owns K i-particles
-// (i = t % P + k P, k < K) and the list slice j = t / P (mod nsl);
-// (K, P, nsl) is chosen per group to keep the most lanes busy.  The list is
-// consumed in chunks of 512 entries (4 per thread); each chunk's
-// superparticles and leaf particles are staged in shared memory, and each
-// thread folds its FP32 partial sums of the chunk into Kahan-compensated
-// running sums once per chunk.
+// One CTA of CB threads (64, 128 or 256: the "block shape" the autotuner
+// picks, with the cap KMAX on i-particles per thread) per i-group.  Thread t
+// owns K <= KMAX i-particles (i = t % P + k P, k < K) and the list slice
+// j = t / P (mod nsl); (K, P, nsl) is chosen per group to keep the most
+// lanes busy.  The list is consumed in chunks of 256 or 512 entries (the
+// tile depth, EPT per thread); each chunk's superparticles and leaf
+// particles are staged in shared memory, and each thread folds its FP32
+// partial sums of the chunk into Kahan-compensated running sums once per
+// chunk.
 
-constexpr int kCB = 128;            // threads per CTA
-constexpr int kCW = kCB / 32;
-// list entries per thread per chunk (EPT) is a template parameter: the
-// chunk ("tile depth") holds kCB * EPT entries, 256 or 512
-constexpr int kCJ = 256;            // leaf particles per shared tile
-constexpr int kRed = 4 * kCB;       // slice-reduction slots per component
+constexpr int kCJ = 256;  // leaf particles per shared tile
 
 struct GroupPlan {
     int K, P, nsl;
 };
 
+template <int CB, int KMAX>
 __device__ __forceinline__ GroupPlan plan_group(uint32_t ni) {
-    // maximise ni * nsl / (kCB * K) over K in {1, 2, 4}; larger K on ties
+    // maximise ni * nsl / (CB * K) over K in {1, 2, 4} (up to KMAX); larger
+    // K on ties
     GroupPlan best{1, 1, 1};
     float bu = -1.f;
 #pragma unroll
-    for (int K = 4; K >= 1; K >>= 1) {
+    for (int K = KMAX; K >= 1; K >>= 1) {
         const int P = (int)((ni + K - 1) / K);
-        if (P > kCB) continue;
-        const int nsl = kCB / P;
-        const float u = (float)ni * nsl / (float)(kCB * K);
+        if (P > CB) continue;
+        const int nsl = CB / P;
+        const float u = (float)ni * nsl / (float)(CB * K);
         if (u > bu + 1e-6f) {
             bu = u;
             best = GroupPlan{K, P, nsl};
         }
     }
-    if (bu < 0.f) best = GroupPlan{4, kCB, 1};  // more than 4 kCB particles: rounds
+    if (bu < 0.f) best = GroupPlan{KMAX, CB, 1};  // more than KMAX CB particles: rounds
     return best;
 }
 
-// Block-wide exclusive scans of two values at once (kCB threads).
+// Block-wide exclusive scans of two values at once (CB threads).
+template <int CB>
 __device__ __forceinline__ void block_scan2(uint32_t a, uint32_t b, uint32_t* ea, uint32_t* eb,
                                             uint32_t* ta, uint32_t* tb, uint32_t* s_w) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -150,13 +150,13 @@ __device__ __forceinline__ void block_scan2(uint32_t a, uint32_t b, uint32_t* ea
     }
     if (lane == 31) {
         s_w[w] = ia;
-        s_w[kCW + w] = ib;
+        s_w[CB / 32 + w] = ib;
     }
     __syncthreads();
     uint32_t oa = 0, ob = 0, sa = 0, sb = 0;
 #pragma unroll
-    for (int k = 0; k < kCW; ++k) {
-        const uint32_t xa = s_w[k], xb = s_w[kCW + k];
+    for (int k = 0; k < CB / 32; ++k) {
+        const uint32_t xa = s_w[k], xb = s_w[CB / 32 + k];
         if (k < w) {
             oa += xa;
             ob += xb;
@@ -173,7 +173,10 @@ __device__ __forceinline__ void block_scan2(uint32_t a, uint32_t b, uint32_t* ea
 // EPT consecutive u32 slots of one thread written as one vector.
 template <int EPT>
 __device__ __forceinline__ void store_entries(uint32_t* dst, const uint32_t (&v)[EPT]) {
-    if (EPT == 4)
+    if (EPT == 8) {
+        reinterpret_cast<uint4*>(dst)[0] = make_uint4(v[0], v[1 % EPT], v[2 % EPT], v[3 % EPT]);
+        reinterpret_cast<uint4*>(dst)[1] = make_uint4(v[4 % EPT], v[5 % EPT], v[6 % EPT], v[7 % EPT]);
+    } else if (EPT == 4)
         *reinterpret_cast<uint4*>(dst) = make_uint4(v[0], v[1 % EPT], v[2 % EPT], v[3 % EPT]);
     else if (EPT == 2)
         *reinterpret_cast<uint2*>(dst) = make_uint2(v[0], v[1 % EPT]);
@@ -192,10 +195,11 @@ __device__ __forceinline__ int owner_chunk(const uint32_t* scan, uint32_t item) 
 }
 
 // Kahan running sums of one thread in shared memory: sum of (q, c) at
-// s_k[((q * 4 + c) * 2) * kCB + t], its compensation kCB further on.
+// s_k[((q * 4 + c) * 2) * CB + t], its compensation CB further on.
+template <int CB>
 __device__ __forceinline__ void kahan_smem_add(float* s_k, int q, int c, float v) {
-    float* s = s_k + ((q * 4 + c) * 2) * kCB + threadIdx.x;
-    float* cp = s + kCB;
+    float* s = s_k + ((q * 4 + c) * 2) * CB + threadIdx.x;
+    float* cp = s + CB;
     const float y = v - *cp;
     const float t = *s + y;
     *cp = (t - *s) - y;
@@ -254,7 +258,7 @@ struct SpjBuf {
 };
 __device__ __forceinline__ f2 f2_bc(float v) { return f2_pk(v, v); }
 
-template <bool QUAD, int K, int EPT>
+template <bool QUAD, int K, int EPT, int CB, int KMAX>
 __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf, uint32_t ni,
                                                 unsigned long long off, uint32_t len, float4 gch,
                                                 float4 gcl, int P, int nsl, uint32_t ib,
@@ -292,9 +296,10 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
     const f2 cm25 = f2_bc(-2.5f), c2 = f2_bc(2.0f);
     const int kbeg = on ? sl : 0x3FFFFFFF;
 #pragma unroll
-    for (int k = 0; k < 8 * K; ++k) s_k[k * kCB + t] = 0.0f;
+    for (int k = 0; k < 8 * K; ++k) s_k[k * CB + t] = 0.0f;
 
-    constexpr int CE = kCB * EPT;
+    constexpr int CE = CB * EPT;
+    constexpr int kRed = KMAX * CB;  // slice-reduction slots per component
     for (uint32_t base = 0; base < len; base += CE) {
         // ---- this thread's EPT consecutive entries: type, node data, leaf range
         uint32_t nspj = 0, npart = 0;
@@ -315,7 +320,7 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
             npart += lcnt[r];
         }
         uint32_t rs, es, ns, total, esc[EPT];
-        block_scan2(nspj, npart, &rs, &es, &ns, &total, s_w);
+        block_scan2<CB>(nspj, npart, &rs, &es, &ns, &total, s_w);
 #pragma unroll
         for (int r = 0; r < EPT; ++r) {
             const bool spj = ent[r] != 0xFFFFFFFFu && !(ent[r] & kLeafTag);
@@ -427,7 +432,7 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
         for (uint32_t c0 = 0; c0 < total; c0 += kCJ) {
             const uint32_t m = total - c0 < (uint32_t)kCJ ? total - c0 : (uint32_t)kCJ;
             if (c0 > 0) __syncthreads();  // previous tile fully consumed
-            for (uint32_t k = t; k < m; k += kCB) {
+            for (uint32_t k = t; k < m; k += CB) {
                 const uint32_t item = c0 + k;
                 const int src = owner_chunk<CE>(s_es, item);
                 const uint32_t p = s_ef[src] + (item - s_es[src]);
@@ -467,26 +472,26 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
             }
         }
         if (K == 1) {
-            kahan_smem_add(s_k, 0, 0, sax[0]);
-            kahan_smem_add(s_k, 0, 1, say[0]);
-            kahan_smem_add(s_k, 0, 2, saz[0]);
-            kahan_smem_add(s_k, 0, 3, spp[0]);
+            kahan_smem_add<CB>(s_k, 0, 0, sax[0]);
+            kahan_smem_add<CB>(s_k, 0, 1, say[0]);
+            kahan_smem_add<CB>(s_k, 0, 2, saz[0]);
+            kahan_smem_add<CB>(s_k, 0, 3, spp[0]);
         }
 #pragma unroll
         for (int h = 0; h < KP; ++h) {
             float lo, hi;
             f2_up(pax[h], lo, hi);
-            kahan_smem_add(s_k, 2 * h, 0, lo);
-            kahan_smem_add(s_k, 2 * h + 1, 0, hi);
+            kahan_smem_add<CB>(s_k, 2 * h, 0, lo);
+            kahan_smem_add<CB>(s_k, 2 * h + 1, 0, hi);
             f2_up(pay[h], lo, hi);
-            kahan_smem_add(s_k, 2 * h, 1, lo);
-            kahan_smem_add(s_k, 2 * h + 1, 1, hi);
+            kahan_smem_add<CB>(s_k, 2 * h, 1, lo);
+            kahan_smem_add<CB>(s_k, 2 * h + 1, 1, hi);
             f2_up(paz[h], lo, hi);
-            kahan_smem_add(s_k, 2 * h, 2, lo);
-            kahan_smem_add(s_k, 2 * h + 1, 2, hi);
+            kahan_smem_add<CB>(s_k, 2 * h, 2, lo);
+            kahan_smem_add<CB>(s_k, 2 * h + 1, 2, hi);
             f2_up(pp[h], lo, hi);
-            kahan_smem_add(s_k, 2 * h, 3, lo);
-            kahan_smem_add(s_k, 2 * h + 1, 3, hi);
+            kahan_smem_add<CB>(s_k, 2 * h, 3, lo);
+            kahan_smem_add<CB>(s_k, 2 * h + 1, 3, hi);
         }
         __syncthreads();  // chunk buffers are rewritten next
     }
@@ -499,11 +504,11 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
 #pragma unroll
             for (int c = 0; c < 4; ++c)
                 s_red[c * kRed + sl * rows + ip + q * P] =
-                    iv[q] ? (double)s_k[((q * 4 + c) * 2) * kCB + t] -
-                                (double)s_k[((q * 4 + c) * 2 + 1) * kCB + t]
+                    iv[q] ? (double)s_k[((q * 4 + c) * 2) * CB + t] -
+                                (double)s_k[((q * 4 + c) * 2 + 1) * CB + t]
                           : 0.0;
     __syncthreads();
-    for (int r = t; r < rows; r += kCB) {
+    for (int r = t; r < rows; r += CB) {
         const uint32_t i = ib + (uint32_t)r;
         if (i >= ni) continue;
         double v[4] = {0.0, 0.0, 0.0, 0.0};
@@ -520,24 +525,24 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
 }
 
 // Shared memory of the FP32 kernels (one CTA per group at a time).
-template <bool QUAD, int EPT>
+template <bool QUAD, int EPT, int CB, int KMAX>
 struct F32Shared {
-    static constexpr int kCE = kCB * EPT;
+    static constexpr int kCE = CB * EPT;
     static constexpr int kSpjBytes = kCE * (QUAD ? 40 : 16);
-    static constexpr int kRedBytes = 4 * kRed * 8;
+    static constexpr int kRedBytes = 4 * KMAX * CB * 8;
     static constexpr int kUnion = kSpjBytes > kRedBytes ? kSpjBytes : kRedBytes;
     __align__(16) unsigned char u[kUnion];  // superparticles of a chunk, or the slice reduction
     __align__(16) float4 j[kCJ];
     __align__(16) uint32_t ef[kCE];
     __align__(16) uint32_t es[kCE];
-    uint32_t w[2 * kCW];
-    float k[4 * 8 * kCB];  // Kahan sums and compensations
+    uint32_t w[2 * (CB / 32)];
+    float k[KMAX * 8 * CB];  // Kahan sums and compensations
 };
 
 // Forces on the particles of group g, with the whole CTA.
-template <bool QUAD, int EPT>
-__device__ __forceinline__ void force_group(const ForceArgs& A, uint32_t g, F32Shared<QUAD, EPT>& sm) {
-    constexpr int kCE = F32Shared<QUAD, EPT>::kCE;
+template <bool QUAD, int EPT, int CB, int KMAX>
+__device__ __forceinline__ void force_group(const ForceArgs& A, uint32_t g, F32Shared<QUAD, EPT, CB, KMAX>& sm) {
+    constexpr int kCE = F32Shared<QUAD, EPT, CB, KMAX>::kCE;
     SpjBuf<QUAD> sb;
     sb.s0 = reinterpret_cast<float4*>(sm.u);
     sb.s1 = reinterpret_cast<float4*>(sm.u + kCE * 16);
@@ -548,23 +553,26 @@ __device__ __forceinline__ void force_group(const ForceArgs& A, uint32_t g, F32S
     const uint32_t len = A.g_len[g];
     const float4 gch = A.g_ch[g], gcl = A.g_cl[g];
     for (uint32_t ib = 0; ib < ni;) {
-        const GroupPlan pl = plan_group(ni - ib);
-        if (pl.K == 1)
-            force_round_f32<QUAD, 1, EPT>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, sm.j, sb, sm.ef,
-                                          sm.es, sm.w, s_red, sm.k);
-        else if (pl.K == 2)
-            force_round_f32<QUAD, 2, EPT>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, sm.j, sb, sm.ef,
-                                          sm.es, sm.w, s_red, sm.k);
-        else
-            force_round_f32<QUAD, 4, EPT>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, sm.j, sb, sm.ef,
-                                          sm.es, sm.w, s_red, sm.k);
+        const GroupPlan pl = plan_group<CB, KMAX>(ni - ib);
+        if (pl.K == 1) {
+            force_round_f32<QUAD, 1, EPT, CB, KMAX>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, sm.j, sb,
+                                                    sm.ef, sm.es, sm.w, s_red, sm.k);
+        } else if (KMAX == 2 || pl.K == 2) {
+            force_round_f32<QUAD, 2, EPT, CB, KMAX>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, sm.j, sb,
+                                                    sm.ef, sm.es, sm.w, s_red, sm.k);
+        } else {
+            if constexpr (KMAX >= 4)
+                force_round_f32<QUAD, 4, EPT, CB, KMAX>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, sm.j,
+                                                        sb, sm.ef, sm.es, sm.w, s_red, sm.k);
+        }
         ib += (uint32_t)(pl.P * pl.K);
     }
 }
 
-template <bool QUAD, int EPT>
-__global__ void __launch_bounds__(kCB, (QUAD ? 4 : 1)) k_force_f32(ForceArgs A) {
-    __shared__ F32Shared<QUAD, EPT> sm;
+// Up to 16 warps per SM (four 128-thread CTAs: 128 registers a thread).
+template <bool QUAD, int EPT, int CB, int KMAX>
+__global__ void __launch_bounds__(CB, (QUAD ? 512 / CB : 1)) k_force_f32(ForceArgs A) {
+    __shared__ F32Shared<QUAD, EPT, CB, KMAX> sm;
     __shared__ uint32_t s_g;
     DevState* st = A.st;
     // lists cut short by a buffer overflow may point past the pool: no work
@@ -577,7 +585,7 @@ __global__ void __launch_bounds__(kCB, (QUAD ? 4 : 1)) k_force_f32(ForceArgs A) 
         const uint32_t g = s_g;
         __syncthreads();
         if (g >= ngroups) break;
-        force_group<QUAD, EPT>(A, g, sm);
+        force_group<QUAD, EPT, CB, KMAX>(A, g, sm);
     }
 }
 
@@ -713,15 +721,40 @@ __global__ void __launch_bounds__(kFBlock) k_force_f64(ForceArgs A) {
 
 }  // namespace
 
-int force_blocks(fdps_ctx* ctx, int precision, int quad) {
+// One resident wave of FP32 force CTAs of the given shape (chunk CE
+// entries, CB threads, at most KMAX i-particles a thread).
+template <bool QUAD, int CE, int CB, int KMAX>
+void launch_f32(const ForceArgs& A, fdps_ctx* ctx, cudaStream_t s) {
+    constexpr int EPT = CE / CB;
     int per_sm = 0;
-    cudaError_t e;
-    if (precision == FDPS_FP64)
-        e = quad ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_f64<true>, kFBlock, 0)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_f64<false>, kFBlock, 0);
-    else
-        e = quad ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_f32<true, 4>, kCB, 0)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_f32<false, 4>, kCB, 0);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_f32<QUAD, EPT, CB, KMAX>, CB, 0) !=
+            cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    k_force_f32<QUAD, EPT, CB, KMAX><<<per_sm * ctx->sm_count, CB, 0, s>>>(A);
+}
+
+template <bool QUAD, int CE>
+void launch_f32_shape(const ForceArgs& A, fdps_ctx* ctx, cudaStream_t s, int cb, int kmax) {
+    if (cb == 64) {
+        if (kmax == 2)
+            launch_f32<QUAD, CE, 64, 2>(A, ctx, s);
+        else
+            launch_f32<QUAD, CE, 64, 4>(A, ctx, s);
+    } else if (cb == 256) {
+        launch_f32<QUAD, CE, 256, 2>(A, ctx, s);  // 256 x 4 does not fit static shared memory
+    } else {
+        if (kmax == 2)
+            launch_f32<QUAD, CE, 128, 2>(A, ctx, s);
+        else
+            launch_f32<QUAD, CE, 128, 4>(A, ctx, s);
+    }
+}
+
+int force_blocks_f64(fdps_ctx* ctx, int quad) {
+    int per_sm = 0;
+    const cudaError_t e = quad ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_f64<true>, kFBlock, 0)
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_f64<false>, kFBlock, 0);
     if (e != cudaSuccess || per_sm < 1) per_sm = 4;
     return per_sm * ctx->sm_count;
 }
@@ -762,26 +795,29 @@ int compute_forces(fdps_tree* t, fdps_psys* ps, int spj_kind) {
     fdps_ctx* ctx = t->ctx;
     const ForceArgs A = force_args(t, ps);
     const bool quad = spj_kind == FDPS_GRAV_SPJ_QUAD;
-    const int blocks = force_blocks(ctx, t->p.precision, quad);
     cudaStream_t s = ctx->stream;
     if (t->p.precision == FDPS_FP64) {
+        const int blocks = force_blocks_f64(ctx, quad);
         if (quad)
             k_force_f64<true><<<blocks, kFBlock, 0, s>>>(A);
         else
             k_force_f64<false><<<blocks, kFBlock, 0, s>>>(A);
     } else {
-        // tile depth: list entries staged per chunk (0 = default 512)
+        // tile depth: list entries staged per chunk (0 = default 512); block
+        // shape: threads per CTA (0 = 128) and i-particles per thread (0 = 4)
         const bool shallow = t->p.tile_depth == 256;
+        const int cb = t->p.block ? t->p.block : 128;
+        const int kmax = t->p.i_per_thread ? t->p.i_per_thread : 4;
         if (quad) {
             if (shallow)
-                k_force_f32<true, 2><<<blocks, kCB, 0, s>>>(A);
+                launch_f32_shape<true, 256>(A, ctx, s, cb, kmax);
             else
-                k_force_f32<true, 4><<<blocks, kCB, 0, s>>>(A);
+                launch_f32_shape<true, 512>(A, ctx, s, cb, kmax);
         } else {
             if (shallow)
-                k_force_f32<false, 2><<<blocks, kCB, 0, s>>>(A);
+                launch_f32_shape<false, 256>(A, ctx, s, cb, kmax);
             else
-                k_force_f32<false, 4><<<blocks, kCB, 0, s>>>(A);
+                launch_f32_shape<false, 512>(A, ctx, s, cb, kmax);
         }
     }
     FDPS_LAUNCH_CHECK(ctx);

@@ -408,6 +408,40 @@ def test_shallow_tile_depth_matches_oracle(G, ctx, quad):
         ps.close()
 
 
+BLOCK_SHAPES = [(64, 2), (64, 4), (128, 2), (128, 4), (256, 2)]
+
+
+@pytest.mark.parametrize("block,ipt", BLOCK_SHAPES, ids=[f"{b}x{k}" for b, k in BLOCK_SHAPES])
+@pytest.mark.parametrize("quad", [False, True])
+def test_every_block_shape_matches_oracle(G, ctx, block, ipt, quad):
+    """Every block shape the autotuner may pick (threads per CTA, cap on
+    i-particles per thread), at both tile depths: the same forces as the
+    oracle on identical lists.  n_grp 1024 makes groups larger than one
+    round of KMAX x CB i-slots for the small shapes."""
+    n = 24001
+    pos, vel, mass, eps = ics.make("hernquist", n, ics.SEED_BASE + 47, 0.01)
+    for n_grp, tile in ((256, 512), (1024, 256)):
+        ps, tree = run_gpu(G, ctx, pos, vel, mass, eps, 0.5, 16, n_grp, quad, tile_depth=tile)
+        tree.close()
+        tree = G.Tree(ctx, theta=0.5, n_leaf=16, n_grp=n_grp, quad=quad, tile_depth=tile, block=block,
+                      i_per_thread=ipt)
+        try:
+            tree.calc_force_all_and_write_back(ps)
+            _, _, acc, pot = ps.get()
+            acc_r, pot_r, _ = oracle.Tree(pos, mass, eps, 0.5, 16, n_grp, quad).force()
+            assert rms_rel(acc, acc_r) <= RMS_FP32
+            assert rms_rel(pot, pot_r) <= RMS_FP32
+        finally:
+            tree.close()
+            ps.close()
+
+
+def test_block_shape_rules(G, ctx):
+    for block, ipt in ((32, 4), (256, 4), (128, 3), (512, 2)):
+        with pytest.raises(G.FdpsError):
+            G.Tree(ctx, theta=0.5, n_leaf=8, n_grp=64, block=block, i_per_thread=ipt)
+
+
 def test_autotuner_picks_a_candidate_and_keeps_parity(G, ctx):
     n = 30000
     pos, vel, mass, eps = ics.make("plummer", n, ics.SEED_BASE + 43, 0.01)
@@ -415,9 +449,11 @@ def test_autotuner_picks_a_candidate_and_keeps_parity(G, ctx):
     tree = G.Tree(ctx, theta=0.6, n_leaf=8, n_grp=64, quad=True)
     try:
         ps.set(pos, vel, mass, eps)
-        best, ms = tree.autotune(ps, n_leaf=(4, 8), n_grp=(2, 32, 128), tile_depth=(256, 512))
+        best, ms = tree.autotune(ps, n_leaf=(4, 8), n_grp=(2, 32, 128), tile_depth=(256, 512),
+                                 block=(64, 128, 256), i_per_thread=(2, 4))
         assert best["n_leaf"] in (4, 8) and best["n_grp"] in (32, 128)  # n_grp 2 < n_leaf: skipped
         assert best["tile_depth"] in (256, 512) and best["theta"] == 0.6 and ms > 0
+        assert (best["block"], best["i_per_thread"]) in BLOCK_SHAPES
         _, _, acc, pot = ps.get()
         acc_r, _, _ = oracle.Tree(pos, mass, eps, 0.6, best["n_leaf"], best["n_grp"], True).force()
         assert rms_rel(acc, acc_r) <= RMS_FP32
