@@ -187,7 +187,11 @@ __global__ void k_reset_counters(DevState* st, int what) {
         st->overflow &= ~(kOvfPool | kOvfChunk | kOvfFrontier);
     }
     if (what & 2) st->force_counter = 0;
-    if (what & 4) st->overflow &= ~(kOvfNodes | kOvfGroups);
+    if (what & 4) {  // tree build
+        st->overflow &= ~(kOvfNodes | kOvfGroups);
+        st->mom_counter = 0;
+        st->grp_done = 0;
+    }
 }
 
 void record(fdps_tree* t, int k) {
@@ -220,11 +224,9 @@ int launch_force_pipeline(fdps_tree* t, fdps_psys* ps, int k_spj) {
     if ((rc = build_tree(t, ps))) return rc;
     if ((rc = compute_moments(t, ps))) return rc;
     if ((rc = select_groups(t, ps))) return rc;
-    k_reset_counters<<<1, 32, 0, s>>>(t->st, 1);
-    FDPS_LAUNCH_CHECK(ctx);
+    // the walk's and the force kernel's counters are still zero from the
+    // state clear above (nothing between touches them): no reset launches
     if ((rc = launch_walk(t, ps->d_sys, (int)(t->n_walk_warps / walk_warps_per_block())))) return rc;
-    k_reset_counters<<<1, 32, 0, s>>>(t->st, 2);
-    FDPS_LAUNCH_CHECK(ctx);
     return compute_forces(t, ps, k_spj);
 }
 
@@ -408,6 +410,7 @@ int fdps_psys_create(fdps_ctx* ctx, int64_t n, fdps_psys** out) {
     if (!ps) return FDPS_ENOMEM;
     ps->ctx = ctx;
     ps->n = n;
+    ps->max_sys_n = n;
     bool ok = true;
     for (int b = 0; b < 2; ++b)
         ok = ok && dev_alloc(&ps->x[b], n) == cudaSuccess && dev_alloc(&ps->y[b], n) == cudaSuccess &&
@@ -450,6 +453,7 @@ int fdps_psys_destroy(fdps_psys* ps) {
     dev_free(ps->d_red);
     dev_free(ps->stage);
     dev_free(ps->d_off);
+    dev_free(ps->d_order);
     dev_free(ps->d_sys);
     dev_free(ps->d_sys_red);
     delete ps;
@@ -889,8 +893,7 @@ int fdps_step(fdps_tree* t, fdps_psys* ps, double dt) {
     if (!ps->has_forces) return set_error(ps->ctx, FDPS_ESTATE, "no force calculation yet");
     cudaSetDevice(ps->ctx->device);
     int rc;
-    if ((rc = launch_kick(ps, 0.5 * dt))) return rc;
-    if ((rc = launch_drift(ps, dt))) return rc;
+    if ((rc = launch_kick_drift(ps, 0.5 * dt, dt))) return rc;
     const int k_spj = t->p.moment == FDPS_QUADRUPOLE ? FDPS_GRAV_SPJ_QUAD : FDPS_GRAV_SPJ_MONO;
     if ((rc = run_force(t, ps, k_spj))) return rc;
     return launch_kick(ps, 0.5 * dt);
@@ -1206,22 +1209,36 @@ int fdps_psys_set_systems(fdps_psys* ps, int32_t n_sys, const int64_t* offsets) 
             return set_error(ctx, FDPS_EINVAL, "system %d is empty or offsets decrease", (int)k);
     cudaSetDevice(ctx->device);
     dev_free(ps->d_off);
+    dev_free(ps->d_order);
     dev_free(ps->d_sys);
     dev_free(ps->d_sys_red);
     ps->n_sys = 1;
+    ps->max_sys_n = ps->n;
     ps->has_data = false;
     ps->has_forces = false;
     if (n_sys == 1) return FDPS_OK;
     if (dev_alloc(&ps->d_off, n_sys + 1) != cudaSuccess || dev_alloc(&ps->d_sys, ps->n) != cudaSuccess ||
-        dev_alloc(&ps->d_sys_red, 2 * (int64_t)n_sys) != cudaSuccess) {
+        dev_alloc(&ps->d_sys_red, 2 * (int64_t)n_sys) != cudaSuccess ||
+        dev_alloc(&ps->d_order, n_sys) != cudaSuccess) {
         cudaGetLastError();
         dev_free(ps->d_off);
+        dev_free(ps->d_order);
         dev_free(ps->d_sys);
         dev_free(ps->d_sys_red);
         return set_error(ctx, FDPS_ENOMEM, "device allocation for %d systems failed", (int)n_sys);
     }
     ps->n_sys = n_sys;
+    ps->max_sys_n = 0;
+    for (int32_t k = 0; k < n_sys; ++k) ps->max_sys_n = std::max<int64_t>(ps->max_sys_n, offsets[k + 1] - offsets[k]);
+    // per-system work (the moments) is handed out largest system first
+    std::vector<int32_t> order(n_sys);
+    for (int32_t k = 0; k < n_sys; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        return offsets[a + 1] - offsets[a] > offsets[b + 1] - offsets[b];
+    });
     FDPS_CUDA_TRY(ctx, cudaMemcpyAsync(ps->d_off, offsets, sizeof(int64_t) * (n_sys + 1),
+                                       cudaMemcpyHostToDevice, ctx->stream));
+    FDPS_CUDA_TRY(ctx, cudaMemcpyAsync(ps->d_order, order.data(), sizeof(int32_t) * n_sys,
                                        cudaMemcpyHostToDevice, ctx->stream));
     int rc = launch_sys_index(ps);
     if (rc) return rc;
@@ -1267,8 +1284,7 @@ int fdps_run(fdps_tree* t, fdps_psys* ps, double dt, int64_t n_steps) {
             FDPS_CUDA_TRY(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
             ctx->capturing = true;
             const int64_t l0 = ctx->launches;
-            rc = launch_kick(ps, 0.5 * dt);
-            if (!rc) rc = launch_drift(ps, dt);
+            rc = launch_kick_drift(ps, 0.5 * dt, dt);
             if (!rc) rc = launch_force_pipeline(t, ps, k_spj);
             if (!rc) rc = launch_kick_guarded(ps, 0.5 * dt, &t->st->overflow, ovf_mask);
             ctx->capturing = false;

@@ -21,6 +21,8 @@
 // i-groups (Barnes 1990; Sect. 5.5): the maximal nodes with <= n_grp
 // particles, and leaves with more (possible only at level 21), in order of
 // their first particle.
+#include <algorithm>
+
 #include "fdps_internal.cuh"
 
 namespace fdps {
@@ -107,17 +109,30 @@ __device__ __forceinline__ bool meta_leaf(uint32_t m) { return (m >> 16) & 1u; }
 // Level 0: one root per system (node k = root of system k, owning
 // positions off[k] .. off[k+1]; a single root over all n if off is null).
 // The other levels' nodes come from the particle-parallel kernels below.
-__global__ void k_roots(int n_roots, const int64_t* __restrict__ off, int64_t n, int n_leaf,
-                        uint32_t* nd_first, uint32_t* nd_count, uint32_t* nd_child, uint32_t* nd_meta,
-                        uint32_t* nd_parent, uint64_t* nd_qlo) {
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_roots; k += gridDim.x * blockDim.x) {
-        const int64_t a = off ? off[k] : 0, b = off ? off[k + 1] : n;
-        nd_first[k] = (uint32_t)a;
-        nd_count[k] = (uint32_t)(b - a);
-        nd_child[k] = 0xFFFFFFFFu;
-        nd_meta[k] = (b - a <= n_leaf ? 1u : 0u) << 16;
-        nd_parent[k] = 0xFFFFFFFFu;
-        nd_qlo[k] = 0;
+struct RootArgs {
+    int n_roots;
+    const int64_t* off;
+    int64_t n;
+    int n_leaf;
+    uint32_t* nd_first;
+    uint32_t* nd_count;
+    uint32_t* nd_child;
+    uint32_t* nd_meta;
+    uint32_t* nd_parent;
+    uint64_t* nd_qlo;
+};
+
+// (done by the blocks of the count pass, grid-strided)
+__device__ __forceinline__ void write_roots(const RootArgs& R) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < R.n_roots;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = R.off ? R.off[k] : 0, b = R.off ? R.off[k + 1] : R.n;
+        R.nd_first[k] = (uint32_t)a;
+        R.nd_count[k] = (uint32_t)(b - a);
+        R.nd_child[k] = 0xFFFFFFFFu;
+        R.nd_meta[k] = (b - a <= R.n_leaf ? 1u : 0u) << 16;
+        R.nd_parent[k] = 0xFFFFFFFFu;
+        R.nd_qlo[k] = 0;
     }
 }
 
@@ -177,7 +192,8 @@ __device__ __forceinline__ bool cell_fits(unsigned long long M, int c, int n_lea
 __global__ void __launch_bounds__(kBT) k_tree_count(int64_t n, int n_leaf, const uint64_t* __restrict__ keys,
                                                     const uint32_t* __restrict__ sys, uint32_t* __restrict__ pk,
                                                     uint32_t* __restrict__ wcount, uint32_t* __restrict__ tcount,
-                                                    int64_t nw, int64_t ntiles) {
+                                                    int64_t nw, int64_t ntiles, RootArgs R) {
+    write_roots(R);  // level 0 (no other work of this pass depends on it)
     __shared__ uint8_t sD[kBTile + 2 * kHalo];
     __shared__ unsigned long long s_m[kBWarps][kMaxLevel + 1];
     __shared__ uint32_t s_wc[kMaxLevel][kBWarps];
@@ -563,31 +579,98 @@ __device__ __forceinline__ void node_moments(const MomArgs& A, int64_t i) {
     }
 }
 
+// Systems of an ensemble with at most this many particles get their whole
+// subtree from one CTA (k_moments_systems); larger ones, and a single
+// system, go through the leaf pass and one pass per level.
+constexpr int64_t kSysMomMax = int64_t(1) << 17;
+
+// Does the level-by-level pass skip node i (its system is done by
+// k_moments_systems)?
+__device__ __forceinline__ bool small_system_node(const MomArgs& A, const int64_t* off, int64_t i) {
+    if (!off) return false;
+    const uint32_t s = A.sys[A.nd_first[i]];
+    return off[s + 1] - off[s] <= kSysMomMax;
+}
+
 // Leaves (of every level) in one launch, then the internal nodes level by
 // level from the deepest up: each internal node finds its children complete.
 template <bool QUAD, bool Q64>
-__global__ void __launch_bounds__(256) k_moments_leaves(MomArgs A) {
+__global__ void __launch_bounds__(256) k_moments_leaves(MomArgs A, const int64_t* off) {
     const int64_t nn = A.st->n_nodes;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn;
          i += (int64_t)gridDim.x * blockDim.x)
-        if (meta_leaf(A.nd_meta[i])) node_moments<QUAD, Q64>(A, i);
+        if (meta_leaf(A.nd_meta[i]) && !small_system_node(A, off, i)) node_moments<QUAD, Q64>(A, i);
 }
 
 template <bool QUAD, bool Q64>
-__global__ void __launch_bounds__(256) k_moments_internal(MomArgs A, int l) {
+__global__ void __launch_bounds__(256) k_moments_internal(MomArgs A, const int64_t* off, int l) {
     const int64_t a = A.st->lvl_start[l], b = A.st->lvl_start[l + 1];
     for (int64_t i = a + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < b;
          i += (int64_t)gridDim.x * blockDim.x)
-        if (!meta_leaf(A.nd_meta[i])) node_moments<QUAD, Q64>(A, i);
+        if (!meta_leaf(A.nd_meta[i]) && !small_system_node(A, off, i)) node_moments<QUAD, Q64>(A, i);
+}
+
+// First node of level range [lo, hi) whose first particle is >= p (the
+// nodes of a level are ordered by their first particle).
+__device__ __forceinline__ int64_t level_lower_bound(const uint32_t* nd_first, int64_t lo, int64_t hi, int64_t p) {
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((int64_t)nd_first[mid] < p)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// One CTA per system of at most kSysMomMax particles (systems taken from a
+// counter, largest first): the system's nodes level by level from the deepest up, with the
+// same per-node code as the level passes, so the sums (and the centres of
+// mass) come out bit for bit the same; one launch instead of 22.
+template <bool QUAD, bool Q64>
+__global__ void __launch_bounds__(256) k_moments_systems(MomArgs A, const int64_t* __restrict__ off,
+                                                       const int32_t* __restrict__ order, int32_t n_sys,
+                                                       uint32_t* counter) {
+    __shared__ int32_t s_k;
+    __shared__ int64_t s_rng[2 * (kMaxLevel + 1)];
+    for (;;) {
+        if (threadIdx.x == 0) s_k = (int32_t)atomicAdd(counter, 1u);
+        __syncthreads();
+        if (s_k >= n_sys) break;
+        const int32_t k = order[s_k];  // largest systems first
+        const int64_t a = off[k], b = off[k + 1];
+        if (b - a <= kSysMomMax) {
+            if (threadIdx.x <= kMaxLevel) {
+                const int l = threadIdx.x;
+                const int64_t lo = A.st->lvl_start[l], hi = A.st->lvl_start[l + 1];
+                s_rng[2 * l] = level_lower_bound(A.nd_first, lo, hi, a);
+                s_rng[2 * l + 1] = level_lower_bound(A.nd_first, lo, hi, b);
+            }
+            __syncthreads();
+            for (int l = kMaxLevel; l >= 0; --l) {
+                for (int64_t i = s_rng[2 * l] + threadIdx.x; i < s_rng[2 * l + 1]; i += blockDim.x)
+                    node_moments<QUAD, Q64>(A, i);
+                __syncthreads();  // this level complete before its parents
+            }
+        }
+        __syncthreads();  // s_k and s_rng are rewritten next round
+    }
 }
 
 template <bool QUAD, bool Q64>
-int launch_moments(fdps_ctx* ctx, const MomArgs& A) {
+int launch_moments(fdps_ctx* ctx, const MomArgs& A, const fdps_psys* ps, DevState* st) {
     const int grid = ctx->sm_count * 8;
-    k_moments_leaves<QUAD, Q64><<<grid, 256, 0, ctx->stream>>>(A);
+    const int64_t* off = ps->n_sys > 1 ? ps->d_off : nullptr;
+    if (off) {
+        const int g = (int)std::min<int64_t>(ps->n_sys, (int64_t)ctx->sm_count * 8);
+        k_moments_systems<QUAD, Q64><<<g, 256, 0, ctx->stream>>>(A, off, ps->d_order, ps->n_sys, &st->mom_counter);
+        FDPS_LAUNCH_CHECK(ctx);
+        if (ps->max_sys_n <= kSysMomMax) return FDPS_OK;
+    }
+    k_moments_leaves<QUAD, Q64><<<grid, 256, 0, ctx->stream>>>(A, off);
     FDPS_LAUNCH_CHECK(ctx);
     for (int l = kMaxLevel - 1; l >= 0; --l) {
-        k_moments_internal<QUAD, Q64><<<grid, 256, 0, ctx->stream>>>(A, l);
+        k_moments_internal<QUAD, Q64><<<grid, 256, 0, ctx->stream>>>(A, off, l);
         FDPS_LAUNCH_CHECK(ctx);
     }
     return FDPS_OK;
@@ -611,8 +694,13 @@ __global__ void __launch_bounds__(256) k_group_mark(const DevState* __restrict__
     }
 }
 
+// Group heads per block; the last block to finish (counted in
+// st->grp_done, zero on entry) scans the per-block counts into offsets and
+// publishes the number of groups.
 __global__ void __launch_bounds__(kB) k_group_count(int64_t n, const uint32_t* __restrict__ head,
-                                                    uint32_t* __restrict__ part) {
+                                                    uint32_t* __restrict__ part, DevState* st,
+                                                    int64_t cap_groups) {
+    __shared__ bool s_last;
     int64_t t0, t1;
     block_tiles(n, &t0, &t1);
     uint32_t c = 0;
@@ -621,16 +709,31 @@ __global__ void __launch_bounds__(kB) k_group_count(int64_t n, const uint32_t* _
         if (i < n && head[i] != 0xFFFFFFFFu) ++c;
     }
     uint32_t tot = block_sum(c);
-    if (threadIdx.x == 0) part[blockIdx.x] = tot;
-}
-
-__global__ void __launch_bounds__(1024) k_group_scan(DevState* st, uint32_t* part, int np,
-                                                     int64_t cap_groups) {
-    uint32_t tot;
-    scan_partials(part, np, &tot);
     if (threadIdx.x == 0) {
-        if ((int64_t)tot > cap_groups) st->overflow |= kOvfGroups;
-        st->n_groups = (int32_t)((int64_t)tot > cap_groups ? cap_groups : tot);
+        part[blockIdx.x] = tot;
+        __threadfence();  // the count is visible before the block counts itself done
+        s_last = atomicAdd(&st->grp_done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int np = (int)gridDim.x;
+    const int per = (np + kB - 1) / kB;
+    const int b = threadIdx.x * per;
+    uint32_t sum = 0;
+    for (int k = 0; k < per; ++k)
+        if (b + k < np) sum += __ldcg(&part[b + k]);
+    uint32_t total;
+    uint32_t off = block_excl(sum, &total);
+    for (int k = 0; k < per; ++k)
+        if (b + k < np) {
+            const uint32_t v = __ldcg(&part[b + k]);
+            part[b + k] = off;
+            off += v;
+        }
+    if (threadIdx.x == 0) {
+        if ((int64_t)total > cap_groups) st->overflow |= kOvfGroups;
+        st->n_groups = (int32_t)((int64_t)total > cap_groups ? cap_groups : total);
     }
 }
 
@@ -762,13 +865,11 @@ int build_tree(fdps_tree* t, fdps_psys* ps) {
     uint32_t* wcount = t->bt_count;                 // [21][nw] per warp
     uint32_t* tcount = wcount + kMaxLevel * nw;     // [21][ntiles] per tile, then scanned
     uint32_t* ltot = tcount + kMaxLevel * ntiles;   // [21]
-    k_roots<<<grid_for(ps->n_sys, 256, 64), 256, 0, s>>>(ps->n_sys, ps->d_off, n, t->p.n_leaf, t->nd_first,
-                                                         t->nd_count, t->nd_child, t->nd_meta, t->nd_parent,
-                                                         t->nd_qlo);
-    FDPS_LAUNCH_CHECK(ctx);
+    const RootArgs R{ps->n_sys, ps->d_off, n, t->p.n_leaf, t->nd_first, t->nd_count,
+                     t->nd_child, t->nd_meta, t->nd_parent, t->nd_qlo};
     // per-position scratch: t->head, rewritten by the group selection
     k_tree_count<<<(unsigned)ntiles, kBT, 0, s>>>(n, t->p.n_leaf, t->keys_sorted, ps->d_sys, t->head, wcount,
-                                                  tcount, nw, ntiles);
+                                                  tcount, nw, ntiles, R);
     FDPS_LAUNCH_CHECK(ctx);
     k_tree_scan<<<kMaxLevel, 1024, 0, s>>>(tcount, ntiles, ltot);
     FDPS_LAUNCH_CHECK(ctx);
@@ -811,9 +912,9 @@ int compute_moments(fdps_tree* t, fdps_psys* ps) {
     A.nd_walk = t->nd_walk;
     A.nd_fq0 = t->nd_fq0;
     A.nd_fq1 = t->nd_fq1;
-    if (t->p.moment != FDPS_QUADRUPOLE) return launch_moments<false, false>(ctx, A);
-    if (t->p.precision == FDPS_FP64) return launch_moments<true, true>(ctx, A);
-    return launch_moments<true, false>(ctx, A);
+    if (t->p.moment != FDPS_QUADRUPOLE) return launch_moments<false, false>(ctx, A, ps, t->st);
+    if (t->p.precision == FDPS_FP64) return launch_moments<true, true>(ctx, A, ps, t->st);
+    return launch_moments<true, false>(ctx, A, ps, t->st);
 }
 
 int select_groups(fdps_tree* t, fdps_psys* ps) {
@@ -826,9 +927,7 @@ int select_groups(fdps_tree* t, fdps_psys* ps) {
     k_group_mark<<<ctx->sm_count * 8, 256, 0, s>>>(t->st, t->p.n_grp, ps->n_sys, t->nd_first, t->nd_count,
                                                    t->nd_meta, t->nd_parent, t->head);
     FDPS_LAUNCH_CHECK(ctx);
-    k_group_count<<<G, kB, 0, s>>>(n, t->head, t->grp_scan);
-    FDPS_LAUNCH_CHECK(ctx);
-    k_group_scan<<<1, 1024, 0, s>>>(t->st, t->grp_scan, G, t->cap_groups);
+    k_group_count<<<G, kB, 0, s>>>(n, t->head, t->grp_scan, t->st, t->cap_groups);
     FDPS_LAUNCH_CHECK(ctx);
     k_group_write<<<G, kB, 0, s>>>(n, t->cap_groups, t->head, t->grp_scan, t->nd_count, t->g_node,
                                    t->g_first, t->g_count);

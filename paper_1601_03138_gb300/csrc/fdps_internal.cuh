@@ -64,7 +64,9 @@ struct DevState {
     uint32_t overflow;
     uint32_t walk_counter;   // dynamic group scheduler of the walk
     uint32_t force_counter;  // dynamic group scheduler of the force kernel
-    uint32_t pad0;
+    uint32_t mom_counter;    // dynamic system scheduler of the per-system moments
+    uint32_t grp_done;       // blocks of the group count finished (the last one scans)
+    uint32_t pad1;
     unsigned long long pool_cursor;  // list pool allocation cursor (entries)
     unsigned long long pool_needed;  // what the walk asked for, incl. overflow
     unsigned long long list_entries;
@@ -132,7 +134,9 @@ struct fdps_psys {
     // independent systems: positions off[k] .. off[k+1] belong to system k;
     // with one system d_off and d_sys stay null
     int32_t n_sys = 1;
+    int64_t max_sys_n = 0;       // particles of the largest system (n with one system)
     int64_t* d_off = nullptr;
+    int32_t* d_order = nullptr;  // systems by decreasing particle count
     uint32_t* d_sys = nullptr;   // system of each position
     double* d_sys_red = nullptr; // per-system energies (2 n_sys)
 };
@@ -303,6 +307,7 @@ int gather_rows_device(fdps_psys* ps, int64_t ns, const int64_t* d_rows, double*
 int launch_kick(fdps_psys* ps, double dt_half);        // integrate.cu
 int launch_kick_guarded(fdps_psys* ps, double dt_half, const uint32_t* flags, uint32_t mask);
 int launch_drift(fdps_psys* ps, double dt);            // integrate.cu
+int launch_kick_drift(fdps_psys* ps, double dt_half, double dt);  // integrate.cu
 int launch_energy(fdps_psys* ps, double* kin, double* pot);  // integrate.cu
 int launch_validate(fdps_psys* ps, uint32_t* bad);     // integrate.cu
 int launch_scatter_in(fdps_psys* ps, const double* pos, const double* vel,

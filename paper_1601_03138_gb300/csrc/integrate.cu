@@ -95,6 +95,24 @@ __global__ void __launch_bounds__(256) k_kick(int64_t n, double h, double* vx, d
     }
 }
 
+// The first half-kick and the drift of a step in one pass (the same two
+// updates per particle, in the same order, as k_kick then k_drift).
+__global__ void __launch_bounds__(256) k_kick_drift(int64_t n, double h, double dt, double* x, double* y,
+                                                    double* z, double* vx, double* vy, double* vz,
+                                                    const double* __restrict__ ax,
+                                                    const double* __restrict__ ay,
+                                                    const double* __restrict__ az) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double ux = vx[i] + h * ax[i], uy = vy[i] + h * ay[i], uz = vz[i] + h * az[i];
+        vx[i] = ux;
+        vy[i] = uy;
+        vz[i] = uz;
+        x[i] += dt * ux;
+        y[i] += dt * uy;
+        z[i] += dt * uz;
+    }
+}
 __global__ void __launch_bounds__(256) k_drift(int64_t n, double dt, double* x, double* y, double* z,
                                                const double* __restrict__ vx,
                                                const double* __restrict__ vy,
@@ -301,6 +319,15 @@ int launch_kick(fdps_psys* ps, double dt_half) {
     return FDPS_OK;
 }
 
+int launch_kick_drift(fdps_psys* ps, double dt_half, double dt) {
+    fdps_ctx* ctx = ps->ctx;
+    const int c = ps->cur;
+    k_kick_drift<<<grid_for(ps->n, 256, ctx->sm_count * 16), 256, 0, ctx->stream>>>(
+        ps->n, dt_half, dt, ps->x[c], ps->y[c], ps->z[c], ps->vx[c], ps->vy[c], ps->vz[c], ps->ax, ps->ay,
+        ps->az);
+    FDPS_LAUNCH_CHECK(ctx);
+    return FDPS_OK;
+}
 int launch_drift(fdps_psys* ps, double dt) {
     fdps_ctx* ctx = ps->ctx;
     const int c = ps->cur;

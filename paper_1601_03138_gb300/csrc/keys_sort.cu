@@ -411,14 +411,17 @@ constexpr int kHistBlocks = 608;
 
 // Morton keys (as k_keys) plus the histograms of all digit passes: hist
 // [pass][256] with passes 0..7 the key bytes and, for several systems,
-// passes 8, 9 the two low bytes of the system id.
+// passes 8, 9 the two low bytes of the system id.  The last block to finish
+// (counted in *done, zero on entry) turns every pass's counts into the
+// exclusive digit bases.
 __global__ void __launch_bounds__(kSortBlock) k_keys_hist(int64_t n, const double* __restrict__ x,
                                                           const double* __restrict__ y,
                                                           const double* __restrict__ z,
                                                           const SysBox* __restrict__ box,
                                                           const uint32_t* __restrict__ sys,
                                                           uint64_t* __restrict__ keys,
-                                                          uint32_t* __restrict__ hist) {
+                                                          uint32_t* __restrict__ hist, uint32_t* done) {
+    __shared__ bool s_last;
     __shared__ uint32_t h[10][kRadix];
     for (int i = threadIdx.x; i < 10 * kRadix; i += kSortBlock) (&h[0][0])[i] = 0;
     __syncthreads();
@@ -443,13 +446,19 @@ __global__ void __launch_bounds__(kSortBlock) k_keys_hist(int64_t n, const doubl
         const uint32_t c = (&h[0][0])[i];
         if (c) atomicAdd(&hist[i], c);
     }
-}
-
-// Exclusive scan of each pass's 256 digit counts: block p scans pass p.
-__global__ void __launch_bounds__(kRadix) k_digit_bases(uint32_t* hist) {
-    uint32_t* row = hist + blockIdx.x * kRadix;
-    const uint32_t v = row[threadIdx.x];
-    row[threadIdx.x] = block_excl_scan(v, nullptr);
+    __threadfence();  // this block's counts are in hist before it counts itself done
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // the last block: exclusive scan of each pass's 256 digit counts
+    static_assert(kSortBlock == kRadix, "one thread per digit");
+    for (int p = 0; p < np; ++p) {
+        uint32_t* row = hist + p * kRadix;
+        const uint32_t v = __ldcg(&row[threadIdx.x]);
+        row[threadIdx.x] = block_excl_scan(v, nullptr);
+    }
 }
 
 // Tile shape of the single-pass kernel and the look-back window: each
@@ -712,10 +721,9 @@ int keys_and_sort(fdps_tree* t, fdps_psys* ps) {
     uint32_t* hist = t->sort_dtot;          // [pass][256] counts, then bases
     uint32_t* tile_ctr = t->sort_dtot + 3072;
     FDPS_CUDA_TRY(ctx, cudaMemsetAsync(t->sort_dtot, 0, sizeof(uint32_t) * 4096, s));
+    uint32_t* hist_done = t->sort_dtot + 4000;  // zeroed with the rest above
     k_keys_hist<<<kHistBlocks, kSortBlock, 0, s>>>(n, ps->x[c], ps->y[c], ps->z[c], t->sys_box, ps->d_sys,
-                                                   t->keys_in, hist);
-    FDPS_LAUNCH_CHECK(ctx);
-    k_digit_bases<<<npass, kRadix, 0, s>>>(hist);
+                                                   t->keys_in, hist, hist_done);
     FDPS_LAUNCH_CHECK(ctx);
     if (t->ev_ok && ctx->profiling && !ctx->capturing) cudaEventRecord(t->ev[1], s);
     const uint64_t* kin = t->keys_in;
