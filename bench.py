@@ -124,13 +124,18 @@ STAGE_BYTES = {
     # and their FP32 copies written
     "ms_moments": (32, 200),
 }
+# The coherent time-step sort: the key pass also writes each key's bucket;
+# the sort is a scatter into the buckets (key and bucket read, key and
+# position written) and the per-bucket sort (the same 12 bytes read and
+# written again).
+STAGE_BYTES_COHERENT = dict(STAGE_BYTES, ms_box_keys=(24 + 24 + 12, 0), ms_sort=(12 + 12 + 12 + 12, 0))
 
 
-def stage_hbm(stages_ms, n, n_nodes, peak_gbs):
+def stage_hbm(stages_ms, n, n_nodes, peak_gbs, coherent=False):
     """Algorithmic GB/s and fraction of the measured HBM copy bandwidth of
-    the HBM-bound stages."""
+    the HBM-bound stages (the byte counts of the sort the call took)."""
     out = {}
-    for k, (bp, bn) in STAGE_BYTES.items():
+    for k, (bp, bn) in (STAGE_BYTES_COHERENT if coherent else STAGE_BYTES).items():
         ms = stages_ms.get(k)
         if not ms:
             continue
@@ -437,7 +442,7 @@ def run_ours(args, rank, world, local_rank):
                 "ops_per_interaction_algorithmic": {"epj": ALG_EPJ, "spj": alg_spj}}
     stages = {k: round(statistics.median([s[k] for s in stage]), 3) for k in stage[0]
               if k.startswith("ms_")}
-    hbm = stage_hbm(stages, n, last["n_nodes"], pk.get("hbm_gbs", 6800.0))
+    hbm = stage_hbm(stages, n, last["n_nodes"], pk.get("hbm_gbs", 6800.0), bool(last.get("sort_coherent")))
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -505,6 +510,7 @@ def run_ours(args, rank, world, local_rank):
                            "replicas": world, "autotuned": tuned},
                 "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk, "fp64_variant": fp64, "stages_ms": stages, "stages_hbm": hbm,
+                "sort_path": "coherent" if last.get("sort_coherent") else "radix",
                 "per_step": {"interactions": inter / args.steps,
                              "interactions_epj": inter_e / args.steps,
                              "interactions_spj": inter_s / args.steps,

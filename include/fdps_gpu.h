@@ -116,8 +116,10 @@ typedef struct {
     int64_t interactions_spj;  /* sum over groups of n_i |SPJ| */
     int64_t fp64_fallbacks;    /* opening tests decided in FP64 */
     int64_t retries;           /* buffer resize-and-retry count */
+    int64_t sort_coherent;     /* 1: the last sort was the coherent time-step
+                                  sort, 0: the radix sort */
     double ms_box_keys;        /* root box + Morton keys */
-    double ms_sort;            /* radix sort */
+    double ms_sort;            /* sort (after the keys) */
     double ms_permute;         /* reorder into key order */
     double ms_build;           /* octree levels */
     double ms_moments;         /* bottom-up moments */

@@ -57,7 +57,7 @@ class fdps_tree_params(C.Structure):
 class fdps_tree_stats(C.Structure):
     _fields_ = [(k, C.c_int64) for k in (
         "n_particles", "n_nodes", "n_groups", "n_levels", "list_entries", "n_epj", "n_spj",
-        "interactions_epj", "interactions_spj", "fp64_fallbacks", "retries")] + [
+        "interactions_epj", "interactions_spj", "fp64_fallbacks", "retries", "sort_coherent")] + [
         (k, C.c_double) for k in (
             "ms_box_keys", "ms_sort", "ms_permute", "ms_build", "ms_moments", "ms_groups",
             "ms_walk", "ms_force", "ms_total")]

@@ -37,6 +37,9 @@ void free_particles(fdps_tree* t) {
     dev_free(t->head);
     dev_free(t->sort_hist);
     dev_free(t->bt_count);
+    dev_free(t->coh_bkt);
+    dev_free(t->coh_cnt);
+    t->coh_ok = false;  // the last sorted keys are gone
     t->cap_n = 0;
     t->cap_tiles = 0;
 }
@@ -50,7 +53,8 @@ int ensure_particles(fdps_tree* t, int64_t n) {
               dev_alloc(&t->vals_b, n) == cudaSuccess && dev_alloc(&t->pf_hi, n) == cudaSuccess &&
               dev_alloc(&t->pf_lo, n) == cudaSuccess && dev_alloc(&t->head, n) == cudaSuccess &&
               dev_alloc(&t->sort_hist, 2 * 256 * tiles) == cudaSuccess &&
-              dev_alloc(&t->bt_count, kMaxLevel * (kBuildWarps + 1) * (tiles + 1) + 32) == cudaSuccess;
+              dev_alloc(&t->bt_count, kMaxLevel * (kBuildWarps + 1) * (tiles + 1) + 32) == cudaSuccess &&
+              dev_alloc(&t->coh_bkt, n) == cudaSuccess && dev_alloc(&t->coh_cnt, 3 * ((n + kCohT - 1) / kCohT + 1) + 8) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_particles(t);
@@ -246,12 +250,17 @@ int run_tree_stages(fdps_tree* t, fdps_psys* ps) {
     t->n = n;
     t->valid = false;
     cudaStream_t s = ctx->stream;
+    // a coherent sort whose bucket did not fit leaves the particles in
+    // their order (the kernels after it copy them as they are): the call
+    // starts over with the radix sort
+    for (int sort_try = 0;; ++sort_try) {
     FDPS_CUDA_TRY(ctx, cudaMemsetAsync(t->st, 0, sizeof(DevState), s));
     record(t, 0);
     if ((rc = keys_and_sort(t, ps))) return rc;
     record(t, 2);
     if ((rc = reorder_particles(t, ps))) return rc;
     record(t, 3);
+    bool redo = false;
     for (int attempt = 0;; ++attempt) {
         if ((rc = build_tree(t, ps))) return rc;
         record(t, 4);
@@ -261,8 +270,17 @@ int run_tree_stages(fdps_tree* t, fdps_psys* ps) {
         record(t, 6);
         if ((rc = read_state(t))) return rc;
         const uint32_t ov = t->h_st.overflow;
-        if (ov & kSortStall)
+        if (ov & kSortStall) {
+            t->coh_ok = false;
             return set_error(ctx, FDPS_ETIMEOUT, "a radix-sort look-back wait exceeded its bound");
+        }
+        if (ov & kSortRedo) {
+            if (sort_try > 0) return set_error(ctx, FDPS_ECUDA, "coherent sort asked for a second redo");
+            t->coh_ok = false;
+            ++t->retries;
+            redo = true;
+            break;
+        }
         if (!(ov & (kOvfNodes | kOvfGroups))) break;
         if (attempt > 8)
             return set_error(ctx, FDPS_EOVERFLOW, "tree build did not fit after %d resizes", attempt);
@@ -273,6 +291,8 @@ int run_tree_stages(fdps_tree* t, fdps_psys* ps) {
             if ((rc = ensure_groups(t, std::min<int64_t>(n, 2 * t->cap_groups)))) return rc;
         k_reset_counters<<<1, 32, 0, s>>>(t->st, 4);
         FDPS_LAUNCH_CHECK(ctx);
+    }
+    if (!redo) break;
     }
     return FDPS_OK;
 }
@@ -361,6 +381,11 @@ int fdps_init(int device, fdps_ctx** out) {
         return FDPS_ECUDA;
     }
     ctx->stream = ctx->own_stream;
+    if (fdps::keys_sort_setup(ctx) != FDPS_OK) {
+        cudaStreamDestroy(ctx->own_stream);
+        delete ctx;
+        return FDPS_ECUDA;
+    }
     *out = ctx;
     return FDPS_OK;
 }
@@ -508,6 +533,7 @@ int fdps_psys_set(fdps_psys* ps, const double* pos3n, const double* vel3n, const
                          (bad & 1) ? " non-finite position" : "", (bad & 2) ? " non-finite velocity" : "",
                          (bad & 4) ? " negative or non-finite mass" : "",
                          (bad & 8) ? " non-positive or non-finite eps" : "");
+    ps->gen++;
     ps->has_data = true;
     return FDPS_OK;
 }
@@ -925,6 +951,7 @@ int fdps_tree_get_stats(const fdps_tree* tc, fdps_tree_stats* out) {
     out->interactions_spj = (int64_t)s.int_spj;
     out->fp64_fallbacks = (int64_t)s.fallbacks;
     out->retries = t->retries;
+    out->sort_coherent = t->sort_coherent ? 1 : 0;
     if (t->ev_ok && t->ctx->profiling) {
         float v[9] = {0};
         for (int k = 0; k < 8; ++k)
@@ -1214,6 +1241,7 @@ int fdps_psys_set_systems(fdps_psys* ps, int32_t n_sys, const int64_t* offsets) 
     dev_free(ps->d_sys_red);
     ps->n_sys = 1;
     ps->max_sys_n = ps->n;
+    ps->gen++;
     ps->has_data = false;
     ps->has_forces = false;
     if (n_sys == 1) return FDPS_OK;
@@ -1272,7 +1300,7 @@ int fdps_run(fdps_tree* t, fdps_psys* ps, double dt, int64_t n_steps) {
     if ((rc = ensure_pool(t, (int64_t)(h.pool_needed * 3 / 2) + 2 * t->n_walk_warps * (int64_t)walk_chunk())))
         return rc;
     if ((rc = ensure_frontier(t, 2 * (int64_t)h.max_frontier + 1024))) return rc;
-    const uint32_t ovf_mask = kOvfNodes | kOvfGroups | kOvfPool | kOvfFrontier | kSortStall;
+    const uint32_t ovf_mask = kOvfNodes | kOvfGroups | kOvfPool | kOvfFrontier | kSortStall | kSortRedo;
     // the particle buffers flip in every force calculation, so a step reads
     // buffer `cur` and leaves buffer 1 - cur: one graph for each parity
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
@@ -1314,9 +1342,11 @@ int fdps_run(fdps_tree* t, fdps_psys* ps, double dt, int64_t n_steps) {
         }
         ps->cur = 1 - par;  // the replayed reorder flipped the buffers
         if (ov & ovf_mask) {
-            // this step's force overflowed: redo it with growing buffers, then
-            // the skipped kick; later steps recapture with the new buffers
+            // this step's force overflowed: redo it with growing buffers (and
+            // the radix sort), then the skipped kick; later steps recapture
+            // with the new buffers
             ++t->retries;
+            t->coh_ok = false;
             for (int q = 0; q < 2; ++q)
                 if (exec[q]) {
                     cudaGraphExecDestroy(exec[q]);

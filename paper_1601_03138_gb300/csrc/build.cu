@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(kBT) k_tree_nodes(
         int64_t s = n_roots;
         // keys left unsorted by a sort that gave up: roots only, so that
         // every later stage stays within its buffers until the retry
-        const bool stalled = st->overflow & kSortStall;
+        const bool stalled = st->overflow & kSortInvalid;
         int cut = stalled ? 1 : kMaxLevel + 1, top = 0;
         s_lvl[0] = 0;
         for (int l = 1; l <= kMaxLevel; ++l) {

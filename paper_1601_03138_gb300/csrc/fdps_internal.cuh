@@ -39,6 +39,7 @@ constexpr int kMaxLeaf = 16;
 constexpr int kMaxGrp = 4096;
 constexpr int kBuildTile = 2048;  // positions per tile of the tree build
 constexpr int kBuildWarps = 8;    // warps per tile of the tree build
+constexpr int kCohT = 1024;       // positions per bucket of the coherent time-step sort
 
 // overflow bits of DevState::overflow
 constexpr uint32_t kOvfNodes = 1u;
@@ -48,9 +49,12 @@ constexpr uint32_t kOvfGroups = 8u;
 constexpr uint32_t kBadInput = 16u;
 constexpr uint32_t kOvfChunk = 32u;
 constexpr uint32_t kSortStall = 64u;  // a radix-sort look-back wait gave up
+constexpr uint32_t kSortRedo = 256u;  // a bucket of the coherent sort overflowed: redo with the radix sort
+constexpr uint32_t kSortInvalid = kSortStall | kSortRedo;  // this call's order is not sorted
 // Any of these leaves the step's lists or particle order invalid: the
 // kernels downstream skip their work (the host redoes the step).
-constexpr uint32_t kStepInvalid = kOvfNodes | kOvfPool | kOvfFrontier | kOvfGroups | kOvfChunk | kSortStall;
+constexpr uint32_t kStepInvalid =
+    kOvfNodes | kOvfPool | kOvfFrontier | kOvfGroups | kOvfChunk | kSortStall | kSortRedo;
 
 // Per-tree device-resident state written by the kernels of one force call.
 struct DevState {
@@ -128,6 +132,7 @@ struct fdps_psys {
     double* pot = nullptr;
     bool has_data = false;
     bool has_forces = false;
+    uint64_t gen = 0;            // incremented whenever the particle data is replaced
     uint32_t* d_flag = nullptr;  // validation flag
     double* d_red = nullptr;     // reduction scratch (energy)
     double* stage = nullptr;     // host-transfer staging (10 n doubles, on first use)
@@ -163,6 +168,15 @@ struct fdps_tree {
     int64_t cap_nd_hmax = 0;
     double* g_hmax = nullptr;
     int64_t cap_g_hmax = 0;
+    // coherent sort: the sorted keys of the last call (keys_b) belong to
+    // psys coh_ps at generation coh_gen, whose particles are in that order
+    bool coh_ok = false;
+    const fdps_psys* coh_ps = nullptr;
+    uint64_t coh_gen = 0;
+    int64_t coh_n = 0;
+    bool sort_coherent = false;    // the last call took the coherent sort
+    uint32_t* coh_bkt = nullptr;   // bucket of every particle
+    uint32_t* coh_cnt = nullptr;   // [nb] counts, [nb + 1] offsets, [nb] cursors, done word
     uint32_t* sort_hist = nullptr; // 2 x [tiles][256]: look-back words of the sort passes
     uint32_t* sort_dtot = nullptr; // [4096]: digit totals / bases of every pass, tile counters
     int64_t cap_tiles = 0;
@@ -285,6 +299,7 @@ inline int grid_for(int64_t n, int block, int max_blocks) {
 int run_tree(fdps_tree* t, fdps_psys* ps);
 int read_device_state(fdps_tree* t);
 int keys_and_sort(fdps_tree* t, fdps_psys* ps);        // keys_sort.cu
+int keys_sort_setup(fdps_ctx* ctx);                    // keys_sort.cu: once per context
 int launch_sys_index(fdps_psys* ps);                   // integrate.cu
 int launch_energy_systems(fdps_psys* ps, double* kin, double* pot);  // integrate.cu
 int reorder_particles(fdps_tree* t, fdps_psys* ps);    // keys_sort.cu

@@ -194,6 +194,15 @@ __device__ __forceinline__ int owner_chunk(const uint32_t* scan, uint32_t item) 
     return lo;
 }
 
+// hi + lo += v with an exact FP32 two-sum (Knuth): hi takes the rounded
+// sum, lo the rounding error.
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
+    const float s = hi + v;
+    const float bb = s - hi;
+    lo += (hi - (s - bb)) + (v - bb);
+    hi = s;
+}
+
 // Kahan running sums of one thread in shared memory: sum of (q, c) at
 // s_k[((q * 4 + c) * 2) * CB + t], its compensation CB further on.
 template <int CB>
@@ -495,31 +504,41 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
         }
         __syncthreads();  // chunk buffers are rewritten next
     }
-    // ---- combine slices (FP64) and write back; s_red overlays the
-    // superparticle buffer, which is idle until the next chunk
+    // ---- combine slices and write back; s_red overlays the superparticle
+    // buffer, which is idle until the next chunk.  A slice's Kahan pair
+    // (s, c) is the double-float s + (-c); the slices are added with exact
+    // two-sums in FP32 and each component is turned into FP64 once (FP64 is
+    // a narrow pipe on this part).  The potential's self term is removed
+    // with the value the list's own entry contributed, m_i rsqrt(eps_i^2)
+    // in FP32, so that the two cancel.
+    float2* s_red2 = reinterpret_cast<float2*>(s_red);
     const int rows = P * K;  // i-slots of this round; nsl * rows <= kRed
 #pragma unroll
     for (int q = 0; q < K; ++q)
         if (on)
 #pragma unroll
             for (int c = 0; c < 4; ++c)
-                s_red[c * kRed + sl * rows + ip + q * P] =
-                    iv[q] ? (double)s_k[((q * 4 + c) * 2) * CB + t] -
-                                (double)s_k[((q * 4 + c) * 2 + 1) * CB + t]
-                          : 0.0;
+                s_red2[c * kRed + sl * rows + ip + q * P] =
+                    iv[q] ? make_float2(s_k[((q * 4 + c) * 2) * CB + t], -s_k[((q * 4 + c) * 2 + 1) * CB + t])
+                          : make_float2(0.0f, 0.0f);
     __syncthreads();
     for (int r = t; r < rows; r += CB) {
         const uint32_t i = ib + (uint32_t)r;
         if (i >= ni) continue;
-        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        float hi[4] = {0.0f, 0.0f, 0.0f, 0.0f}, lo[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         for (int s2 = 0; s2 < nsl; ++s2)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) v[c] += s_red[c * kRed + s2 * rows + r];
+            for (int c = 0; c < 4; ++c) {
+                const float2 v = s_red2[c * kRed + s2 * rows + r];
+                two_sum_acc(hi[c], lo[c], v.x);
+                lo[c] += v.y;
+            }
         const uint32_t p = gf + i;
-        A.ax[p] = v[0];
-        A.ay[p] = v[1];
-        A.az[p] = v[2];
-        A.pot[p] = v[3] + A.pm[p] / A.peps[p];
+        two_sum_acc(hi[3], lo[3], A.pf_hi[p].w * rsqrtf(A.pf_lo[p].w));
+        A.ax[p] = (double)hi[0] + (double)lo[0];
+        A.ay[p] = (double)hi[1] + (double)lo[1];
+        A.az[p] = (double)hi[2] + (double)lo[2];
+        A.pot[p] = (double)hi[3] + (double)lo[3];
     }
     __syncthreads();
 }

@@ -37,20 +37,47 @@ __device__ __forceinline__ double unord64(unsigned long long o) {
     return __longlong_as_double((long long)u);
 }
 
-__global__ void __launch_bounds__(256) k_box_partial(int64_t n, const double* __restrict__ x,
+constexpr int kBoxBlock = 512;  // threads per block of the root-box reduction
+
+__global__ void __launch_bounds__(kBoxBlock, 4) k_box_partial(int64_t n, const double* __restrict__ x,
                                                      const double* __restrict__ y,
                                                      const double* __restrict__ z,
                                                      BoxPartial* __restrict__ part) {
     unsigned long long lo[3] = {~0ull, ~0ull, ~0ull};
     unsigned long long hi[3] = {0ull, 0ull, 0ull};
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        unsigned long long v[3] = {ord64(x[i]), ord64(y[i]), ord64(z[i])};
+    auto take = [&](double vx, double vy, double vz) {
+        const unsigned long long o[3] = {ord64(vx), ord64(vy), ord64(vz)};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            lo[a] = v[a] < lo[a] ? v[a] : lo[a];
-            hi[a] = v[a] > hi[a] ? v[a] : hi[a];
+            lo[a] = o[a] < lo[a] ? o[a] : lo[a];
+            hi[a] = o[a] > hi[a] ? o[a] : hi[a];
         }
+    };
+    const int64_t G = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if ((((uintptr_t)x | (uintptr_t)y | (uintptr_t)z) & 15) == 0) {
+        // 16-byte loads, two pairs of particles in flight per thread
+        const double2* x2 = reinterpret_cast<const double2*>(x);
+        const double2* y2 = reinterpret_cast<const double2*>(y);
+        const double2* z2 = reinterpret_cast<const double2*>(z);
+        const int64_t n2 = n >> 1;
+        int64_t p = t0;
+        for (; p + G < n2; p += 2 * G) {
+            const double2 a0 = x2[p], b0 = y2[p], c0 = z2[p];
+            const double2 a1 = x2[p + G], b1 = y2[p + G], c1 = z2[p + G];
+            take(a0.x, b0.x, c0.x);
+            take(a0.y, b0.y, c0.y);
+            take(a1.x, b1.x, c1.x);
+            take(a1.y, b1.y, c1.y);
+        }
+        for (; p < n2; p += G) {
+            const double2 a0 = x2[p], b0 = y2[p], c0 = z2[p];
+            take(a0.x, b0.x, c0.x);
+            take(a0.y, b0.y, c0.y);
+        }
+        if ((n & 1) && t0 == 0) take(x[n - 1], y[n - 1], z[n - 1]);
+    } else {
+        for (int64_t i = t0; i < n; i += G) take(x[i], y[i], z[i]);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -62,7 +89,7 @@ __global__ void __launch_bounds__(256) k_box_partial(int64_t n, const double* __
             hi[a] = h > hi[a] ? h : hi[a];
         }
     }
-    __shared__ unsigned long long s_lo[8][3], s_hi[8][3];
+    __shared__ unsigned long long s_lo[kBoxBlock / 32][3], s_hi[kBoxBlock / 32][3];
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0)
         for (int a = 0; a < 3; ++a) {
@@ -461,6 +488,342 @@ __global__ void __launch_bounds__(kSortBlock) k_keys_hist(int64_t n, const doubl
     }
 }
 
+// ------------------------------------------------ coherent time-step sort
+//
+// In time stepping the particles enter each sort in the previous call's key
+// order and move little in one step.  The previous call's sorted keys at
+// every kCohT-th position are then splitters that put almost every particle
+// in the bucket of its own position: bucket b holds the keys in
+// [prev[b kCohT], prev[(b + 1) kCohT]) (bucket 0 from 0, the last bucket
+// to the end).  Three passes give the stable permutation of the radix sort:
+// keys, buckets and bucket counts (the last block scans the counts into
+// offsets and checks that every bucket fits one CTA), a scatter into the
+// buckets, and a merge sort of each bucket in shared memory by (key,
+// position).  A bucket above kCohCap keys
+// sets kSortRedo: the kernels after the sort treat the call's order as
+// unsorted and the host redoes the call with the radix sort.
+
+constexpr int kCohCap = 2048; // largest bucket one CTA sorts
+constexpr int kCohBlock = 256;
+constexpr int kCohWarps = kCohBlock / 32;
+constexpr int kCohNear = 2;   // buckets t - 2 .. t + 2 counted in shared memory
+static_assert(kCohT % kCohBlock == 0, "whole rounds per tile");
+
+// Splitter b (b >= 1) is prev[b kCohT]; the bucket of key k is the largest b
+// with splitter(b) <= k (splitter(0) = 0), starting from position tile t.
+__device__ __forceinline__ uint32_t coh_bucket(uint64_t k, uint32_t t, uint32_t nb,
+                                               const uint64_t* __restrict__ prev) {
+    const uint64_t lo = t == 0 ? 0ull : prev[(int64_t)t * kCohT];
+    const bool below_hi = t + 1 >= nb || k < prev[(int64_t)(t + 1) * kCohT];
+    if (k >= lo && below_hi) return t;
+    uint32_t a, z;  // the answer lies in [a, z); splitter(a) <= k
+    if (k < lo) {
+        a = 0;
+        z = t;
+    } else {
+        a = t + 1;
+        z = nb;
+    }
+    while (z - a > 1) {
+        const uint32_t mid = (a + z) >> 1;
+        if (prev[(int64_t)mid * kCohT] <= k)
+            a = mid;
+        else
+            z = mid;
+    }
+    return a;
+}
+
+// Pass 1 (one block per tile of kCohT positions): Morton keys as k_keys,
+// the bucket of every key, bucket counts; the last block turns the counts
+// into offsets and cursors and flags a bucket above kCohCap.
+__global__ void __launch_bounds__(kCohBlock) k_coh_keys(int64_t n, const double* __restrict__ x,
+                                                        const double* __restrict__ y,
+                                                        const double* __restrict__ z,
+                                                        const SysBox* __restrict__ box,
+                                                        const uint64_t* __restrict__ prev, uint32_t nb,
+                                                        uint64_t* __restrict__ keys, uint32_t* __restrict__ bkt,
+                                                        uint32_t* cnt, uint32_t* off, uint32_t* cur,
+                                                        uint32_t* done, uint32_t* err) {
+    __shared__ uint32_t s_near[2 * kCohNear + 1];
+    __shared__ uint32_t s_max[kCohWarps];
+    __shared__ bool s_last;
+    const uint32_t t = blockIdx.x;
+    if (threadIdx.x < 2 * kCohNear + 1) s_near[threadIdx.x] = 0;
+    __syncthreads();
+    const SysBox& b = box[0];
+    const int lane = threadIdx.x & 31;
+    for (int r = 0; r < kCohT / kCohBlock; ++r) {
+        const int64_t i = (int64_t)t * kCohT + r * kCohBlock + threadIdx.x;
+        int d = 0x7FFFFFFF;  // no particle
+        if (i < n) {
+            const uint32_t qx = quantise(x[i], b.lo[0], b.s), qy = quantise(y[i], b.lo[1], b.s),
+                           qz = quantise(z[i], b.lo[2], b.s);
+            const uint64_t k = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+            keys[i] = k;
+            const uint32_t bk = coh_bucket(k, t, nb, prev);
+            bkt[i] = bk;
+            d = (int)bk - (int)t;
+            if (d < -kCohNear || d > kCohNear) atomicAdd(&cnt[bk], 1u);
+        }
+        // one shared atomic per warp and nearby bucket
+#pragma unroll
+        for (int v = -kCohNear; v <= kCohNear; ++v) {
+            const uint32_t mk = __ballot_sync(0xFFFFFFFFu, d == v);
+            if (mk && lane == __ffs(mk) - 1) atomicAdd(&s_near[v + kCohNear], (uint32_t)__popc(mk));
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * kCohNear + 1) {
+        const int bk = (int)t + (int)threadIdx.x - kCohNear;
+        const uint32_t c = s_near[threadIdx.x];
+        if (c && bk >= 0 && bk < (int)nb) atomicAdd(&cnt[bk], c);
+    }
+    __threadfence();  // this block's counts land before it counts itself done
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // exclusive scan of the counts in rounds of 4 kCohBlock consecutive
+    // buckets (4 per thread), the next round's counts loaded ahead
+    constexpr int kRound = 4 * kCohBlock;
+    uint32_t carry = 0, mx = 0, c[4], cn[4];
+    auto load4 = [&](int r0, uint32_t* v) {
+        const int j = r0 + 4 * (int)threadIdx.x;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = j + q < (int)nb ? __ldcg(&cnt[j + q]) : 0u;
+    };
+    load4(0, c);
+    for (int r0 = 0; r0 < (int)nb; r0 += kRound) {
+        load4(r0 + kRound, cn);
+        uint32_t tot;
+        uint32_t o = carry + block_excl_scan(c[0] + c[1] + c[2] + c[3], &tot);
+        const int j = r0 + 4 * (int)threadIdx.x;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (j + q < (int)nb) {
+                off[j + q] = o;
+                cur[j + q] = o;
+            }
+            o += c[q];
+            mx = c[q] > mx ? c[q] : mx;
+            c[q] = cn[q];
+        }
+        carry += tot;
+    }
+    mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        off[nb] = carry;
+        uint32_t m = 0;
+        for (int w = 0; w < kCohWarps; ++w) m = s_max[w] > m ? s_max[w] : m;
+        if (m > (uint32_t)kCohCap) atomicOr(err, kSortRedo);
+    }
+}
+
+// Pass 2: every (key, position) into its bucket; one atomic per block and
+// nearby bucket reserves the block's slots, far movers take one each.  The
+// order inside a bucket is arbitrary (pass 3 sorts by position too).
+__global__ void __launch_bounds__(kCohBlock) k_coh_scatter(int64_t n, const uint64_t* __restrict__ keys,
+                                                           const uint32_t* __restrict__ bkt, uint32_t nb,
+                                                           uint32_t* cur, uint64_t* __restrict__ k2,
+                                                           uint32_t* __restrict__ i2, const uint32_t* err) {
+    constexpr int R = kCohT / kCohBlock;
+    __shared__ uint32_t s_cnt[2 * kCohNear + 1], s_base[2 * kCohNear + 1];
+    if (*err & kSortRedo) return;
+    const uint32_t t = blockIdx.x;
+    if (threadIdx.x < 2 * kCohNear + 1) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    uint64_t kk[R];
+    uint32_t bb[R], rank[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int64_t i = (int64_t)t * kCohT + r * kCohBlock + threadIdx.x;
+        bb[r] = 0xFFFFFFFFu;
+        rank[r] = 0xFFFFFFFFu;
+        kk[r] = 0;
+        if (i < n) {
+            kk[r] = keys[i];
+            bb[r] = bkt[i];
+        }
+        // ranks among this block's pairs for the nearby buckets: one shared
+        // atomic per warp and bucket, lanes ranked by the ballot
+        const int d = bb[r] == 0xFFFFFFFFu ? 0x7FFFFFFF : (int)bb[r] - (int)t;
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int v = -kCohNear; v <= kCohNear; ++v) {
+            const uint32_t mk = __ballot_sync(0xFFFFFFFFu, d == v);
+            if (mk) {
+                const int lead = __ffs(mk) - 1;
+                uint32_t base = 0;
+                if (lane == lead) base = atomicAdd(&s_cnt[v + kCohNear], (uint32_t)__popc(mk));
+                base = __shfl_sync(0xFFFFFFFFu, base, lead);
+                if (d == v) rank[r] = base + (uint32_t)__popc(mk & ((1u << lane) - 1u));
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * kCohNear + 1) {
+        const int bk = (int)t + (int)threadIdx.x - kCohNear;
+        const uint32_t c = s_cnt[threadIdx.x];
+        s_base[threadIdx.x] = (c && bk >= 0 && bk < (int)nb) ? atomicAdd(&cur[bk], c) : 0u;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (bb[r] == 0xFFFFFFFFu) continue;
+        const int64_t i = (int64_t)t * kCohT + r * kCohBlock + threadIdx.x;
+        const uint32_t pos = rank[r] != 0xFFFFFFFFu ? s_base[(int)bb[r] - (int)t + kCohNear] + rank[r]
+                                                    : atomicAdd(&cur[bb[r]], 1u);
+        k2[pos] = kk[r];
+        i2[pos] = (uint32_t)i;
+    }
+}
+
+// Shared memory of the bucket sort: two key and two position buffers,
+// element j at j + j / 16 (keys) and j + j / 32 (positions), so that the
+// threads of a warp reading or writing their EPT consecutive elements fall
+// in different banks.
+constexpr int kCohKP = kCohCap + kCohCap / 16;
+constexpr int kCohIP = kCohCap + kCohCap / 32;
+struct CohShared {
+    unsigned long long k[2][kCohKP];
+    uint32_t i[2][kCohIP];
+};
+__device__ __forceinline__ int coh_kp(int j) { return j + (j >> 4); }
+__device__ __forceinline__ int coh_ip(int j) { return j + (j >> 5); }
+
+// (key, position) order: all pairs of a call differ, so any correct sort of
+// them is the stable sort by key.  The padding pair (all ones) orders last.
+__device__ __forceinline__ bool coh_less(unsigned long long ka, uint32_t ia, unsigned long long kb, uint32_t ib) {
+    return ka < kb || (ka == kb && ia < ib);
+}
+
+// Merge sort of kCohBlock * EPT pairs in buffer 0: each thread sorts its
+// EPT consecutive pairs in registers, then every round merges runs of
+// length L pairwise (L = EPT, 2 EPT, ...), each thread writing EPT
+// consecutive outputs from the split of its output diagonal found by
+// binary search (merge path).  Returns the buffer holding the result.
+template <int EPT>
+__device__ __noinline__ int coh_merge_sort(CohShared& sm) {
+    constexpr int np = kCohBlock * EPT;
+    const int o = threadIdx.x * EPT;
+    {
+        unsigned long long k[EPT];
+        uint32_t x[EPT];
+#pragma unroll
+        for (int r = 0; r < EPT; ++r) {
+            k[r] = sm.k[0][coh_kp(o + r)];
+            x[r] = sm.i[0][coh_ip(o + r)];
+        }
+        // odd-even transposition sort
+#pragma unroll
+        for (int p = 0; p < EPT; ++p)
+#pragma unroll
+            for (int r = p & 1; r + 1 < EPT; r += 2)
+                if (coh_less(k[r + 1], x[r + 1], k[r], x[r])) {
+                    const unsigned long long tk = k[r];
+                    k[r] = k[r + 1];
+                    k[r + 1] = tk;
+                    const uint32_t tx = x[r];
+                    x[r] = x[r + 1];
+                    x[r + 1] = tx;
+                }
+#pragma unroll
+        for (int r = 0; r < EPT; ++r) {
+            sm.k[0][coh_kp(o + r)] = k[r];
+            sm.i[0][coh_ip(o + r)] = x[r];
+        }
+    }
+    __syncthreads();
+    int src = 0;
+    for (int L = EPT; L < np; L *= 2) {
+        const int a0 = (o / (2 * L)) * (2 * L);  // run A is [a0, a0 + L), run B follows
+        const int b0 = a0 + L;
+        const int d = o - a0;
+        const unsigned long long* K = sm.k[src];
+        const uint32_t* X = sm.i[src];
+        // ia = how many of the first d outputs come from A
+        int lo = d > L ? d - L : 0, hi = d < L ? d : L;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            const int jb = b0 + d - 1 - mid;
+            if (coh_less(K[coh_kp(a0 + mid)], X[coh_ip(a0 + mid)], K[coh_kp(jb)], X[coh_ip(jb)]))
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        int ia = lo, ib = d - lo;
+        unsigned long long ka = K[coh_kp(a0 + min(ia, L - 1))], kb = K[coh_kp(b0 + min(ib, L - 1))];
+        uint32_t xa = X[coh_ip(a0 + min(ia, L - 1))], xb = X[coh_ip(b0 + min(ib, L - 1))];
+        unsigned long long* OK = sm.k[src ^ 1];
+        uint32_t* OX = sm.i[src ^ 1];
+#pragma unroll
+        for (int r = 0; r < EPT; ++r) {
+            const bool ta = ib >= L || (ia < L && coh_less(ka, xa, kb, xb));
+            OK[coh_kp(o + r)] = ta ? ka : kb;
+            OX[coh_ip(o + r)] = ta ? xa : xb;
+            if (ta) {
+                ++ia;
+                const int j = a0 + min(ia, L - 1);
+                ka = K[coh_kp(j)];
+                xa = X[coh_ip(j)];
+            } else {
+                ++ib;
+                const int j = b0 + min(ib, L - 1);
+                kb = K[coh_kp(j)];
+                xb = X[coh_ip(j)];
+            }
+        }
+        __syncthreads();
+        src ^= 1;
+    }
+    return src;
+}
+
+// Pass 3 (one block per bucket): the bucket's m pairs, padded to
+// kCohBlock * EPT with EPT = ceil(m / kCohBlock), sorted by (key, position)
+// in shared memory and written to their final slots.
+__global__ void __launch_bounds__(kCohBlock) k_coh_sort(const uint32_t* __restrict__ off, uint32_t nb,
+                                                        const uint64_t* __restrict__ k2,
+                                                        const uint32_t* __restrict__ i2,
+                                                        uint64_t* __restrict__ keys_out,
+                                                        uint32_t* __restrict__ perm_out, const uint32_t* err) {
+    extern __shared__ __align__(16) unsigned char coh_dsm[];
+    CohShared& sm = *reinterpret_cast<CohShared*>(coh_dsm);
+    if (*err & kSortRedo) return;
+    const uint32_t b = blockIdx.x;
+    const uint32_t a0 = off[b];
+    const int m = (int)(off[b + 1] - a0);
+    if (m > kCohCap || m == 0) return;  // an overflow is flagged by pass 1
+    const int ept = (m + kCohBlock - 1) / kCohBlock;
+    const int np = ept * kCohBlock;
+    for (int j = threadIdx.x; j < np; j += kCohBlock) {
+        const bool v = j < m;
+        sm.k[0][coh_kp(j)] = v ? k2[a0 + j] : ~0ull;
+        sm.i[0][coh_ip(j)] = v ? i2[a0 + j] : 0xFFFFFFFFu;
+    }
+    __syncthreads();
+    static_assert(kCohCap == 8 * kCohBlock, "at most 8 pairs a thread");
+    int src = 0;
+    switch (ept) {
+        case 1: src = coh_merge_sort<1>(sm); break;
+        case 2: src = coh_merge_sort<2>(sm); break;
+        case 3: src = coh_merge_sort<3>(sm); break;
+        case 4: src = coh_merge_sort<4>(sm); break;
+        case 5: src = coh_merge_sort<5>(sm); break;
+        case 6: src = coh_merge_sort<6>(sm); break;
+        case 7: src = coh_merge_sort<7>(sm); break;
+        default: src = coh_merge_sort<8>(sm); break;
+    }
+    for (int j = threadIdx.x; j < m; j += kCohBlock) {
+        keys_out[a0 + j] = sm.k[src][coh_kp(j)];
+        perm_out[a0 + j] = sm.i[src][coh_ip(j)];
+    }
+}
+
 // Tile shape of the single-pass kernel and the look-back window: each
 // look-back step reads the statuses of kLook earlier tiles at once.
 constexpr int kOsBlock = 256;
@@ -673,7 +1036,7 @@ __global__ void __launch_bounds__(256) k_reorder(
     double* __restrict__ vx2, double* __restrict__ vy2, double* __restrict__ vz2,
     double* __restrict__ m2, double* __restrict__ eps2, uint32_t* __restrict__ id2,
     float4* __restrict__ pf_hi, float4* __restrict__ pf_lo) {
-    const bool sorted = !(st->overflow & kSortStall);
+    const bool sorted = !(st->overflow & kSortInvalid);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const SysBox& b = box[sys ? sys[i] : 0];
@@ -700,20 +1063,60 @@ __global__ void __launch_bounds__(256) k_reorder(
 
 }  // namespace
 
+int keys_sort_setup(fdps_ctx* ctx) {
+    if (cudaFuncSetAttribute(k_coh_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CohShared)) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ctx, FDPS_ECUDA, "coherent sort set-up failed");
+    }
+    return FDPS_OK;
+}
+
 int keys_and_sort(fdps_tree* t, fdps_psys* ps) {
     fdps_ctx* ctx = t->ctx;
     cudaStream_t s = ctx->stream;
     const int64_t n = ps->n;
     const int c = ps->cur;
     const int ntiles = (int)((n + kOsTile - 1) / kOsTile);
+    // the particles are in the order of this tree's last sort (same system,
+    // same data, moved by the caller since): the coherent sort
+    const bool coherent = ps->n_sys == 1 && t->coh_ok && t->coh_ps == ps && t->coh_gen == ps->gen &&
+                          t->coh_n == n && n >= 2 * (int64_t)kCohT;
+    t->coh_ok = ps->n_sys == 1;
+    t->coh_ps = ps;
+    t->coh_gen = ps->gen;
+    t->coh_n = n;
+    t->sort_coherent = coherent;
     if (ps->n_sys == 1) {
-        k_box_partial<<<t->box_blocks, 256, 0, s>>>(n, ps->x[c], ps->y[c], ps->z[c], t->box_part);
+        k_box_partial<<<t->box_blocks, kBoxBlock, 0, s>>>(n, ps->x[c], ps->y[c], ps->z[c], t->box_part);
         FDPS_LAUNCH_CHECK(ctx);
         k_box_final<<<1, 32, 0, s>>>(t->box_blocks, t->box_part, t->st, t->sys_box);
         FDPS_LAUNCH_CHECK(ctx);
     } else {
         k_box_seg<<<ps->n_sys, 256, 0, s>>>(ps->d_off, ps->x[c], ps->y[c], ps->z[c], t->sys_box);
         FDPS_LAUNCH_CHECK(ctx);
+    }
+    if (coherent) {
+        const uint32_t nb = (uint32_t)((n + kCohT - 1) / kCohT);
+        uint32_t* cnt = t->coh_cnt;
+        uint32_t* off = cnt + nb;       // nb + 1
+        uint32_t* cur = off + nb + 1;   // nb
+        uint32_t* done = cur + nb;
+        FDPS_CUDA_TRY(ctx, cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (3 * (size_t)nb + 2), s));
+        // the previous sorted keys (keys_b) are the splitters
+        k_coh_keys<<<nb, kCohBlock, 0, s>>>(n, ps->x[c], ps->y[c], ps->z[c], t->sys_box, t->keys_b, nb,
+                                             t->keys_in, t->coh_bkt, cnt, off, cur, done, &t->st->overflow);
+        FDPS_LAUNCH_CHECK(ctx);
+        if (t->ev_ok && ctx->profiling && !ctx->capturing) cudaEventRecord(t->ev[1], s);
+        k_coh_scatter<<<nb, kCohBlock, 0, s>>>(n, t->keys_in, t->coh_bkt, nb, cur, t->keys_a, t->vals_a,
+                                                &t->st->overflow);
+        FDPS_LAUNCH_CHECK(ctx);
+        k_coh_sort<<<nb, kCohBlock, sizeof(CohShared), s>>>(off, nb, t->keys_a, t->vals_a, t->keys_b, t->vals_b,
+                                                             &t->st->overflow);
+        FDPS_LAUNCH_CHECK(ctx);
+        t->keys_sorted = t->keys_b;
+        t->perm = t->vals_b;
+        return FDPS_OK;
     }
     // 8 passes over the key; with several systems 2 more, stable, over the
     // system id, so each system's particles end in its own segment in key order
@@ -895,7 +1298,7 @@ extern "C" int fdps_morton_sort_noalloc(const double* x, const double* y, const 
         cudaGetLastError();
         return FDPS_ECUDA;
     }
-    k_box_partial<<<kNoAllocBoxBlocks, 256, 0, s>>>(n, x, y, z, box);
+    k_box_partial<<<kNoAllocBoxBlocks, kBoxBlock, 0, s>>>(n, x, y, z, box);
     k_box_final<<<1, 32, 0, s>>>(kNoAllocBoxBlocks, box, st, sbox);
     k_keys<<<ntiles, kSortBlock, 0, s>>>(n, x, y, z, sbox, nullptr, keys_in, hist, ntiles);
     const uint64_t* kin = keys_in;
