@@ -114,16 +114,23 @@ struct GroupPlan {
 
 template <int CB, int KMAX>
 __device__ __forceinline__ GroupPlan plan_group(uint32_t ni) {
-    // maximise ni * nsl / (CB * K) over K in {1, 2, 4} (up to KMAX); larger
-    // K on ties
+    // maximise ni * nsl / (CB * K) over K in {1, 2, 3, 4} (up to KMAX);
+    // larger K on ties
     GroupPlan best{1, 1, 1};
     float bu = -1.f;
+    // K = 3 is one packed pair and one scalar lane: it issues as many
+    // instructions per list entry as K = 4 for three quarters of the work,
+    // so it must fill the CTA 6 % better to be taken
+    constexpr float kOdd = 1.06f;
+    const int Ks[4] = {4, 3, 2, 1};
 #pragma unroll
-    for (int K = KMAX; K >= 1; K >>= 1) {
+    for (int c = 0; c < 4; ++c) {
+        const int K = Ks[c];
+        if (K > KMAX) continue;
         const int P = (int)((ni + K - 1) / K);
         if (P > CB) continue;
         const int nsl = CB / P;
-        const float u = (float)ni * nsl / (float)(CB * K);
+        const float u = (float)ni * nsl / (float)(CB * K) / (K == 3 ? kOdd : 1.0f);
         if (u > bu + 1e-6f) {
             bu = u;
             best = GroupPlan{K, P, nsl};
@@ -272,9 +279,9 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
                                                 unsigned long long off, uint32_t len, float4 gch,
                                                 float4 gcl, int P, int nsl, uint32_t ib,
                                                 float4* s_j, SpjBuf<QUAD> sb, uint32_t* s_ef,
-                                                uint32_t* s_es, uint32_t* s_w, double* s_red,
+                                                uint32_t* s_es, uint32_t* s_w,
                                                 float* s_k) {
-    constexpr int KP = K / 2;  // i-pairs (K = 1 takes the scalar path)
+    constexpr int KP = K / 2;  // i-pairs; an odd K takes its last i-particle on the scalar path
     const int t = threadIdx.x;
     const int ip = t % P, sl = t / P;
     const bool on = sl < nsl;
@@ -308,7 +315,6 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
     for (int k = 0; k < 8 * K; ++k) s_k[k * CB + t] = 0.0f;
 
     constexpr int CE = CB * EPT;
-    constexpr int kRed = KMAX * CB;  // slice-reduction slots per component
     for (uint32_t base = 0; base < len; base += CE) {
         // ---- this thread's EPT consecutive entries: type, node data, leaf range
         uint32_t nspj = 0, npart = 0;
@@ -368,9 +374,9 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
                 q0 = sb.s1[k];
                 q1 = sb.s2[k];
             }
-            if (K == 1) {
-                const float rx = xi[0] - a.x, ry = yi[0] - a.y, rz = zi[0] - a.z;
-                const float R2 = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, e2[0])));
+            if (K & 1) {  // the odd i-particle (index K - 1) in scalar FP32
+                const float rx = xi[K - 1] - a.x, ry = yi[K - 1] - a.y, rz = zi[K - 1] - a.z;
+                const float R2 = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, e2[K - 1])));
                 const float Ri = rsqrtf(R2);
                 const float Ri2 = Ri * Ri;
                 if (QUAD) {
@@ -383,19 +389,20 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
                     const float w = rQr * Ri4;                 // r.Q.r / R^4
                     const float hh = fmaf(-2.5f, w, a.w);      // -M - 5/2 w
                     const float hR2 = hh * R2;
-                    sax[0] = fmaf(Ri5, fmaf(hR2, rx, Qrx), sax[0]);
-                    say[0] = fmaf(Ri5, fmaf(hR2, ry, Qry), say[0]);
-                    saz[0] = fmaf(Ri5, fmaf(hR2, rz, Qrz), saz[0]);
-                    spp[0] = fmaf(Ri, fmaf(2.0f, w, hh), spp[0]);  // (-M - w/2) / R
+                    sax[K - 1] = fmaf(Ri5, fmaf(hR2, rx, Qrx), sax[K - 1]);
+                    say[K - 1] = fmaf(Ri5, fmaf(hR2, ry, Qry), say[K - 1]);
+                    saz[K - 1] = fmaf(Ri5, fmaf(hR2, rz, Qrz), saz[K - 1]);
+                    spp[K - 1] = fmaf(Ri, fmaf(2.0f, w, hh), spp[K - 1]);  // (-M - w/2) / R
                 } else {
                     const float Ri3 = Ri * Ri2;
                     const float nMRi3 = a.w * Ri3;
-                    sax[0] = fmaf(nMRi3, rx, sax[0]);
-                    say[0] = fmaf(nMRi3, ry, say[0]);
-                    saz[0] = fmaf(nMRi3, rz, saz[0]);
-                    spp[0] = fmaf(a.w, Ri, spp[0]);
+                    sax[K - 1] = fmaf(nMRi3, rx, sax[K - 1]);
+                    say[K - 1] = fmaf(nMRi3, ry, say[K - 1]);
+                    saz[K - 1] = fmaf(nMRi3, rz, saz[K - 1]);
+                    spp[K - 1] = fmaf(a.w, Ri, spp[K - 1]);
                 }
-            } else {
+            }
+            if (KP > 0) {
                 const f2 jx = f2_bc(a.x), jy = f2_bc(a.y), jz = f2_bc(a.z), nM = f2_bc(a.w);
                 f2 qxx, qyy, qzz, qxy, qxz, qyz;
                 if (QUAD) {
@@ -453,17 +460,18 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
 #pragma unroll 2
             for (int k = kbeg; k < (int)m; k += nsl) {
                 const float4 j = s_j[k];
-                if (K == 1) {
-                    const float dx = j.x - xi[0], dy = j.y - yi[0], dz = j.z - zi[0];
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, e2[0])));
+                if (K & 1) {
+                    const float dx = j.x - xi[K - 1], dy = j.y - yi[K - 1], dz = j.z - zi[K - 1];
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, e2[K - 1])));
                     const float ri = rsqrtf(r2);
                     const float mri = j.w * ri;
                     const float mri3 = mri * (ri * ri);
-                    sax[0] = fmaf(mri3, dx, sax[0]);
-                    say[0] = fmaf(mri3, dy, say[0]);
-                    saz[0] = fmaf(mri3, dz, saz[0]);
-                    spp[0] -= mri;
-                } else {
+                    sax[K - 1] = fmaf(mri3, dx, sax[K - 1]);
+                    say[K - 1] = fmaf(mri3, dy, say[K - 1]);
+                    saz[K - 1] = fmaf(mri3, dz, saz[K - 1]);
+                    spp[K - 1] -= mri;
+                }
+                if (KP > 0) {
                     const f2 jx = f2_bc(j.x), jy = f2_bc(j.y), jz = f2_bc(j.z), jm = f2_bc(j.w);
 #pragma unroll
                     for (int h = 0; h < KP; ++h) {
@@ -480,11 +488,11 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
                 }
             }
         }
-        if (K == 1) {
-            kahan_smem_add<CB>(s_k, 0, 0, sax[0]);
-            kahan_smem_add<CB>(s_k, 0, 1, say[0]);
-            kahan_smem_add<CB>(s_k, 0, 2, saz[0]);
-            kahan_smem_add<CB>(s_k, 0, 3, spp[0]);
+        if (K & 1) {
+            kahan_smem_add<CB>(s_k, K - 1, 0, sax[K - 1]);
+            kahan_smem_add<CB>(s_k, K - 1, 1, say[K - 1]);
+            kahan_smem_add<CB>(s_k, K - 1, 2, saz[K - 1]);
+            kahan_smem_add<CB>(s_k, K - 1, 3, spp[K - 1]);
         }
 #pragma unroll
         for (int h = 0; h < KP; ++h) {
@@ -504,35 +512,28 @@ __device__ __forceinline__ void force_round_f32(const ForceArgs& A, uint32_t gf,
         }
         __syncthreads();  // chunk buffers are rewritten next
     }
-    // ---- combine slices and write back; s_red overlays the superparticle
-    // buffer, which is idle until the next chunk.  A slice's Kahan pair
-    // (s, c) is the double-float s + (-c); the slices are added with exact
-    // two-sums in FP32 and each component is turned into FP64 once (FP64 is
-    // a narrow pipe on this part).  The potential's self term is removed
-    // with the value the list's own entry contributed, m_i rsqrt(eps_i^2)
-    // in FP32, so that the two cancel.
-    float2* s_red2 = reinterpret_cast<float2*>(s_red);
-    const int rows = P * K;  // i-slots of this round; nsl * rows <= kRed
-#pragma unroll
-    for (int q = 0; q < K; ++q)
-        if (on)
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-                s_red2[c * kRed + sl * rows + ip + q * P] =
-                    iv[q] ? make_float2(s_k[((q * 4 + c) * 2) * CB + t], -s_k[((q * 4 + c) * 2 + 1) * CB + t])
-                          : make_float2(0.0f, 0.0f);
-    __syncthreads();
+    // ---- combine slices and write back.  A slice's Kahan pair (s, c) is the
+    // double-float s + (-c); the combining thread of a row reads the pairs
+    // of all its slices from the Kahan arrays, adds them with exact
+    // two-sums in FP32 and turns each component into FP64 once (FP64 is a
+    // narrow pipe on this part).  The potential's self term is removed with
+    // the value the list's own entry contributed, m_i rsqrt(eps_i^2) in
+    // FP32, so that the two cancel.
+    const int rows = P * K;  // i-slots of this round: row r = ip + q P
+    __syncthreads();         // every thread's Kahan sums are final
     for (int r = t; r < rows; r += CB) {
         const uint32_t i = ib + (uint32_t)r;
         if (i >= ni) continue;
+        const int q = r / P, ipr = r - q * P;
         float hi[4] = {0.0f, 0.0f, 0.0f, 0.0f}, lo[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        for (int s2 = 0; s2 < nsl; ++s2)
+        for (int s2 = 0; s2 < nsl; ++s2) {
+            const int t2 = s2 * P + ipr;  // the thread of slice s2 holding row r
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                const float2 v = s_red2[c * kRed + s2 * rows + r];
-                two_sum_acc(hi[c], lo[c], v.x);
-                lo[c] += v.y;
+                two_sum_acc(hi[c], lo[c], s_k[((q * 4 + c) * 2) * CB + t2]);
+                lo[c] -= s_k[((q * 4 + c) * 2 + 1) * CB + t2];
             }
+        }
         const uint32_t p = gf + i;
         two_sum_acc(hi[3], lo[3], A.pf_hi[p].w * rsqrtf(A.pf_lo[p].w));
         A.ax[p] = (double)hi[0] + (double)lo[0];
@@ -548,9 +549,7 @@ template <bool QUAD, int EPT, int CB, int KMAX>
 struct F32Shared {
     static constexpr int kCE = CB * EPT;
     static constexpr int kSpjBytes = kCE * (QUAD ? 40 : 16);
-    static constexpr int kRedBytes = 4 * KMAX * CB * 8;
-    static constexpr int kUnion = kSpjBytes > kRedBytes ? kSpjBytes : kRedBytes;
-    __align__(16) unsigned char u[kUnion];  // superparticles of a chunk, or the slice reduction
+    __align__(16) unsigned char u[kSpjBytes];  // superparticles of a chunk
     __align__(16) float4 j[kCJ];
     __align__(16) uint32_t ef[kCE];
     __align__(16) uint32_t es[kCE];
@@ -566,7 +565,6 @@ __device__ __forceinline__ void force_group(const ForceArgs& A, uint32_t g, F32S
     sb.s0 = reinterpret_cast<float4*>(sm.u);
     sb.s1 = reinterpret_cast<float4*>(sm.u + kCE * 16);
     sb.s2 = reinterpret_cast<float2*>(sm.u + kCE * 32);
-    double* s_red = reinterpret_cast<double*>(sm.u);
     const uint32_t ni = A.g_count[g], gf = A.g_first[g];
     const unsigned long long off = A.g_off[g];
     const uint32_t len = A.g_len[g];
@@ -575,14 +573,18 @@ __device__ __forceinline__ void force_group(const ForceArgs& A, uint32_t g, F32S
         const GroupPlan pl = plan_group<CB, KMAX>(ni - ib);
         if (pl.K == 1) {
             force_round_f32<QUAD, 1, EPT, CB, KMAX>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, sm.j, sb,
-                                                    sm.ef, sm.es, sm.w, s_red, sm.k);
+                                                    sm.ef, sm.es, sm.w, sm.k);
+        } else if (KMAX >= 4 && pl.K == 3) {
+            if constexpr (KMAX >= 4)
+                force_round_f32<QUAD, 3, EPT, CB, KMAX>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, sm.j, sb,
+                                                        sm.ef, sm.es, sm.w, sm.k);
         } else if (KMAX == 2 || pl.K == 2) {
             force_round_f32<QUAD, 2, EPT, CB, KMAX>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, sm.j, sb,
-                                                    sm.ef, sm.es, sm.w, s_red, sm.k);
+                                                    sm.ef, sm.es, sm.w, sm.k);
         } else {
             if constexpr (KMAX >= 4)
                 force_round_f32<QUAD, 4, EPT, CB, KMAX>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, sm.j,
-                                                        sb, sm.ef, sm.es, sm.w, s_red, sm.k);
+                                                        sb, sm.ef, sm.es, sm.w, sm.k);
         }
         ib += (uint32_t)(pl.P * pl.K);
     }

@@ -84,20 +84,23 @@ __device__ __forceinline__ bool open_fp64(double L, int level, double theta2, co
 // and its totals for the device state word.  Every field is the same in
 // all lanes.
 struct WalkState {
-    unsigned long long cursor, chunk_end;
+    unsigned long long cbase;  // start of the warp's pool chunk
+    uint32_t coff, clen;       // cursor and length within it
     bool ovf;
-    unsigned long long acc_entries, acc_epj, acc_spj, acc_iepj, acc_ispj, acc_fb;
+    unsigned long long acc_entries, acc_epj, acc_spj, acc_iepj, acc_ispj;
     uint32_t max_front;
 };
 
 __device__ __forceinline__ WalkState walk_state_init() {
     WalkState S;
-    S.cursor = S.chunk_end = 0;
+    S.cbase = 0;
+    S.coff = S.clen = 0;
     S.ovf = false;
-    S.acc_entries = S.acc_epj = S.acc_spj = S.acc_iepj = S.acc_ispj = S.acc_fb = 0;
+    S.acc_entries = S.acc_epj = S.acc_spj = S.acc_iepj = S.acc_ispj = 0;
     S.max_front = 0;
     return S;
 }
+
 
 // The list of group g, walked by the calling warp (all 32 lanes), with its
 // two frontier buffers fa and fb.
@@ -122,8 +125,22 @@ __device__ __forceinline__ void walk_group(const WalkArgs& A, uint32_t g, uint32
     const float4 blo = A.g_blo[g], bhi = A.g_bhi[g];
     const float hb = fmaxf(fmaxf(fmaxf(-blo.x, -blo.y), fmaxf(-blo.z, bhi.x)), fmaxf(bhi.y, bhi.z));
     const double* box64 = A.g_box + 6 * (int64_t)g;
+    // Coefficients of the filter's error bound as a polynomial in M = max|d| +
+    // hb (d the FP32 offset of a cell's centre of mass, hb the largest
+    // |corner| of the group box): with E = 4uM + e0 the error of one
+    // coordinate and S1 = t_x + t_y + t_z <= 3M, theta^2 (2 E S1 + 3 E^2) <=
+    // theta^2 (25 u M^2 + 7 e0 M + 4 e0^2); 1 % on top covers the rounding of
+    // the bound's own FP32 evaluation.
+    const float e0 = 1e-13f * Lf;
+    const float mc1 = 1.01f * A.theta2f * 25.0f * kU32, mc2 = 1.01f * A.theta2f * 7.0f * e0,
+                mc3 = 1.01f * A.theta2f * 4.0f * e0 * e0;
 
-    unsigned long long gstart = S.cursor;
+    if (S.ovf) {  // counting only: keep the in-chunk cursor small
+        S.cbase += S.coff;
+        S.coff = 0;
+    }
+    unsigned long long gstart = S.cbase + S.coff;
+    uint32_t* cptr = A.pool + S.cbase;
     uint32_t nspj = 0, nepj_lane = 0;
     uint32_t fsize = 1;
     if (lane == 0) fa[0] = sysid;
@@ -159,7 +176,6 @@ __device__ __forceinline__ void walk_group(const WalkArgs& A, uint32_t g, uint32
             if (idx + 64 < fsize) node_nx2 = fa[idx + 64];
             int action = 0;  // 1 SPJ, 2 EPJ leaf, 3 open internal
             uint32_t nch = 0, child = 0;
-            bool fallback = false;
             if (act) {
                 const int level = (int)((rec.x >> 21) & 31u);
                 const bool leaf = (rec.x >> 26) & 1u;
@@ -182,19 +198,15 @@ __device__ __forceinline__ void walk_group(const WalkArgs& A, uint32_t g, uint32
                     const float r2 = A.theta2f * d2;
                     const float T = l2 - r2;
                     // bound on |T - (ell^2 - theta^2 D^2)|, D the exact distance
-                    const float E = 4.0f * kU32 *
-                                        (fmaxf(fmaxf(fabsf(dx), fabsf(dy)), fabsf(dz)) + hb) +
-                                    1e-13f * Lf;
-                    const float S1 = tx + ty + tz;
-                    const float margin =
-                        8.0f * kU32 * (l2 + r2) + A.theta2f * (2.0f * E * S1 + 3.0f * E * E);
+                    const float M = fmaxf(fmaxf(fabsf(dx), fabsf(dy)), fabsf(dz)) + hb;
+                    const float margin = fmaf(8.0f * kU32, l2 + r2, fmaf(fmaf(mc1, M, mc2), M, mc3));
                     if (filt && T > margin) {
                         open = true;
                     } else if (filt && T < -margin) {
                         open = false;
                     } else {
-                        fallback = true;
                         open = open_fp64(L, level, A.theta2, A.nd_com[node], box64);
+                        atomicAdd(&st->fallbacks, 1ull);  // rare: counted where it happens
                     }
                 }
                 if (!open) {
@@ -208,22 +220,21 @@ __device__ __forceinline__ void walk_group(const WalkArgs& A, uint32_t g, uint32
                     nch = rec.x >> 27;
                 }
             }
-            S.acc_fb += __popc(__ballot_sync(0xFFFFFFFFu, fallback));
             // ---- append SPJ / EPJ entries
             const bool emit = action == 1 || action == 2;
             const uint32_t emask = __ballot_sync(0xFFFFFFFFu, emit);
             const uint32_t k = __popc(emask);
             if (k) {
-                if (S.cursor + k > S.chunk_end) {
+                if (S.coff + k > S.clen) {
                     // new chunk: at least kChunk entries and twice the
                     // group's list so far, so long lists move O(log) times
-                    const unsigned long long sofar = S.cursor - gstart;
+                    const unsigned long long sofar = S.cbase + S.coff - gstart;
                     const unsigned long long want =
                         2 * (sofar + k) > kChunk ? 2 * (sofar + k) : kChunk;
                     unsigned long long nb = 0;
                     if (lane == 0) nb = atomicAdd(&st->pool_cursor, want);
                     nb = shfl_u64(nb, 0);
-                    if (!S.ovf && nb + want > A.cap_pool) {
+                    if (!S.ovf && (nb + want > A.cap_pool || want > 0xFFFFFFFFull)) {
                         if (lane == 0) atomicOr(&st->overflow, kOvfPool);
                         S.ovf = true;
                     }
@@ -232,15 +243,19 @@ __device__ __forceinline__ void walk_group(const WalkArgs& A, uint32_t g, uint32
                             A.pool[nb + j] = A.pool[gstart + j];
                         __syncwarp();
                         gstart = nb;
-                        S.cursor = nb + sofar;
-                        S.chunk_end = nb + want;
+                        S.cbase = nb;
+                        S.coff = (uint32_t)sofar;
+                        S.clen = (uint32_t)want;
+                        cptr = A.pool + nb;
                     } else {
-                        S.chunk_end = ~0ull;  // count only from here on
+                        // count only from here on
+                        S.cbase = gstart;
+                        S.coff = (uint32_t)sofar;
+                        S.clen = 0xFFFFFFFFu;
                     }
                 }
-                if (emit && !S.ovf)
-                    A.pool[S.cursor + __popc(emask & lt)] = action == 2 ? (node | kLeafTag) : node;
-                S.cursor += k;
+                if (emit && !S.ovf) cptr[S.coff + __popc(emask & lt)] = action == 2 ? (node | kLeafTag) : node;
+                S.coff += k;
             }
             nspj += __popc(__ballot_sync(0xFFFFFFFFu, action == 1));
             // ---- push children of opened internal cells (deep in the
@@ -270,7 +285,7 @@ __device__ __forceinline__ void walk_group(const WalkArgs& A, uint32_t g, uint32
         fsize = nsize;
     }
     const uint32_t nepj = __reduce_add_sync(0xFFFFFFFFu, nepj_lane);
-    const unsigned long long len = S.cursor - gstart;
+    const unsigned long long len = S.cbase + S.coff - gstart;
     if (lane == 0) {
         A.g_off[g] = gstart;
         A.g_len[g] = (uint32_t)len;
@@ -295,7 +310,6 @@ __device__ __forceinline__ void walk_flush(const WalkArgs& A, const WalkState& S
         atomicAdd(&st->n_spj, S.acc_spj);
         atomicAdd(&st->int_epj, S.acc_iepj);
         atomicAdd(&st->int_spj, S.acc_ispj);
-        atomicAdd(&st->fallbacks, S.acc_fb);
         atomicMax(&st->max_frontier, S.max_front);
     }
 }

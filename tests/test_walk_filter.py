@@ -44,7 +44,7 @@ def open_fp64(L, level, theta2, com, box):
     return ell * ell >= theta2 * d2
 
 
-def filter_f32(L, level, theta2, com, box, c0, fused):
+def filter_f32(L, level, theta2, com, box, c0, fused, shrink=1.0):
     cc = [(box[a] + box[3 + a]) * 0.5 for a in range(3)]
     gc = [split(cc[a] - c0[a]) for a in range(3)]
     blo = [round_down(box[a] - cc[a]) for a in range(3)]
@@ -62,13 +62,15 @@ def filter_f32(L, level, theta2, com, box, c0, fused):
     l2 = ell * ell
     r2 = theta2f * d2
     T = l2 - r2
-    dmax = max(abs(d[0]), abs(d[1]), abs(d[2]))
-    if fused:
-        E = fma32(f32(4.0) * U, dmax + hb, f32(1e-13) * Lf)
-    else:
-        E = f32(4.0) * U * (dmax + hb) + f32(1e-13) * Lf
-    S1 = t[0] + t[1] + t[2]
-    margin = f32(8.0) * U * (l2 + r2) + theta2f * (f32(2.0) * E * S1 + f32(3.0) * E * E)
+    # the bound as the kernel evaluates it: theta^2 (2 E S1 + 3 E^2) with E =
+    # 4uM + e0, S1 <= 3M, as a polynomial in M = max|d| + hb, plus 1 %
+    e0 = f32(1e-13) * Lf
+    mc1 = f32(1.01) * theta2f * f32(25.0) * U
+    mc2 = f32(1.01) * theta2f * f32(7.0) * e0
+    mc3 = f32(1.01) * theta2f * f32(4.0) * e0 * e0
+    M = max(abs(d[0]), abs(d[1]), abs(d[2])) + hb
+    margin = fma32(f32(8.0) * U, l2 + r2, fma32(fma32(mc1, M, mc2), M, mc3))
+    margin = f32(margin * f32(shrink))
     if T > margin:
         return 1
     if T < -margin:
@@ -76,11 +78,8 @@ def filter_f32(L, level, theta2, com, box, c0, fused):
     return -1  # inside the bound: the FP64 sequence decides
 
 
-@pytest.mark.parametrize("fused", [False, True])
-def test_filter_never_contradicts_the_fp64_test(fused):
-    rng = np.random.default_rng(20260 + fused)
-    decided, inside, inside_far = 0, 0, 0
-    for _ in range(6000):
+def _cases(rng, count):
+    for _ in range(count):
         L = 10.0 ** rng.uniform(-3, 3)
         level = int(rng.integers(0, 22))
         theta = rng.uniform(0.2, 1.2)
@@ -96,6 +95,14 @@ def test_filter_never_contradicts_the_fp64_test(fused):
         u /= np.linalg.norm(u)
         sign = rng.choice([-1.0, 1.0], 3)
         com = np.where(sign > 0, box[3:] + u * dist, box[:3] - u * dist)
+        yield L, level, theta, theta2, c0, box, com, rel, half, dist
+
+
+@pytest.mark.parametrize("fused", [False, True])
+def test_filter_never_contradicts_the_fp64_test(fused):
+    rng = np.random.default_rng(20260 + fused)
+    decided, inside, inside_far = 0, 0, 0
+    for L, level, theta, theta2, c0, box, com, rel, half, dist in _cases(rng, 6000):
         want = open_fp64(L, level, theta2, com, box)
         got = filter_f32(L, level, theta2, com, box, c0, fused)
         if got < 0:
@@ -110,3 +117,15 @@ def test_filter_never_contradicts_the_fp64_test(fused):
     # the bound is tight enough to leave only near-threshold cases to FP64
     assert inside_far == 0
     assert decided > 0 and inside > 0  # both branches are exercised
+
+
+def test_filter_with_a_shrunk_bound_contradicts_the_fp64_test():
+    """The bound is not vacuous: divided by 1000 it lets the FP32 value decide
+    cases that the FP64 sequence decides the other way."""
+    rng = np.random.default_rng(20262)
+    wrong = 0
+    for L, level, theta, theta2, c0, box, com, rel, half, dist in _cases(rng, 6000):
+        got = filter_f32(L, level, theta2, com, box, c0, False, shrink=1e-3)
+        if got >= 0 and bool(got) != open_fp64(L, level, theta2, com, box):
+            wrong += 1
+    assert wrong > 0
