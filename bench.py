@@ -381,7 +381,7 @@ def run_ours(args, rank, world, local_rank):
         # n_grp in {64, 128, 256, 512} (and n_leaf, tile depth) by measured
         # time of the whole force calculation
         best, ms = tree.autotune(ps, n_leaf=(8, 16), n_grp=(64, 128, 256, 512),
-                                 tile_depth=(256, 512), block=(64, 128, 256), i_per_thread=(2, 4), repeats=1)
+                                 tile_depth=(256, 512), block=(64, 128, 256), i_per_thread=(2, 4, 5), repeats=1)
         tuned = {**best, "force_ms": ms}
         args.n_leaf, args.n_grp = best["n_leaf"], best["n_grp"]
     tree.calc_force_all_and_write_back(ps)
@@ -558,7 +558,7 @@ def run_ensemble(args, rank=0, world=1, local_rank=0):
     tuned = None
     if not args.no_autotune:
         best, ms = tree.autotune(ps, n_leaf=(8, 16), n_grp=(32, 64, 128, 256), tile_depth=(256, 512),
-                                 block=(64, 128, 256), i_per_thread=(2, 4), repeats=1)
+                                 block=(64, 128, 256), i_per_thread=(2, 4, 5), repeats=1)
         tuned = {**best, "force_ms": ms}
     tree.calc_force_all_and_write_back(ps)
     ek0, ep0 = ps.energy_systems()
@@ -645,7 +645,7 @@ def run_config(G, torch, name, model, n, eps, theta, quad, n_leaf, n_grp, steps,
     tuned = None
     if autotune:
         best, ms = tree.autotune(ps, n_leaf=(8, 16), n_grp=(64, 128, 256, 512), tile_depth=(256, 512),
-                                 block=(64, 128, 256), i_per_thread=(2, 4), repeats=1)
+                                 block=(64, 128, 256), i_per_thread=(2, 4, 5), repeats=1)
         tuned = {**best, "force_ms": ms}
     tree.calc_force_all_and_write_back(ps)
     st0 = tree.stats()

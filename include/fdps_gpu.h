@@ -85,8 +85,8 @@ typedef enum {
      block      threads per CTA of the FP32 force kernel: 0 (default, =
                 128), 64, 128 or 256
      i_per_thread  at most this many i-particles per thread of the FP32
-                force kernel: 0 (default, = 4), 2 or 4; block 256 takes 2
-                at most (its Kahan sums would not fit shared memory)
+                force kernel: 0 (default, = 5), 2, 4 or 5; block 256 takes
+                2 at most (its Kahan sums would not fit shared memory)
      (block and i_per_thread, the "block shape", change only the speed;
      the FP64 variant ignores them)                                      */
 typedef struct {
@@ -169,14 +169,20 @@ int64_t fdps_psys_size(const fdps_psys* ps);
    ParticleParticleNbody, eps_i of the receiving particle).  vel3n may be
    NULL (zero velocities).  Values are validated on the device: NaN/Inf,
    negative mass or non-positive eps give FDPS_EINVAL.  Resets the
-   particle order to the caller's order. */
+   particle order to the caller's order.  on_device = 0: host arrays; the
+   device reads page-locked or managed host arrays directly (over the
+   CPU-GPU link, no staging copy) and stages the others through device
+   memory with copies.  The call returns after the data has been read, so
+   the caller may reuse its arrays at once. */
 int fdps_psys_set(fdps_psys* ps, const double* pos3n, const double* vel3n,
                   const double* mass, const double* eps, int on_device);
 /* Copy particle data out in the caller's order (rows as passed to
    fdps_psys_set).  Any output pointer may be NULL.  acc3n and pot are the
    results of the last force calculation (copyFromForce); the potential has
    the self term removed.  FDPS_ESTATE if acc/pot are requested before any
-   force calculation. */
+   force calculation.  Page-locked or managed host arrays are written by
+   the device directly, others through a device staging buffer and copies;
+   the call returns when the data is in place. */
 int fdps_psys_get(const fdps_psys* ps, double* pos3n, double* vel3n,
                   double* acc3n, double* pot, int on_device);
 

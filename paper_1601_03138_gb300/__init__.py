@@ -318,7 +318,7 @@ def fdps_tree_autotune(ctx, tree, ps, n_leaf=(8, 16), n_grp=(64, 128, 256, 512),
                                     C.byref(ms)), ctx)
     return ({"theta": best.theta, "n_leaf": best.n_leaf, "n_grp": best.n_grp,
              "tile_depth": best.tile_depth, "block": best.block or 128,
-             "i_per_thread": best.i_per_thread or 4}, ms.value)
+             "i_per_thread": best.i_per_thread or 5}, ms.value)
 
 
 def fdps_psys_energy(ctx, ps):

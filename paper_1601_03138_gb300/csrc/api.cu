@@ -347,7 +347,7 @@ bool valid_params(const fdps_tree_params* p) {
            (p->precision == FDPS_FP32REL || p->precision == FDPS_FP64) &&
            (p->tile_depth == 0 || p->tile_depth == 256 || p->tile_depth == 512) &&
            (p->block == 0 || p->block == 64 || p->block == 128 || p->block == 256) &&
-           (p->i_per_thread == 0 || p->i_per_thread == 2 || p->i_per_thread == 4) &&
+           (p->i_per_thread == 0 || p->i_per_thread == 2 || p->i_per_thread == 4 || p->i_per_thread == 5) &&
            !(p->block == 256 && p->i_per_thread != 2);
 }
 
@@ -477,6 +477,7 @@ int fdps_psys_destroy(fdps_psys* ps) {
     dev_free(ps->d_flag);
     dev_free(ps->d_red);
     dev_free(ps->stage);
+    dev_free(ps->inv);
     dev_free(ps->d_off);
     dev_free(ps->d_order);
     dev_free(ps->d_sys);
@@ -486,6 +487,30 @@ int fdps_psys_destroy(fdps_psys* ps) {
 }
 
 int64_t fdps_psys_size(const fdps_psys* ps) { return ps ? ps->n : -1; }
+
+}  // extern "C"
+
+namespace {
+
+// The address under which the current device reads a caller's host
+// pointer directly (page-locked or managed memory: on this part a kernel
+// moves data over the CPU-GPU link as fast as a copy does), else null:
+// such data is staged by copies instead.
+const double* device_view(const double* p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeManaged) return p;
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) return static_cast<const double*>(a.devicePointer);
+    return nullptr;
+}
+
+}  // namespace
+
+extern "C" {
 
 int fdps_psys_set(fdps_psys* ps, const double* pos3n, const double* vel3n, const double* mass,
                   const double* eps, int on_device) {
@@ -498,8 +523,17 @@ int fdps_psys_set(fdps_psys* ps, const double* pos3n, const double* vel3n, const
     ps->cur = 0;
     ps->has_data = false;
     ps->has_forces = false;
+    uint32_t bad = 0;
+    const double* vp = on_device ? nullptr : device_view(pos3n);
+    const double* vv = on_device ? nullptr : device_view(vel3n);
+    const double* vm = on_device ? nullptr : device_view(mass);
+    const double* ve = on_device ? nullptr : device_view(eps);
     if (on_device) {
-        int rc = launch_scatter_in(ps, pos3n, vel3n, mass, eps);
+        int rc = launch_scatter_in(ps, pos3n, vel3n, mass, eps, &bad);
+        if (rc) return rc;
+    } else if (vp && vm && ve && (!vel3n || vv)) {
+        // the device reads the caller's buffers over the link
+        int rc = launch_scatter_in(ps, vp, vel3n ? vv : nullptr, vm, ve, &bad);
         if (rc) return rc;
     } else {
         // host data is staged in the psys's transfer buffer
@@ -521,13 +555,10 @@ int fdps_psys_set(fdps_psys* ps, const double* pos3n, const double* vel3n, const
         if (e1 || e2 || e3 || e4)
             rc = set_error(ctx, FDPS_ECUDA, "host to device copy failed");
         else
-            rc = launch_scatter_in(ps, st_pos, vel3n ? st_vel : nullptr, st_m, st_e);
+            rc = launch_scatter_in(ps, st_pos, vel3n ? st_vel : nullptr, st_m, st_e, &bad);
         cudaStreamSynchronize(s);
         if (rc) return rc;
     }
-    uint32_t bad = 0;
-    int rc = launch_validate(ps, &bad);
-    if (rc) return rc;
     if (bad)
         return set_error(ctx, FDPS_EINVAL, "invalid particle data:%s%s%s%s",
                          (bad & 1) ? " non-finite position" : "", (bad & 2) ? " non-finite velocity" : "",
@@ -548,20 +579,31 @@ int fdps_psys_get(const fdps_psys* ps, double* pos3n, double* vel3n, double* acc
     cudaSetDevice(ctx->device);
     cudaStream_t s = ctx->stream;
     const int64_t n = ps->n;
+    fdps_psys* pm = const_cast<fdps_psys*>(ps);
     if (on_device) {
-        int rc = launch_gather_out(ps, pos3n, vel3n, acc3n, pot);
+        int rc = launch_gather_out(pm, pos3n, vel3n, acc3n, pot);
         if (rc) return rc;
         FDPS_CUDA_TRY(ctx, cudaStreamSynchronize(s));
         return FDPS_OK;
     }
-    fdps_psys* pm = const_cast<fdps_psys*>(ps);
+    // the device writes the caller's buffers over the link where it can
+    double* vp = const_cast<double*>(device_view(pos3n));
+    double* vv = const_cast<double*>(device_view(vel3n));
+    double* va = const_cast<double*>(device_view(acc3n));
+    double* vq = const_cast<double*>(device_view(pot));
+    if ((!pos3n || vp) && (!vel3n || vv) && (!acc3n || va) && (!pot || vq)) {
+        int rc = launch_gather_out(pm, vp, vv, va, vq);
+        if (rc) return rc;
+        FDPS_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        return FDPS_OK;
+    }
     if (!pm->stage && dev_alloc(&pm->stage, 10 * n) != cudaSuccess) {
         cudaGetLastError();
         pm->stage = nullptr;
         return set_error(ctx, FDPS_ENOMEM, "staging allocation failed");
     }
     double* stage = pm->stage;
-    int rc = launch_gather_out(ps, pos3n ? stage : nullptr, vel3n ? stage + 3 * n : nullptr,
+    int rc = launch_gather_out(pm, pos3n ? stage : nullptr, vel3n ? stage + 3 * n : nullptr,
                                acc3n ? stage + 6 * n : nullptr, pot ? stage + 9 * n : nullptr);
     cudaError_t e = cudaSuccess;
     if (!rc) {
@@ -583,7 +625,7 @@ int fdps_tree_create(fdps_ctx* ctx, const fdps_tree_params* params, fdps_tree** 
     if (!valid_params(params))
         return set_error(ctx, FDPS_EINVAL,
                          "invalid tree parameters (theta >= 0, 1 <= n_leaf <= %d, n_leaf <= n_grp <= %d, "
-                         "tile_depth 0/256/512, block 0/64/128/256, i_per_thread 0/2/4, block 256 with "
+                         "tile_depth 0/256/512, block 0/64/128/256, i_per_thread 0/2/4/5, block 256 with "
                          "i_per_thread 2)",
                          kMaxLeaf, kMaxGrp);
     cudaSetDevice(ctx->device);

@@ -106,7 +106,7 @@ __device__ __forceinline__ int owner(const uint32_t* scan, uint32_t item) {
 // partial sums of the chunk into Kahan-compensated running sums once per
 // chunk.
 
-constexpr int kCJ = 256;  // leaf particles per shared tile
+constexpr int kCJ = 224;  // leaf particles per shared tile (the shared memory of 128 x 5 fits 48 KB)
 
 struct GroupPlan {
     int K, P, nsl;
@@ -114,23 +114,23 @@ struct GroupPlan {
 
 template <int CB, int KMAX>
 __device__ __forceinline__ GroupPlan plan_group(uint32_t ni) {
-    // maximise ni * nsl / (CB * K) over K in {1, 2, 3, 4} (up to KMAX);
+    // maximise ni * nsl / (CB * K) over K in {1, ..., 5} (up to KMAX);
     // larger K on ties
     GroupPlan best{1, 1, 1};
     float bu = -1.f;
-    // K = 3 is one packed pair and one scalar lane: it issues as many
-    // instructions per list entry as K = 4 for three quarters of the work,
-    // so it must fill the CTA 6 % better to be taken
+    // an odd K is packed pairs plus one scalar lane: the scalar lane issues
+    // as many instructions per list entry as a pair for half the work, so an
+    // odd K must fill the CTA 6 % better to be taken
     constexpr float kOdd = 1.06f;
-    const int Ks[4] = {4, 3, 2, 1};
+    const int Ks[5] = {5, 4, 3, 2, 1};
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < 5; ++c) {
         const int K = Ks[c];
         if (K > KMAX) continue;
         const int P = (int)((ni + K - 1) / K);
         if (P > CB) continue;
         const int nsl = CB / P;
-        const float u = (float)ni * nsl / (float)(CB * K) / (K == 3 ? kOdd : 1.0f);
+        const float u = (float)ni * nsl / (float)(CB * K) / ((K & 1) && K > 1 ? kOdd : 1.0f);
         if (u > bu + 1e-6f) {
             bu = u;
             best = GroupPlan{K, P, nsl};
@@ -574,6 +574,10 @@ __device__ __forceinline__ void force_group(const ForceArgs& A, uint32_t g, F32S
         if (pl.K == 1) {
             force_round_f32<QUAD, 1, EPT, CB, KMAX>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, sm.j, sb,
                                                     sm.ef, sm.es, sm.w, sm.k);
+        } else if (KMAX >= 5 && pl.K == 5) {
+            if constexpr (KMAX >= 5)
+                force_round_f32<QUAD, 5, EPT, CB, KMAX>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, sm.j, sb,
+                                                        sm.ef, sm.es, sm.w, sm.k);
         } else if (KMAX >= 4 && pl.K == 3) {
             if constexpr (KMAX >= 4)
                 force_round_f32<QUAD, 3, EPT, CB, KMAX>(A, gf, ni, off, len, gch, gcl, pl.P, pl.nsl, ib, sm.j, sb,
@@ -760,15 +764,19 @@ void launch_f32_shape(const ForceArgs& A, fdps_ctx* ctx, cudaStream_t s, int cb,
     if (cb == 64) {
         if (kmax == 2)
             launch_f32<QUAD, CE, 64, 2>(A, ctx, s);
-        else
+        else if (kmax == 4)
             launch_f32<QUAD, CE, 64, 4>(A, ctx, s);
+        else
+            launch_f32<QUAD, CE, 64, 5>(A, ctx, s);
     } else if (cb == 256) {
         launch_f32<QUAD, CE, 256, 2>(A, ctx, s);  // 256 x 4 does not fit static shared memory
     } else {
         if (kmax == 2)
             launch_f32<QUAD, CE, 128, 2>(A, ctx, s);
-        else
+        else if (kmax == 4)
             launch_f32<QUAD, CE, 128, 4>(A, ctx, s);
+        else
+            launch_f32<QUAD, CE, 128, 5>(A, ctx, s);
     }
 }
 
@@ -825,10 +833,10 @@ int compute_forces(fdps_tree* t, fdps_psys* ps, int spj_kind) {
             k_force_f64<false><<<blocks, kFBlock, 0, s>>>(A);
     } else {
         // tile depth: list entries staged per chunk (0 = default 512); block
-        // shape: threads per CTA (0 = 128) and i-particles per thread (0 = 4)
+        // shape: threads per CTA (0 = 128) and i-particles per thread (0 = 5)
         const bool shallow = t->p.tile_depth == 256;
         const int cb = t->p.block ? t->p.block : 128;
-        const int kmax = t->p.i_per_thread ? t->p.i_per_thread : 4;
+        const int kmax = t->p.i_per_thread ? t->p.i_per_thread : 5;
         if (quad) {
             if (shallow)
                 launch_f32_shape<true, 256>(A, ctx, s, cb, kmax);

@@ -9,77 +9,121 @@
 namespace fdps {
 namespace {
 
-__global__ void __launch_bounds__(256) k_scatter_in(int64_t n, const double* __restrict__ pos,
-                                                    const double* __restrict__ vel,
-                                                    const double* __restrict__ mass,
-                                                    const double* __restrict__ eps, double* x,
-                                                    double* y, double* z, double* vx, double* vy,
-                                                    double* vz, double* m, double* e, uint32_t* id) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        x[i] = pos[3 * i];
-        y[i] = pos[3 * i + 1];
-        z[i] = pos[3 * i + 2];
-        vx[i] = vel ? vel[3 * i] : 0.0;
-        vy[i] = vel ? vel[3 * i + 1] : 0.0;
-        vz[i] = vel ? vel[3 * i + 2] : 0.0;
-        m[i] = mass[i];
-        e[i] = eps[i];
-        id[i] = (uint32_t)i;
-    }
+// The input rules as bit tests (FP64 compares run on a narrow pipe on this
+// part): finite = exponent field not all ones; mass >= 0 holds for +0, -0
+// and positive values; eps > 0 for positive nonzero values.
+__device__ __forceinline__ bool finite64(double v) {
+    return ((__double_as_longlong(v) >> 52) & 0x7FF) != 0x7FF;
+}
+__device__ __forceinline__ bool nonneg64(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) == 0 || b == 0x8000000000000000ull;
+}
+__device__ __forceinline__ bool positive64(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) == 0 && b != 0;
 }
 
-__global__ void __launch_bounds__(256) k_validate(int64_t n, const double* __restrict__ x,
-                                                  const double* __restrict__ y,
-                                                  const double* __restrict__ z,
-                                                  const double* __restrict__ vx,
-                                                  const double* __restrict__ vy,
-                                                  const double* __restrict__ vz,
-                                                  const double* __restrict__ m,
-                                                  const double* __restrict__ e, uint32_t* flag) {
+constexpr int kIoTile = 256;  // particles per block and round of the in/out kernels
+
+// [n][3] rows base .. base + m of a caller array into s[3 m] (flat, so that
+// a warp's loads are contiguous: this matters when the array is host memory
+// read over the CPU-GPU link).
+__device__ __forceinline__ void load_rows3(const double* __restrict__ a, int64_t base, int m, double* s) {
+    for (int k = threadIdx.x; k < 3 * m; k += kIoTile) s[k] = a[3 * base + k];
+}
+__device__ __forceinline__ void store_rows3(double* a, int64_t base, int m, const double* s) {
+    for (int k = threadIdx.x; k < 3 * m; k += kIoTile) a[3 * base + k] = s[k];
+}
+
+// Caller-order input arrays (device memory, or host memory the device can
+// read) into the structure-of-arrays buffers, checked on the way: flag bit
+// 1 a non-finite position, 2 a non-finite velocity, 4 a negative or
+// non-finite mass, 8 a non-positive or non-finite softening.
+__global__ void __launch_bounds__(kIoTile) k_scatter_in(int64_t n, const double* __restrict__ pos,
+                                                        const double* __restrict__ vel,
+                                                        const double* __restrict__ mass,
+                                                        const double* __restrict__ eps, double* x,
+                                                        double* y, double* z, double* vx, double* vy,
+                                                        double* vz, double* m, double* e, uint32_t* id,
+                                                        uint32_t* flag) {
+    __shared__ double s_p[3 * kIoTile], s_v[3 * kIoTile];
     uint32_t bad = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        if (!isfinite(x[i]) || !isfinite(y[i]) || !isfinite(z[i])) bad |= 1u;
-        if (!isfinite(vx[i]) || !isfinite(vy[i]) || !isfinite(vz[i])) bad |= 2u;
-        if (!(m[i] >= 0.0) || !isfinite(m[i])) bad |= 4u;
-        if (!(e[i] > 0.0) || !isfinite(e[i])) bad |= 8u;
+    for (int64_t base = (int64_t)blockIdx.x * kIoTile; base < n; base += (int64_t)gridDim.x * kIoTile) {
+        const int cnt = n - base < kIoTile ? (int)(n - base) : kIoTile;
+        load_rows3(pos, base, cnt, s_p);
+        if (vel) load_rows3(vel, base, cnt, s_v);
+        __syncthreads();
+        const int t = threadIdx.x;
+        if (t < cnt) {
+            const int64_t i = base + t;
+            const double px = s_p[3 * t], py = s_p[3 * t + 1], pz = s_p[3 * t + 2];
+            const double ux = vel ? s_v[3 * t] : 0.0, uy = vel ? s_v[3 * t + 1] : 0.0,
+                         uz = vel ? s_v[3 * t + 2] : 0.0;
+            const double mi = mass[i], ei = eps[i];
+            bad |= (finite64(px) && finite64(py) && finite64(pz)) ? 0u : 1u;
+            bad |= (finite64(ux) && finite64(uy) && finite64(uz)) ? 0u : 2u;
+            bad |= (finite64(mi) && nonneg64(mi)) ? 0u : 4u;
+            bad |= (finite64(ei) && positive64(ei)) ? 0u : 8u;
+            x[i] = px;
+            y[i] = py;
+            z[i] = pz;
+            vx[i] = ux;
+            vy[i] = uy;
+            vz[i] = uz;
+            m[i] = mi;
+            e[i] = ei;
+            id[i] = (uint32_t)i;
+        }
+        __syncthreads();  // the tiles are rewritten next round
     }
     bad = __reduce_or_sync(0xFFFFFFFFu, bad);
     if ((threadIdx.x & 31) == 0 && bad) atomicOr(flag, bad);
 }
 
-__global__ void __launch_bounds__(256) k_gather_out(int64_t n, const uint32_t* __restrict__ id,
-                                                    const double* __restrict__ x,
-                                                    const double* __restrict__ y,
-                                                    const double* __restrict__ z,
-                                                    const double* __restrict__ vx,
-                                                    const double* __restrict__ vy,
-                                                    const double* __restrict__ vz,
-                                                    const double* __restrict__ ax,
-                                                    const double* __restrict__ ay,
-                                                    const double* __restrict__ az,
-                                                    const double* __restrict__ phi, double* pos,
-                                                    double* vel, double* acc, double* pot) {
+// Inverse of the current order: inv[caller index] = position.
+__global__ void __launch_bounds__(256) k_invert(int64_t n, const uint32_t* __restrict__ id,
+                                                uint32_t* __restrict__ inv) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t d = id[i];
-        if (pos) {
-            pos[3 * d] = x[i];
-            pos[3 * d + 1] = y[i];
-            pos[3 * d + 2] = z[i];
+         i += (int64_t)gridDim.x * blockDim.x)
+        inv[id[i]] = (uint32_t)i;
+}
+
+// Results in the caller's order: a block takes kIoTile consecutive caller
+// indices j, reads each from position inv[j] and writes the rows out
+// contiguously (through shared memory for the [n][3] arrays).
+__global__ void __launch_bounds__(kIoTile) k_gather_out(int64_t n, const uint32_t* __restrict__ inv,
+                                                        const double* __restrict__ x,
+                                                        const double* __restrict__ y,
+                                                        const double* __restrict__ z,
+                                                        const double* __restrict__ vx,
+                                                        const double* __restrict__ vy,
+                                                        const double* __restrict__ vz,
+                                                        const double* __restrict__ ax,
+                                                        const double* __restrict__ ay,
+                                                        const double* __restrict__ az,
+                                                        const double* __restrict__ phi, double* pos,
+                                                        double* vel, double* acc, double* pot) {
+    __shared__ double s_t[3 * kIoTile];
+    for (int64_t base = (int64_t)blockIdx.x * kIoTile; base < n; base += (int64_t)gridDim.x * kIoTile) {
+        const int cnt = n - base < kIoTile ? (int)(n - base) : kIoTile;
+        const int t = threadIdx.x;
+        const int64_t s = t < cnt ? (int64_t)inv[base + t] : 0;
+        const double* src[3][3] = {{x, y, z}, {vx, vy, vz}, {ax, ay, az}};
+        double* dst[3] = {pos, vel, acc};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (!dst[a]) continue;
+            if (t < cnt) {
+                s_t[3 * t] = src[a][0][s];
+                s_t[3 * t + 1] = src[a][1][s];
+                s_t[3 * t + 2] = src[a][2][s];
+            }
+            __syncthreads();
+            store_rows3(dst[a], base, cnt, s_t);
+            __syncthreads();
         }
-        if (vel) {
-            vel[3 * d] = vx[i];
-            vel[3 * d + 1] = vy[i];
-            vel[3 * d + 2] = vz[i];
-        }
-        if (acc) {
-            acc[3 * d] = ax[i];
-            acc[3 * d + 1] = ay[i];
-            acc[3 * d + 2] = az[i];
-        }
-        if (pot) pot[d] = phi[i];
+        if (pot && t < cnt) pot[base + t] = phi[s];
     }
 }
 
@@ -276,23 +320,13 @@ int launch_energy_systems(fdps_psys* ps, double* kin, double* pot) {
 int energy_scratch_doubles() { return 2 * kEnergyBlocks + 2; }
 
 int launch_scatter_in(fdps_psys* ps, const double* pos, const double* vel, const double* mass,
-                      const double* eps) {
-    fdps_ctx* ctx = ps->ctx;
-    const int c = ps->cur;
-    k_scatter_in<<<grid_for(ps->n, 256, ctx->sm_count * 16), 256, 0, ctx->stream>>>(
-        ps->n, pos, vel, mass, eps, ps->x[c], ps->y[c], ps->z[c], ps->vx[c], ps->vy[c], ps->vz[c],
-        ps->m[c], ps->eps[c], ps->id[c]);
-    FDPS_LAUNCH_CHECK(ctx);
-    return FDPS_OK;
-}
-
-int launch_validate(fdps_psys* ps, uint32_t* bad) {
+                      const double* eps, uint32_t* bad) {
     fdps_ctx* ctx = ps->ctx;
     const int c = ps->cur;
     FDPS_CUDA_TRY(ctx, cudaMemsetAsync(ps->d_flag, 0, sizeof(uint32_t), ctx->stream));
-    k_validate<<<grid_for(ps->n, 256, ctx->sm_count * 16), 256, 0, ctx->stream>>>(
-        ps->n, ps->x[c], ps->y[c], ps->z[c], ps->vx[c], ps->vy[c], ps->vz[c], ps->m[c], ps->eps[c],
-        ps->d_flag);
+    k_scatter_in<<<grid_for(ps->n, kIoTile, ctx->sm_count * 8), kIoTile, 0, ctx->stream>>>(
+        ps->n, pos, vel, mass, eps, ps->x[c], ps->y[c], ps->z[c], ps->vx[c], ps->vy[c], ps->vz[c],
+        ps->m[c], ps->eps[c], ps->id[c], ps->d_flag);
     FDPS_LAUNCH_CHECK(ctx);
     FDPS_CUDA_TRY(ctx, cudaMemcpyAsync(bad, ps->d_flag, sizeof(uint32_t), cudaMemcpyDeviceToHost,
                                        ctx->stream));
@@ -300,12 +334,20 @@ int launch_validate(fdps_psys* ps, uint32_t* bad) {
     return FDPS_OK;
 }
 
-int launch_gather_out(const fdps_psys* ps, double* pos, double* vel, double* acc, double* pot) {
+int launch_gather_out(fdps_psys* ps, double* pos, double* vel, double* acc, double* pot) {
     fdps_ctx* ctx = ps->ctx;
     const int c = ps->cur;
-    k_gather_out<<<grid_for(ps->n, 256, ctx->sm_count * 16), 256, 0, ctx->stream>>>(
-        ps->n, ps->id[c], ps->x[c], ps->y[c], ps->z[c], ps->vx[c], ps->vy[c], ps->vz[c], ps->ax,
-        ps->ay, ps->az, ps->pot, pos, vel, acc, pot);
+    if (!ps->inv && dev_alloc(&ps->inv, ps->n) != cudaSuccess) {
+        cudaGetLastError();
+        ps->inv = nullptr;
+        return set_error(ctx, FDPS_ENOMEM, "inverse-order allocation failed");
+    }
+    const int grid = grid_for(ps->n, 256, ctx->sm_count * 16);
+    k_invert<<<grid, 256, 0, ctx->stream>>>(ps->n, ps->id[c], ps->inv);
+    FDPS_LAUNCH_CHECK(ctx);
+    k_gather_out<<<grid_for(ps->n, kIoTile, ctx->sm_count * 8), kIoTile, 0, ctx->stream>>>(ps->n, ps->inv, ps->x[c], ps->y[c], ps->z[c], ps->vx[c],
+                                                ps->vy[c], ps->vz[c], ps->ax, ps->ay, ps->az, ps->pot, pos, vel,
+                                                acc, pot);
     FDPS_LAUNCH_CHECK(ctx);
     return FDPS_OK;
 }

@@ -294,6 +294,47 @@ def test_device_pointer_roundtrip_and_order(G, ctx):
     ps.close()
 
 
+def test_page_locked_host_arrays_roundtrip(G, ctx):
+    """Page-locked host arrays are read and written by the device directly
+    (no staging copy); the results equal those of ordinary (pageable) host
+    arrays bit for bit, the caller's order comes back, and the same input
+    rules hold (NaN position, negative mass, zero eps rejected; -0.0 mass
+    accepted)."""
+    torch = pytest.importorskip("torch")
+    n = 100_003
+    pos, vel, mass, eps = ics.make("hernquist", n, 78, 0.01)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    tree = G.Tree(ctx, theta=0.5, n_leaf=16, n_grp=256, quad=True)
+    out = []
+    for wrap in (lambda a: a, pin):
+        ps = G.ParticleSystem(ctx, n)
+        ps.set(wrap(pos), wrap(vel), wrap(mass), wrap(eps))
+        tree.calc_force_all_and_write_back(ps)
+        p2, v2, a2, f2 = (wrap(np.full((n, 3), np.nan)), wrap(np.full((n, 3), np.nan)),
+                          wrap(np.full((n, 3), np.nan)), wrap(np.full(n, np.nan)))
+        G.fdps_psys_get(ctx.h, ps.h, p2, v2, a2, f2)
+        np.testing.assert_array_equal(p2, pos)
+        np.testing.assert_array_equal(v2, vel)
+        out.append((a2.copy(), f2.copy()))
+        ps.close()
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    tree.close()
+    ps = G.ParticleSystem(ctx, 8)
+    p8, v8, m8, e8 = (np.random.default_rng(3).normal(size=(8, 3)), np.zeros((8, 3)), np.ones(8),
+                      np.full(8, 0.1))
+    for k, bad in enumerate([("pos", np.nan), ("mass", -1.0), ("eps", 0.0), ("eps", -0.0)]):
+        a = {"pos": p8.copy(), "mass": m8.copy(), "eps": e8.copy()}
+        a[bad[0]].reshape(-1)[5] = bad[1]
+        with pytest.raises(G.FdpsError) as e:
+            ps.set(pin(a["pos"]), pin(v8), pin(a["mass"]), pin(a["eps"]))
+        assert e.value.code == G.FDPS_EINVAL
+    m0 = m8.copy()
+    m0[2] = -0.0
+    ps.set(pin(p8), pin(v8), pin(m0), pin(e8))
+    ps.close()
+
+
 def test_leapfrog_matches_oracle_integration(G, ctx):
     """Ten KDK steps of the GPU pipeline against ten oracle steps with the
     oracle tree (monopole); trajectories agree to the force tolerance."""
@@ -408,7 +449,7 @@ def test_shallow_tile_depth_matches_oracle(G, ctx, quad):
         ps.close()
 
 
-BLOCK_SHAPES = [(64, 2), (64, 4), (128, 2), (128, 4), (256, 2)]
+BLOCK_SHAPES = [(64, 2), (64, 4), (64, 5), (128, 2), (128, 4), (128, 5), (256, 2)]
 
 
 @pytest.mark.parametrize("block,ipt", BLOCK_SHAPES, ids=[f"{b}x{k}" for b, k in BLOCK_SHAPES])
@@ -437,7 +478,7 @@ def test_every_block_shape_matches_oracle(G, ctx, block, ipt, quad):
 
 
 def test_block_shape_rules(G, ctx):
-    for block, ipt in ((32, 4), (256, 4), (128, 3), (512, 2)):
+    for block, ipt in ((32, 4), (256, 4), (256, 5), (128, 3), (128, 6), (512, 2)):
         with pytest.raises(G.FdpsError):
             G.Tree(ctx, theta=0.5, n_leaf=8, n_grp=64, block=block, i_per_thread=ipt)
 
@@ -450,7 +491,7 @@ def test_autotuner_picks_a_candidate_and_keeps_parity(G, ctx):
     try:
         ps.set(pos, vel, mass, eps)
         best, ms = tree.autotune(ps, n_leaf=(4, 8), n_grp=(2, 32, 128), tile_depth=(256, 512),
-                                 block=(64, 128, 256), i_per_thread=(2, 4))
+                                 block=(64, 128, 256), i_per_thread=(2, 4, 5))
         assert best["n_leaf"] in (4, 8) and best["n_grp"] in (32, 128)  # n_grp 2 < n_leaf: skipped
         assert best["tile_depth"] in (256, 512) and best["theta"] == 0.6 and ms > 0
         assert (best["block"], best["i_per_thread"]) in BLOCK_SHAPES
