@@ -39,6 +39,7 @@ void free_particles(fdps_tree* t) {
     dev_free(t->bt_count);
     dev_free(t->coh_bkt);
     dev_free(t->coh_cnt);
+    t->cap_coh = 0;
     t->coh_ok = false;  // the last sorted keys are gone
     t->cap_n = 0;
     t->cap_tiles = 0;
@@ -55,6 +56,7 @@ int ensure_particles(fdps_tree* t, int64_t n) {
               dev_alloc(&t->sort_hist, 2 * 256 * tiles) == cudaSuccess &&
               dev_alloc(&t->bt_count, kMaxLevel * (kBuildWarps + 1) * (tiles + 1) + 32) == cudaSuccess &&
               dev_alloc(&t->coh_bkt, n) == cudaSuccess && dev_alloc(&t->coh_cnt, 3 * ((n + kCohT - 1) / kCohT + 1) + 8) == cudaSuccess;
+    t->cap_coh = ok ? 3 * ((n + kCohT - 1) / kCohT + 1) + 8 : 0;
     if (!ok) {
         cudaGetLastError();
         free_particles(t);
@@ -482,6 +484,9 @@ int fdps_psys_destroy(fdps_psys* ps) {
     dev_free(ps->d_order);
     dev_free(ps->d_sys);
     dev_free(ps->d_sys_red);
+    dev_free(ps->d_cbs);
+    dev_free(ps->d_cbsys);
+    dev_free(ps->d_csfb);
     delete ps;
     return FDPS_OK;
 }
@@ -1281,6 +1286,10 @@ int fdps_psys_set_systems(fdps_psys* ps, int32_t n_sys, const int64_t* offsets) 
     dev_free(ps->d_order);
     dev_free(ps->d_sys);
     dev_free(ps->d_sys_red);
+    dev_free(ps->d_cbs);
+    dev_free(ps->d_cbsys);
+    dev_free(ps->d_csfb);
+    ps->coh_nb = 0;
     ps->n_sys = 1;
     ps->max_sys_n = ps->n;
     ps->gen++;
@@ -1312,6 +1321,35 @@ int fdps_psys_set_systems(fdps_psys* ps, int32_t n_sys, const int64_t* offsets) 
                                        cudaMemcpyHostToDevice, ctx->stream));
     int rc = launch_sys_index(ps);
     if (rc) return rc;
+    // buckets of the coherent time-step sort: each system's positions in
+    // runs of kCohT (its last run ragged)
+    std::vector<uint32_t> cbs, cbsys, csfb(n_sys + 1);
+    for (int32_t k = 0; k < n_sys; ++k) {
+        csfb[k] = (uint32_t)cbs.size();
+        for (int64_t p = offsets[k]; p < offsets[k + 1]; p += kCohT) {
+            cbs.push_back((uint32_t)p);
+            cbsys.push_back((uint32_t)k);
+        }
+    }
+    csfb[n_sys] = (uint32_t)cbs.size();
+    const int64_t nbk = (int64_t)cbsys.size();
+    cbs.push_back((uint32_t)ps->n);
+    if (dev_alloc(&ps->d_cbs, nbk + 1) == cudaSuccess && dev_alloc(&ps->d_cbsys, nbk) == cudaSuccess &&
+        dev_alloc(&ps->d_csfb, (int64_t)n_sys + 1) == cudaSuccess) {
+        FDPS_CUDA_TRY(ctx, cudaMemcpyAsync(ps->d_cbs, cbs.data(), sizeof(uint32_t) * (nbk + 1),
+                                           cudaMemcpyHostToDevice, ctx->stream));
+        FDPS_CUDA_TRY(ctx, cudaMemcpyAsync(ps->d_cbsys, cbsys.data(), sizeof(uint32_t) * nbk,
+                                           cudaMemcpyHostToDevice, ctx->stream));
+        FDPS_CUDA_TRY(ctx, cudaMemcpyAsync(ps->d_csfb, csfb.data(), sizeof(uint32_t) * (n_sys + 1),
+                                           cudaMemcpyHostToDevice, ctx->stream));
+        ps->coh_nb = nbk;
+    } else {
+        // without the tables the ensemble keeps the radix sort
+        cudaGetLastError();
+        dev_free(ps->d_cbs);
+        dev_free(ps->d_cbsys);
+        dev_free(ps->d_csfb);
+    }
     FDPS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     return FDPS_OK;
 }

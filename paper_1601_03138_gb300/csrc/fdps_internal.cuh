@@ -144,6 +144,13 @@ struct fdps_psys {
     int64_t* d_off = nullptr;
     int32_t* d_order = nullptr;  // systems by decreasing particle count
     uint32_t* d_sys = nullptr;   // system of each position
+    // buckets of the coherent time-step sort (several systems): bucket b
+    // holds positions d_cbs[b] .. d_cbs[b + 1] - 1 of system d_cbsys[b];
+    // system k's buckets start at d_csfb[k]
+    uint32_t* d_cbs = nullptr;
+    uint32_t* d_cbsys = nullptr;
+    uint32_t* d_csfb = nullptr;
+    int64_t coh_nb = 0;
     double* d_sys_red = nullptr; // per-system energies (2 n_sys)
 };
 
@@ -178,6 +185,7 @@ struct fdps_tree {
     bool sort_coherent = false;    // the last call took the coherent sort
     uint32_t* coh_bkt = nullptr;   // bucket of every particle
     uint32_t* coh_cnt = nullptr;   // [nb] counts, [nb + 1] offsets, [nb] cursors, done word
+    int64_t cap_coh = 0;           // words of coh_cnt
     uint32_t* sort_hist = nullptr; // 2 x [tiles][256]: look-back words of the sort passes
     uint32_t* sort_dtot = nullptr; // [4096]: digit totals / bases of every pass, tile counters
     int64_t cap_tiles = 0;

@@ -509,24 +509,43 @@ constexpr int kCohWarps = kCohBlock / 32;
 constexpr int kCohNear = 2;   // buckets t - 2 .. t + 2 counted in shared memory
 static_assert(kCohT % kCohBlock == 0, "whole rounds per tile");
 
-// Splitter b (b >= 1) is prev[b kCohT]; the bucket of key k is the largest b
-// with splitter(b) <= k (splitter(0) = 0), starting from position tile t.
-__device__ __forceinline__ uint32_t coh_bucket(uint64_t k, uint32_t t, uint32_t nb,
-                                               const uint64_t* __restrict__ prev) {
-    const uint64_t lo = t == 0 ? 0ull : prev[(int64_t)t * kCohT];
-    const bool below_hi = t + 1 >= nb || k < prev[(int64_t)(t + 1) * kCohT];
+// Where the buckets lie: bucket b takes the positions [start(b), start(b +
+// 1)) of the previous order, of system sys(b); the buckets of system k are
+// first(k) .. first(k + 1) - 1 and never cross a system's segment (the
+// systems keep their segments from call to call).  One system: start(b) =
+// b kCohT (the last bucket ragged), no tables.
+struct CohLayout {
+    const uint32_t* start;  // [nb + 1], or null
+    const uint32_t* sys;    // [nb], or null (system 0)
+    const uint32_t* first;  // [n_sys + 1], or null ({0, nb})
+    uint32_t nb;
+    int64_t n;
+};
+__device__ __forceinline__ int64_t coh_start(const CohLayout& L, uint32_t b) {
+    if (L.start) return (int64_t)L.start[b];
+    const int64_t p = (int64_t)b * kCohT;
+    return p < L.n ? p : L.n;
+}
+
+// The splitter of bucket j (above its system's first bucket) is
+// prev[start(j)]; the bucket of key k in system buckets [j0, j1) is the
+// largest j with splitter(j) <= k (splitter(j0) = 0), starting from t.
+__device__ __forceinline__ uint32_t coh_bucket(uint64_t k, uint32_t t, uint32_t j0, uint32_t j1,
+                                               const uint64_t* __restrict__ prev, const CohLayout& L) {
+    const uint64_t lo = t == j0 ? 0ull : prev[coh_start(L, t)];
+    const bool below_hi = t + 1 >= j1 || k < prev[coh_start(L, t + 1)];
     if (k >= lo && below_hi) return t;
     uint32_t a, z;  // the answer lies in [a, z); splitter(a) <= k
     if (k < lo) {
-        a = 0;
+        a = j0;
         z = t;
     } else {
         a = t + 1;
-        z = nb;
+        z = j1;
     }
     while (z - a > 1) {
         const uint32_t mid = (a + z) >> 1;
-        if (prev[(int64_t)mid * kCohT] <= k)
+        if (prev[coh_start(L, mid)] <= k)
             a = mid;
         else
             z = mid;
@@ -534,14 +553,14 @@ __device__ __forceinline__ uint32_t coh_bucket(uint64_t k, uint32_t t, uint32_t 
     return a;
 }
 
-// Pass 1 (one block per tile of kCohT positions): Morton keys as k_keys,
-// the bucket of every key, bucket counts; the last block turns the counts
-// into offsets and cursors and flags a bucket above kCohCap.
-__global__ void __launch_bounds__(kCohBlock) k_coh_keys(int64_t n, const double* __restrict__ x,
+// Pass 1 (one block per bucket's positions, at most kCohT): Morton keys as
+// k_keys, the bucket of every key, bucket counts; the last block turns the
+// counts into offsets and cursors and flags a bucket above kCohCap.
+__global__ void __launch_bounds__(kCohBlock) k_coh_keys(CohLayout L, const double* __restrict__ x,
                                                         const double* __restrict__ y,
                                                         const double* __restrict__ z,
                                                         const SysBox* __restrict__ box,
-                                                        const uint64_t* __restrict__ prev, uint32_t nb,
+                                                        const uint64_t* __restrict__ prev,
                                                         uint64_t* __restrict__ keys, uint32_t* __restrict__ bkt,
                                                         uint32_t* cnt, uint32_t* off, uint32_t* cur,
                                                         uint32_t* done, uint32_t* err) {
@@ -549,19 +568,23 @@ __global__ void __launch_bounds__(kCohBlock) k_coh_keys(int64_t n, const double*
     __shared__ uint32_t s_max[kCohWarps];
     __shared__ bool s_last;
     const uint32_t t = blockIdx.x;
+    const uint32_t nb = L.nb;
     if (threadIdx.x < 2 * kCohNear + 1) s_near[threadIdx.x] = 0;
     __syncthreads();
-    const SysBox& b = box[0];
+    const int64_t p0 = coh_start(L, t), p1 = coh_start(L, t + 1);
+    const uint32_t sys = L.sys ? L.sys[t] : 0u;
+    const uint32_t j0 = L.first ? L.first[sys] : 0u, j1 = L.first ? L.first[sys + 1] : nb;
+    const SysBox& b = box[sys];
     const int lane = threadIdx.x & 31;
     for (int r = 0; r < kCohT / kCohBlock; ++r) {
-        const int64_t i = (int64_t)t * kCohT + r * kCohBlock + threadIdx.x;
+        const int64_t i = p0 + r * kCohBlock + threadIdx.x;
         int d = 0x7FFFFFFF;  // no particle
-        if (i < n) {
+        if (i < p1) {
             const uint32_t qx = quantise(x[i], b.lo[0], b.s), qy = quantise(y[i], b.lo[1], b.s),
                            qz = quantise(z[i], b.lo[2], b.s);
             const uint64_t k = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
             keys[i] = k;
-            const uint32_t bk = coh_bucket(k, t, nb, prev);
+            const uint32_t bk = coh_bucket(k, t, j0, j1, prev, L);
             bkt[i] = bk;
             d = (int)bk - (int)t;
             if (d < -kCohNear || d > kCohNear) atomicAdd(&cnt[bk], 1u);
@@ -626,25 +649,27 @@ __global__ void __launch_bounds__(kCohBlock) k_coh_keys(int64_t n, const double*
 // Pass 2: every (key, position) into its bucket; one atomic per block and
 // nearby bucket reserves the block's slots, far movers take one each.  The
 // order inside a bucket is arbitrary (pass 3 sorts by position too).
-__global__ void __launch_bounds__(kCohBlock) k_coh_scatter(int64_t n, const uint64_t* __restrict__ keys,
-                                                           const uint32_t* __restrict__ bkt, uint32_t nb,
+__global__ void __launch_bounds__(kCohBlock) k_coh_scatter(CohLayout L, const uint64_t* __restrict__ keys,
+                                                           const uint32_t* __restrict__ bkt,
                                                            uint32_t* cur, uint64_t* __restrict__ k2,
                                                            uint32_t* __restrict__ i2, const uint32_t* err) {
     constexpr int R = kCohT / kCohBlock;
     __shared__ uint32_t s_cnt[2 * kCohNear + 1], s_base[2 * kCohNear + 1];
     if (*err & kSortRedo) return;
     const uint32_t t = blockIdx.x;
+    const uint32_t nb = L.nb;
+    const int64_t p0 = coh_start(L, t), p1 = coh_start(L, t + 1);
     if (threadIdx.x < 2 * kCohNear + 1) s_cnt[threadIdx.x] = 0;
     __syncthreads();
     uint64_t kk[R];
     uint32_t bb[R], rank[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const int64_t i = (int64_t)t * kCohT + r * kCohBlock + threadIdx.x;
+        const int64_t i = p0 + r * kCohBlock + threadIdx.x;
         bb[r] = 0xFFFFFFFFu;
         rank[r] = 0xFFFFFFFFu;
         kk[r] = 0;
-        if (i < n) {
+        if (i < p1) {
             kk[r] = keys[i];
             bb[r] = bkt[i];
         }
@@ -674,7 +699,7 @@ __global__ void __launch_bounds__(kCohBlock) k_coh_scatter(int64_t n, const uint
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         if (bb[r] == 0xFFFFFFFFu) continue;
-        const int64_t i = (int64_t)t * kCohT + r * kCohBlock + threadIdx.x;
+        const int64_t i = p0 + r * kCohBlock + threadIdx.x;
         const uint32_t pos = rank[r] != 0xFFFFFFFFu ? s_base[(int)bb[r] - (int)t + kCohNear] + rank[r]
                                                     : atomicAdd(&cur[bb[r]], 1u);
         k2[pos] = kk[r];
@@ -1078,11 +1103,30 @@ int keys_and_sort(fdps_tree* t, fdps_psys* ps) {
     const int64_t n = ps->n;
     const int c = ps->cur;
     const int ntiles = (int)((n + kOsTile - 1) / kOsTile);
-    // the particles are in the order of this tree's last sort (same system,
-    // same data, moved by the caller since): the coherent sort
-    const bool coherent = ps->n_sys == 1 && t->coh_ok && t->coh_ps == ps && t->coh_gen == ps->gen &&
-                          t->coh_n == n && n >= 2 * (int64_t)kCohT;
-    t->coh_ok = ps->n_sys == 1;
+    // the particles are in the order of this tree's last sort (same
+    // particle system, same data, moved by the caller since): the coherent
+    // sort, with its bucket tables for several systems
+    const bool layout = ps->n_sys == 1 || ps->d_cbs;
+    const int64_t nbl = ps->n_sys == 1 ? (n + kCohT - 1) / kCohT : ps->coh_nb;
+    bool coherent = layout && t->coh_ok && t->coh_ps == ps && t->coh_gen == ps->gen && t->coh_n == n &&
+                    n >= 2 * (int64_t)kCohT;
+    if (coherent && 3 * nbl + 8 > t->cap_coh) {
+        // more buckets than particle tiles (many small systems): grow the
+        // counters, except inside a graph capture
+        if (ctx->capturing) {
+            coherent = false;
+        } else {
+            dev_free(t->coh_cnt);
+            t->cap_coh = 0;
+            if (dev_alloc(&t->coh_cnt, 3 * nbl + 8) != cudaSuccess) {
+                cudaGetLastError();
+                t->coh_cnt = nullptr;
+                return set_error(ctx, FDPS_ENOMEM, "coherent-sort counters allocation failed");
+            }
+            t->cap_coh = 3 * nbl + 8;
+        }
+    }
+    t->coh_ok = layout;
     t->coh_ps = ps;
     t->coh_gen = ps->gen;
     t->coh_n = n;
@@ -1097,18 +1141,24 @@ int keys_and_sort(fdps_tree* t, fdps_psys* ps) {
         FDPS_LAUNCH_CHECK(ctx);
     }
     if (coherent) {
-        const uint32_t nb = (uint32_t)((n + kCohT - 1) / kCohT);
+        CohLayout L;
+        L.start = ps->n_sys == 1 ? nullptr : ps->d_cbs;
+        L.sys = ps->n_sys == 1 ? nullptr : ps->d_cbsys;
+        L.first = ps->n_sys == 1 ? nullptr : ps->d_csfb;
+        L.nb = (uint32_t)nbl;
+        L.n = n;
+        const uint32_t nb = L.nb;
         uint32_t* cnt = t->coh_cnt;
         uint32_t* off = cnt + nb;       // nb + 1
         uint32_t* cur = off + nb + 1;   // nb
         uint32_t* done = cur + nb;
         FDPS_CUDA_TRY(ctx, cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (3 * (size_t)nb + 2), s));
         // the previous sorted keys (keys_b) are the splitters
-        k_coh_keys<<<nb, kCohBlock, 0, s>>>(n, ps->x[c], ps->y[c], ps->z[c], t->sys_box, t->keys_b, nb,
-                                             t->keys_in, t->coh_bkt, cnt, off, cur, done, &t->st->overflow);
+        k_coh_keys<<<nb, kCohBlock, 0, s>>>(L, ps->x[c], ps->y[c], ps->z[c], t->sys_box, t->keys_b, t->keys_in,
+                                             t->coh_bkt, cnt, off, cur, done, &t->st->overflow);
         FDPS_LAUNCH_CHECK(ctx);
         if (t->ev_ok && ctx->profiling && !ctx->capturing) cudaEventRecord(t->ev[1], s);
-        k_coh_scatter<<<nb, kCohBlock, 0, s>>>(n, t->keys_in, t->coh_bkt, nb, cur, t->keys_a, t->vals_a,
+        k_coh_scatter<<<nb, kCohBlock, 0, s>>>(L, t->keys_in, t->coh_bkt, cur, t->keys_a, t->vals_a,
                                                 &t->st->overflow);
         FDPS_LAUNCH_CHECK(ctx);
         k_coh_sort<<<nb, kCohBlock, sizeof(CohShared), s>>>(off, nb, t->keys_a, t->vals_a, t->keys_b, t->vals_b,

@@ -160,3 +160,56 @@ def test_coherent_sort_ties_keep_starting_order(G, ctx):
     finally:
         tree.close()
         ps.close()
+
+
+def test_coherent_sort_ensemble_keeps_systems_in_their_segments(G, ctx):
+    """Several systems (smaller than one bucket, exact multiples of it, and
+    ragged): the coherent sort's buckets never cross a system's segment, and
+    every call's permutation is the stable sort by (system, key); each
+    system's keys, nodes and groups are the oracle's on that system alone."""
+    sizes = [5000, 700, 3072, 1024, 2048, 9001, 300, 1500, 64]
+    rng = np.random.default_rng(ics.SEED_BASE + 65)
+    parts = [ics.make("plummer", m, ics.SEED_BASE + 66 + k, 0.02) for k, m in enumerate(sizes)]
+    pos = np.concatenate([p[0] * (1.0 + k) + rng.uniform(-5, 5, 3) for k, p in enumerate(parts)])
+    vel = np.concatenate([p[1] for p in parts])
+    mass = np.concatenate([p[2] for p in parts])
+    eps = np.concatenate([p[3] for p in parts])
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n = int(off[-1])
+    sys_of = np.repeat(np.arange(len(sizes)), sizes)
+    ps = G.ParticleSystem(ctx, n)
+    tree = G.Tree(ctx, theta=0.5, n_leaf=8, n_grp=64, quad=True)
+    try:
+        ps.set_systems(off)
+        ps.set(pos, vel, mass, eps)
+        tree.calc_force_all_and_write_back(ps)
+        assert tree.stats()["sort_coherent"] == 0  # the first call sorts from scratch
+        for _ in range(3):
+            tree.step(ps, 1.0 / 64.0)
+            assert tree.stats()["sort_coherent"] == 1
+            keys, perm = tree.keys(n)
+            want = np.lexsort((keys, sys_of)).astype(perm.dtype)  # stable: ties by position
+            np.testing.assert_array_equal(perm, want)
+        p_now, _ = ps.get_state()
+        nodes, groups = tree.nodes(), tree.groups()
+        node_sys = np.searchsorted(off, nodes["first"], side="right") - 1
+        grp_sys = np.searchsorted(off, groups["first"], side="right") - 1
+        for k in range(len(sizes)):
+            a, b = off[k], off[k + 1]
+            ref = oracle.Tree(p_now[a:b], mass[a:b], eps[a:b], theta=0.5, n_leaf=8, n_grp=64, quad=True)
+            kr, _ = ref.keys()
+            np.testing.assert_array_equal(np.sort(keys[a:b]), np.sort(kr))
+            nr = ref.nodes()
+            sel = np.nonzero(node_sys == k)[0]
+            assert len(sel) == ref.n_nodes
+            for f in ("level", "count", "nchild"):
+                np.testing.assert_array_equal(nodes[f][sel], nr[f], err_msg=f)
+            np.testing.assert_array_equal(nodes["first"][sel] - a, nr["first"])
+            np.testing.assert_array_equal(nodes["com"][sel], nr["com"])
+            gsel = np.nonzero(grp_sys == k)[0]
+            gr = ref.groups()
+            np.testing.assert_array_equal(groups["first"][gsel] - a, gr["first"])
+            np.testing.assert_array_equal(groups["count"][gsel], gr["count"])
+    finally:
+        tree.close()
+        ps.close()
