@@ -460,8 +460,7 @@ int fdps_user_law_destroy(fdps_user_law* law);
    thread; that error is left pending for the caller).  The work is queued
    on `stream` and not waited for.  The first call on a device, with that
    device current, looks up the scratch array's device address and keeps it
-   for the process; make that first call before any stream capture.  The
-   address belongs to the device's primary context (the one the CUDA
+   for the process.  The address belongs to the device's primary context (the one the CUDA
    runtime API uses): calls from other contexts, or after a cudaDeviceReset
    of the device, are not supported.  All calls on a device share the one
    scratch array, which keeps the last call's contents: calls that may
