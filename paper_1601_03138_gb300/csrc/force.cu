@@ -191,9 +191,11 @@ __device__ __forceinline__ void store_entries(uint32_t* dst, const uint32_t (&v)
         for (int r = 0; r < EPT; ++r) dst[r] = v[r];
 }
 
-// Largest e in [0, CE) with scan[e] <= item.
+// Largest e in [0, CE) with scan[e] <= item (binary lifting: CE a power of
+// two).
 template <int CE>
 __device__ __forceinline__ int owner_chunk(const uint32_t* scan, uint32_t item) {
+    static_assert(CE > 0 && (CE & (CE - 1)) == 0, "list chunks of a power-of-two length");
     int lo = 0;
 #pragma unroll
     for (int step = CE / 2; step > 0; step >>= 1)
