@@ -419,10 +419,21 @@ __global__ void __launch_bounds__(256) k_tree_finish(const DevState* __restrict_
 
 // ------------------------------------------------------------ moments
 
-__device__ __forceinline__ void split_hilo(double v, float* hi, float* lo) {
-    float h = __double2float_rn(v);
-    *hi = h;
-    *lo = __double2float_rn(v - (double)h);
+__device__ __forceinline__ void split_hilo(double v, float* hi, float* lo) { split_f32(v, *hi, *lo); }
+
+// S / M correctly rounded.  With one reciprocal y = RN(1/M) for a node's three
+// quotients, Markstein's correction q0 = RN(S y), r = S - M q0 (exact by a
+// fused multiply-add), q = RN(q0 + r y) gives RN(S / M) (Markstein 1990);
+// the exponent guards keep every intermediate a normal number, elsewhere
+// the division instruction sequence runs.
+__device__ __forceinline__ bool exp_mid(double v) {
+    const int e = (int)((__double_as_longlong(v) >> 52) & 0x7FF);
+    return e >= 200 && e <= 1850;
+}
+__device__ __forceinline__ double quot(double S, double M, double y, bool ok) {
+    if (!ok || !exp_mid(S)) return __ddiv_rn(S, M);  // zero, tiny or huge S: the division
+    const double q0 = __dmul_rn(S, y);
+    return __fma_rn(__fma_rn(-M, q0, S), y, q0);
 }
 
 struct MomArgs {
@@ -486,9 +497,11 @@ __device__ __forceinline__ void node_moments(const MomArgs& A, int64_t i) {
     }
     double cx = 0.0, cy = 0.0, cz = 0.0;
     if (M > 0.0) {
-        cx = __ddiv_rn(Sx, M);
-        cy = __ddiv_rn(Sy, M);
-        cz = __ddiv_rn(Sz, M);
+        const bool ok = exp_mid(M);
+        const double y = ok ? __ddiv_rn(1.0, M) : 0.0;
+        cx = quot(Sx, M, y, ok);
+        cy = quot(Sy, M, y, ok);
+        cz = quot(Sz, M, y, ok);
     }
     A.nd_sx[i] = Sx;
     A.nd_sy[i] = Sy;
@@ -498,7 +511,7 @@ __device__ __forceinline__ void node_moments(const MomArgs& A, int64_t i) {
     split_hilo(cx - bx.c0[0], &hx, &lx);
     split_hilo(cy - bx.c0[1], &hy, &ly);
     split_hilo(cz - bx.c0[2], &hz, &lz);
-    A.nd_f[2 * i] = make_float4(hx, hy, hz, __double2float_rn(M));
+    A.nd_f[2 * i] = make_float4(hx, hy, hz, to_f32(M));
     A.nd_f[2 * i + 1] = make_float4(lx, ly, lz, 0.0f);
     // walk record: (q_x | level << 21 | leaf << 26 | children << 27, q_y, q_z,
     // first child of an internal node or particle count of a leaf)

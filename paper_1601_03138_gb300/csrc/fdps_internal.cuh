@@ -83,6 +83,47 @@ struct DevState {
     int32_t max_level;
 };
 
+// FP64 -> FP32 conversions on the integer pipes (GB300's FP64 pipe is
+// narrow).  split_f32 gives hi = RN32(v) and lo = RN32(v - hi), the values
+// of __double2float_rn(v) and __double2float_rn(v - (double)hi): the 53-bit
+// significand rounded to nearest even at 24 bits, the remainder (exact in
+// the 29 dropped bits, as an integer) converted by one correctly rounded
+// int-to-float conversion and scaled by a power of two.  Values whose parts
+// would leave the FP32 normal range take the FP64 instructions.
+__device__ __forceinline__ void split_f32(double v, float& hi, float& lo) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (e < 949 || e > 1149) {
+        hi = __double2float_rn(v);
+        lo = __double2float_rn(v - (double)hi);
+        return;
+    }
+    const unsigned long long sig = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    unsigned int keep = (unsigned int)(sig >> 29);
+    const unsigned int rem = (unsigned int)(sig & 0x1FFFFFFFull);
+    const bool up = rem > 0x10000000u || (rem == 0x10000000u && (keep & 1u));
+    const int diff = (int)rem - (up ? 0x20000000 : 0);  // |v| - |hi| in units of 2^(e - 1075)
+    keep += up ? 1u : 0u;
+    int eh = e - 1023 + 127;
+    if (keep == (1u << 24)) {  // rounded up to the next power of two
+        keep >>= 1;
+        ++eh;
+    }
+    const unsigned int sgn = (unsigned int)(b >> 63) << 31;
+    hi = __uint_as_float(sgn | ((unsigned int)eh << 23) | (keep & 0x7FFFFFu));
+    if (diff == 0) {
+        lo = 0.0f;  // v - hi = +0
+        return;
+    }
+    const float p2 = __uint_as_float((unsigned int)(e - 1075 + 127) << 23);
+    lo = __uint_as_float(__float_as_uint(__fmul_rn(__int2float_rn(diff), p2)) ^ sgn);
+}
+__device__ __forceinline__ float to_f32(double v) {
+    float hi, lo;
+    split_f32(v, hi, lo);
+    return hi;
+}
+
 // Root box of one system: lo = per-axis minimum, L = largest extent (1 if
 // 0), s = 2^21 / L, c0 = lo + L/2 (origin of the FP32 hi/lo copies).
 struct SysBox {

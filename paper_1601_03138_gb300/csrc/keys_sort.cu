@@ -1078,11 +1078,12 @@ __global__ void __launch_bounds__(256) k_reorder(
         eps2[i] = pe;
         id2[i] = id[s];
         double rx = px - c0, ry = py - c1, rz = pz - c2;
-        float hx = __double2float_rn(rx), hy = __double2float_rn(ry), hz = __double2float_rn(rz);
-        float lx = __double2float_rn(rx - (double)hx), ly = __double2float_rn(ry - (double)hy),
-              lz = __double2float_rn(rz - (double)hz);
-        pf_hi[i] = make_float4(hx, hy, hz, __double2float_rn(pm));
-        pf_lo[i] = make_float4(lx, ly, lz, __double2float_rn(pe * pe));
+        float hx, hy, hz, lx, ly, lz;  // hi/lo parts, converted on the integer pipes
+        split_f32(rx, hx, lx);
+        split_f32(ry, hy, ly);
+        split_f32(rz, hz, lz);
+        pf_hi[i] = make_float4(hx, hy, hz, to_f32(pm));
+        pf_lo[i] = make_float4(lx, ly, lz, to_f32(pe * pe));
     }
 }
 
