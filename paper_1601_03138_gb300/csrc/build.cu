@@ -422,10 +422,10 @@ __global__ void __launch_bounds__(256) k_tree_finish(const DevState* __restrict_
 __device__ __forceinline__ void split_hilo(double v, float* hi, float* lo) { split_f32(v, *hi, *lo); }
 
 // S / M correctly rounded.  With one reciprocal y = RN(1/M) for a node's three
-// quotients, Markstein's correction q0 = RN(S y), r = S - M q0 (exact by a
-// fused multiply-add), q = RN(q0 + r y) gives RN(S / M) (Markstein 1990);
-// the exponent guards keep every intermediate a normal number, elsewhere
-// the division instruction sequence runs.
+// quotients, Markstein's correction q0 = RN(S y), r = RN(S - M q0) and
+// q = RN(q0 + r y), each step one fused multiply-add, gives RN(S / M)
+// (Markstein 1990); the exponent guards keep every intermediate a normal
+// number, elsewhere the division instruction sequence runs.
 __device__ __forceinline__ bool exp_mid(double v) {
     const int e = (int)((__double_as_longlong(v) >> 52) & 0x7FF);
     return e >= 200 && e <= 1850;
