@@ -168,8 +168,14 @@ int64_t fdps_psys_size(const fdps_psys* ps);
    vel3n are [n][3]; mass [n] >= 0; eps [n] > 0 (the softening of Eq.
    ParticleParticleNbody, eps_i of the receiving particle).  vel3n may be
    NULL (zero velocities).  Values are validated on the device: NaN/Inf,
-   negative mass or non-positive eps give FDPS_EINVAL.  Resets the
-   particle order to the caller's order.  on_device = 0: host arrays; the
+   negative mass or non-positive eps give FDPS_EINVAL.  The first data
+   after fdps_psys_create or fdps_psys_set_systems, and the call after a
+   rejected one, put the particles in the caller's order; later calls keep
+   the order the library holds them in (the last force calculation's
+   sorted order), so that a force calculation on data that moved little
+   starts from nearly sorted keys.  Row i always stays particle i; the
+   internal order only decides how equal Morton keys are broken
+   (fdps_tree_get_keys).  on_device = 0: host arrays; the
    device reads page-locked or managed host arrays directly (over the
    CPU-GPU link, no staging copy) and stages the others through device
    memory with copies.  The call returns after the data has been read, so

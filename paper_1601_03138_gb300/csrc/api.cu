@@ -480,6 +480,7 @@ int fdps_psys_destroy(fdps_psys* ps) {
     dev_free(ps->d_red);
     dev_free(ps->stage);
     dev_free(ps->inv);
+    dev_free(ps->rec);
     dev_free(ps->d_off);
     dev_free(ps->d_order);
     dev_free(ps->d_sys);
@@ -525,7 +526,11 @@ int fdps_psys_set(fdps_psys* ps, const double* pos3n, const double* vel3n, const
     cudaSetDevice(ctx->device);
     cudaStream_t s = ctx->stream;
     const int64_t n = ps->n;
-    ps->cur = 0;
+    // new data for particles the system already holds keeps their order
+    // (the last force calculation's), so that the next sort starts close to
+    // sorted; the first data after creation, after set_systems or after a
+    // rejected set take the caller's order
+    const bool keep = ps->has_data;
     ps->has_data = false;
     ps->has_forces = false;
     uint32_t bad = 0;
@@ -534,11 +539,11 @@ int fdps_psys_set(fdps_psys* ps, const double* pos3n, const double* vel3n, const
     const double* vm = on_device ? nullptr : device_view(mass);
     const double* ve = on_device ? nullptr : device_view(eps);
     if (on_device) {
-        int rc = launch_scatter_in(ps, pos3n, vel3n, mass, eps, &bad);
+        int rc = launch_scatter_in(ps, pos3n, vel3n, mass, eps, keep, &bad);
         if (rc) return rc;
     } else if (vp && vm && ve && (!vel3n || vv)) {
         // the device reads the caller's buffers over the link
-        int rc = launch_scatter_in(ps, vp, vel3n ? vv : nullptr, vm, ve, &bad);
+        int rc = launch_scatter_in(ps, vp, vel3n ? vv : nullptr, vm, ve, keep, &bad);
         if (rc) return rc;
     } else {
         // host data is staged in the psys's transfer buffer
@@ -560,7 +565,7 @@ int fdps_psys_set(fdps_psys* ps, const double* pos3n, const double* vel3n, const
         if (e1 || e2 || e3 || e4)
             rc = set_error(ctx, FDPS_ECUDA, "host to device copy failed");
         else
-            rc = launch_scatter_in(ps, st_pos, vel3n ? st_vel : nullptr, st_m, st_e, &bad);
+            rc = launch_scatter_in(ps, st_pos, vel3n ? st_vel : nullptr, st_m, st_e, keep, &bad);
         cudaStreamSynchronize(s);
         if (rc) return rc;
     }
@@ -569,7 +574,7 @@ int fdps_psys_set(fdps_psys* ps, const double* pos3n, const double* vel3n, const
                          (bad & 1) ? " non-finite position" : "", (bad & 2) ? " non-finite velocity" : "",
                          (bad & 4) ? " negative or non-finite mass" : "",
                          (bad & 8) ? " non-positive or non-finite eps" : "");
-    ps->gen++;
+    if (!keep) ps->gen++;  // the order changed: the last sorted keys no longer apply
     ps->has_data = true;
     return FDPS_OK;
 }

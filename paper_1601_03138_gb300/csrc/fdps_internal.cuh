@@ -178,6 +178,7 @@ struct fdps_psys {
     double* d_red = nullptr;     // reduction scratch (energy)
     double* stage = nullptr;     // host-transfer staging (10 n doubles, on first use)
     uint32_t* inv = nullptr;     // inverse of the current order (on first use)
+    double* rec = nullptr;       // [n][8] records of new data in the current order (on first use)
     // independent systems: positions off[k] .. off[k+1] belong to system k;
     // with one system d_off and d_sys stay null
     int32_t n_sys = 1;
@@ -374,9 +375,11 @@ int launch_kick_guarded(fdps_psys* ps, double dt_half, const uint32_t* flags, ui
 int launch_drift(fdps_psys* ps, double dt);            // integrate.cu
 int launch_kick_drift(fdps_psys* ps, double dt_half, double dt);  // integrate.cu
 int launch_energy(fdps_psys* ps, double* kin, double* pot);  // integrate.cu
-// caller-order input into the current buffers, validated (*bad: flag bits)
+// caller-order input into the current buffers, validated (*bad: flag bits);
+// keep_order: caller row i goes to the position the current order holds it
+// at (id unchanged), else to position i (id = identity)
 int launch_scatter_in(fdps_psys* ps, const double* pos, const double* vel,
-                      const double* mass, const double* eps, uint32_t* bad);  // integrate.cu
+                      const double* mass, const double* eps, bool keep_order, uint32_t* bad);  // integrate.cu
 // current buffers and results out in the caller's order
 int launch_gather_out(fdps_psys* ps, double* pos, double* vel,
                       double* acc, double* pot);       // integrate.cu

@@ -39,13 +39,20 @@ __device__ __forceinline__ void store_rows3(double* a, int64_t base, int m, cons
 // Caller-order input arrays (device memory, or host memory the device can
 // read) into the structure-of-arrays buffers, checked on the way: flag bit
 // 1 a non-finite position, 2 a non-finite velocity, 4 a negative or
-// non-finite mass, 8 a non-positive or non-finite softening.
+// non-finite mass, 8 a non-positive or non-finite softening.  Caller row i
+// goes to position inv[i] (the order the buffers already hold; the caller
+// arrays are still read contiguously), or with inv null to position i with
+// id[i] = i.  With inv, a record buffer rec (64 bytes a particle) takes the
+// particle's eight values as one record at position inv[i] (whole 32-byte
+// sectors, where scattered 8-byte writes into eight arrays would each
+// rewrite part of a sector); k_rec_split then fills the arrays in order.
 __global__ void __launch_bounds__(kIoTile) k_scatter_in(int64_t n, const double* __restrict__ pos,
                                                         const double* __restrict__ vel,
                                                         const double* __restrict__ mass,
                                                         const double* __restrict__ eps, double* x,
                                                         double* y, double* z, double* vx, double* vy,
                                                         double* vz, double* m, double* e, uint32_t* id,
+                                                        const uint32_t* __restrict__ inv, double2* rec,
                                                         uint32_t* flag) {
     __shared__ double s_p[3 * kIoTile], s_v[3 * kIoTile];
     uint32_t bad = 0;
@@ -65,20 +72,47 @@ __global__ void __launch_bounds__(kIoTile) k_scatter_in(int64_t n, const double*
             bad |= (finite64(ux) && finite64(uy) && finite64(uz)) ? 0u : 2u;
             bad |= (finite64(mi) && nonneg64(mi)) ? 0u : 4u;
             bad |= (finite64(ei) && positive64(ei)) ? 0u : 8u;
-            x[i] = px;
-            y[i] = py;
-            z[i] = pz;
-            vx[i] = ux;
-            vy[i] = uy;
-            vz[i] = uz;
-            m[i] = mi;
-            e[i] = ei;
-            id[i] = (uint32_t)i;
+            const int64_t d = inv ? (int64_t)inv[i] : i;
+            if (rec) {
+                double2* r = rec + 4 * d;
+                r[0] = make_double2(px, py);
+                r[1] = make_double2(pz, ux);
+                r[2] = make_double2(uy, uz);
+                r[3] = make_double2(mi, ei);
+            } else {
+                x[d] = px;
+                y[d] = py;
+                z[d] = pz;
+                vx[d] = ux;
+                vy[d] = uy;
+                vz[d] = uz;
+                m[d] = mi;
+                e[d] = ei;
+            }
+            if (!inv) id[i] = (uint32_t)i;
         }
         __syncthreads();  // the tiles are rewritten next round
     }
     bad = __reduce_or_sync(0xFFFFFFFFu, bad);
     if ((threadIdx.x & 31) == 0 && bad) atomicOr(flag, bad);
+}
+
+// Records (x, y, z, vx, vy, vz, m, eps) in position order into the arrays.
+__global__ void __launch_bounds__(256) k_rec_split(int64_t n, const double2* __restrict__ rec, double* x,
+                                                   double* y, double* z, double* vx, double* vy, double* vz,
+                                                   double* m, double* e) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const double2 a = rec[4 * j], b = rec[4 * j + 1], c = rec[4 * j + 2], d = rec[4 * j + 3];
+        x[j] = a.x;
+        y[j] = a.y;
+        z[j] = b.x;
+        vx[j] = b.y;
+        vy[j] = c.x;
+        vz[j] = c.y;
+        m[j] = d.x;
+        e[j] = d.y;
+    }
 }
 
 // Inverse of the current order: inv[caller index] = position.
@@ -320,14 +354,36 @@ int launch_energy_systems(fdps_psys* ps, double* kin, double* pot) {
 int energy_scratch_doubles() { return 2 * kEnergyBlocks + 2; }
 
 int launch_scatter_in(fdps_psys* ps, const double* pos, const double* vel, const double* mass,
-                      const double* eps, uint32_t* bad) {
+                      const double* eps, bool keep_order, uint32_t* bad) {
     fdps_ctx* ctx = ps->ctx;
+    if (!keep_order) ps->cur = 0;
     const int c = ps->cur;
+    if (keep_order) {
+        if (!ps->inv && dev_alloc(&ps->inv, ps->n) != cudaSuccess) {
+            cudaGetLastError();
+            ps->inv = nullptr;
+            return set_error(ctx, FDPS_ENOMEM, "inverse-order allocation failed");
+        }
+        k_invert<<<grid_for(ps->n, 256, ctx->sm_count * 16), 256, 0, ctx->stream>>>(ps->n, ps->id[c], ps->inv);
+        FDPS_LAUNCH_CHECK(ctx);
+        // without the record buffer the values are written straight into
+        // the arrays (scattered 8-byte writes, slower)
+        if (!ps->rec && dev_alloc(&ps->rec, 8 * ps->n) != cudaSuccess) {
+            cudaGetLastError();
+            ps->rec = nullptr;
+        }
+    }
+    double2* rec = keep_order ? reinterpret_cast<double2*>(ps->rec) : nullptr;
     FDPS_CUDA_TRY(ctx, cudaMemsetAsync(ps->d_flag, 0, sizeof(uint32_t), ctx->stream));
     k_scatter_in<<<grid_for(ps->n, kIoTile, ctx->sm_count * 8), kIoTile, 0, ctx->stream>>>(
         ps->n, pos, vel, mass, eps, ps->x[c], ps->y[c], ps->z[c], ps->vx[c], ps->vy[c], ps->vz[c],
-        ps->m[c], ps->eps[c], ps->id[c], ps->d_flag);
+        ps->m[c], ps->eps[c], ps->id[c], keep_order ? ps->inv : nullptr, rec, ps->d_flag);
     FDPS_LAUNCH_CHECK(ctx);
+    if (rec) {
+        k_rec_split<<<grid_for(ps->n, 256, ctx->sm_count * 16), 256, 0, ctx->stream>>>(
+            ps->n, rec, ps->x[c], ps->y[c], ps->z[c], ps->vx[c], ps->vy[c], ps->vz[c], ps->m[c], ps->eps[c]);
+        FDPS_LAUNCH_CHECK(ctx);
+    }
     FDPS_CUDA_TRY(ctx, cudaMemcpyAsync(bad, ps->d_flag, sizeof(uint32_t), cudaMemcpyDeviceToHost,
                                        ctx->stream));
     FDPS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));

@@ -213,3 +213,41 @@ def test_coherent_sort_ensemble_keeps_systems_in_their_segments(G, ctx):
     finally:
         tree.close()
         ps.close()
+
+
+def test_set_keeps_the_order_for_the_coherent_sort(G, ctx):
+    """New data for the particles of a system keeps the order the library
+    holds them in: after positions that moved a little the next force
+    calculation takes the coherent sort, and with distinct keys (one sorted
+    order) its results equal a fresh system's on the same data bit for bit;
+    so do the results after unrelated data (another distribution) on the
+    same system.  The caller's rows come back in place."""
+    n = 100_003
+    pos, vel, mass, eps = ics.make("plummer", n, ics.SEED_BASE + 67, 0.01)
+    ps, tree = _setup(G, ctx, pos, vel, mass, eps, quad=True)
+    pos3, vel3, mass3, eps3 = ics.make("hernquist", n, ics.SEED_BASE + 68, 0.02)
+    try:
+        for new, coherent in (((pos + vel / 256.0, vel, mass, eps), True), ((pos3, vel3, mass3, eps3), None)):
+            ps.set(*new)
+            tree.calc_force_all_and_write_back(ps)
+            if coherent:
+                assert tree.stats()["sort_coherent"] == 1
+            keys, _ = _check_sorted(tree, n)
+            assert len(np.unique(keys)) == n
+            p, v, acc, pot = ps.get()
+            np.testing.assert_array_equal(p, new[0])
+            np.testing.assert_array_equal(v, new[1])
+            fresh, ftree = _setup(G, ctx, *new, quad=True)
+            try:
+                _, _, acc_f, pot_f = fresh.get()
+                np.testing.assert_array_equal(acc, acc_f)
+                np.testing.assert_array_equal(pot, pot_f)
+                nd, nf = tree.nodes(), ftree.nodes()
+                for k in ("level", "first", "count", "com"):
+                    np.testing.assert_array_equal(nd[k], nf[k], err_msg=k)
+            finally:
+                ftree.close()
+                fresh.close()
+    finally:
+        tree.close()
+        ps.close()
