@@ -79,6 +79,9 @@ def parse():
                     help="one JSON line per workload configuration: Plummer 2^20 (10 steps), "
                          "Hernquist 2^24 at theta 0.3/0.5/0.7, clumpy 2^26; with force errors "
                          "against the FP64 direct sum on a random subsample and energy drift")
+    ap.add_argument("--largest", action="store_true",
+                    help="the clumpy mixture at the largest particle count that fits the device "
+                         "(one JSON line: throughput, force error, drift, bytes per particle)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep n_leaf / n_grp as given instead of the autotuner's choice")
     return ap.parse_args()
@@ -629,7 +632,7 @@ def run_ensemble(args, rank=0, world=1, local_rank=0):
 
 
 def run_config(G, torch, name, model, n, eps, theta, quad, n_leaf, n_grp, steps, dt, n_direct,
-               autotune, fp64_step, seed):
+               autotune, fp64_step, seed, tile_depth=0, extra=None):
     """One configuration: time `steps` graph-replayed KDK steps, force error of
     the first force calculation against the FP64 direct sum on n_direct random
     particles (oracle), relative energy drift over the run."""
@@ -640,7 +643,7 @@ def run_config(G, torch, name, model, n, eps, theta, quad, n_leaf, n_grp, steps,
     ctx.set_profiling(True)
     stream = torch.cuda.ExternalStream(ctx.stream)
     ps = G.ParticleSystem(ctx, n)
-    tree = G.Tree(ctx, theta=theta, n_leaf=n_leaf, n_grp=n_grp, quad=quad)
+    tree = G.Tree(ctx, theta=theta, n_leaf=n_leaf, n_grp=n_grp, quad=quad, tile_depth=tile_depth)
     ps.set(pos, vel, mass, e)
     tuned = None
     if autotune:
@@ -678,6 +681,13 @@ def run_config(G, torch, name, model, n, eps, theta, quad, n_leaf, n_grp, steps,
                                       "oracle_direct_s": round(t_direct, 1)},
             "energy": {"E0": ek0 + ep0, "rel_drift": abs((ek1 + ep1) - (ek0 + ep0)) / abs(ek0 + ep0)},
             "n_nodes": st0["n_nodes"], "n_groups": st0["n_groups"], "fp64_fallbacks": st0["fp64_fallbacks"]}
+    # the force kernel against the FP32 peak, on the algorithmic count
+    pk, pk_kind = peaks()
+    sm_count = torch.cuda.get_device_properties(0).multi_processor_count
+    peak_ops = sm_count * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6
+    alg = st0["interactions_epj"] * ALG_EPJ + st0["interactions_spj"] * (ALG_SPJ_QUAD if quad else ALG_SPJ_MONO)
+    line["force_frac_algorithmic"] = alg / (st0["ms_force"] / 1e3) / peak_ops
+    line.update(extra or {})
     tree.close()
     ps.close()
     if fp64_step:
@@ -780,6 +790,70 @@ def run_theta_target(args):
     ctx.close()
 
 
+def host_memory_available():
+    """Bytes of host memory this process may still use: MemAvailable, and
+    below the cgroup's limit where one is set."""
+    with open("/proc/meminfo") as f:
+        avail = next(int(l.split()[1]) * 1024 for l in f if l.startswith("MemAvailable"))
+    for lim, cur in (("/sys/fs/cgroup/memory.max", "/sys/fs/cgroup/memory.current"),
+                     ("/sys/fs/cgroup/memory/memory.limit_in_bytes",
+                      "/sys/fs/cgroup/memory/memory.usage_in_bytes")):
+        try:
+            with open(lim) as f:
+                v = f.read().strip()
+            with open(cur) as f:
+                u = int(f.read().strip())
+        except (OSError, ValueError):
+            continue
+        if v.isdigit():
+            avail = min(avail, int(v) - u)
+    return avail
+
+
+def run_largest(args):
+    """The clumpy mixture (1000 Plummer clumps, 20 % background, eps 0.002,
+    theta 0.5 quadrupole) at the largest particle count that fits the
+    device: the library's device bytes per particle are measured on a 2^25
+    clumpy set (every buffer at its grown size after one force calculation),
+    raised by 10 % for the longer lists of a larger set, and N is the
+    multiple of 2^20 that fills 80 % of the free device memory with that
+    (capped so that the run's host arrays, about 150 bytes a particle at
+    their peak, stay well within the available host memory).  n_leaf 16, n_grp 256, tile depth 512 (the
+    autotuner's pick at 2^26); two graph-replayed steps."""
+    import torch
+    import ics
+    import paper_1601_03138_gb300 as G
+    from paper_1601_03138_gb300 import build as B
+    B.build()
+    S = ics.SEED_BASE
+    n0 = 1 << 25
+    pos, vel, mass, e = ics.make("clumpy", n0, S + 4, 0.002)
+    torch.cuda.init()
+    free0, total = torch.cuda.mem_get_info(0)
+    ctx = G.Context(0)
+    ps = G.ParticleSystem(ctx, n0)
+    tree = G.Tree(ctx, theta=0.5, n_leaf=16, n_grp=256, quad=True, tile_depth=512)
+    ps.set(pos, vel, mass, e)
+    tree.calc_force_all_and_write_back(ps)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info(0)
+    tree.close()
+    ps.close()
+    ctx.close()
+    del pos, vel, mass, e
+    bpp = (free0 - free1) / n0
+    n_dev = int(0.8 * free0 / (1.1 * bpp))
+    avail = host_memory_available()
+    n_host = int(0.6 * avail / 300)  # the run's host arrays peak near 150 bytes a particle
+    n = min(n_dev, n_host, 0x7FFFFFFF) >> 20 << 20
+    extra = {"largest": {"device_bytes_per_particle_at_2^25": round(bpp, 1),
+                         "device_free_gb": round(free0 / 1e9, 1), "device_total_gb": round(total / 1e9, 1),
+                         "n_device_limit": n_dev, "n_host_limit": n_host,
+                         "host_available_gb": round(avail / 1e9, 1)}}
+    run_config(G, torch, "clumpy-largest", "clumpy", n, 0.002, 0.5, True, 16, 256, 2, 1.0 / 512.0,
+               256, False, False, S + 4, tile_depth=512, extra=extra)
+
+
 def run_suite(args):
     import torch
     import ics
@@ -821,6 +895,10 @@ def main():
     if args.sph:
         if rank == 0:
             run_sph(args)
+        return
+    if args.largest:
+        if rank == 0:
+            run_largest(args)
         return
     if args.theta_target is not None:
         if rank == 0:
