@@ -93,7 +93,7 @@ def parse():
 # bench reports null once that source has changed
 FORCE_TRAFFIC = {
     "hernquist N=16777216 theta=0.5 quad n_leaf=16 n_grp=256 eps=0.005 dt=0.00195312":
-        ("ff0181d4bf5361b3", 4.2481e9 + 532.41e6),
+        ("80cf8cab93dcebe0", 4.2531e9 + 532.69e6),
 }
 
 

@@ -237,11 +237,6 @@ __device__ __forceinline__ f2 f2_pk(float lo, float hi) {
 __device__ __forceinline__ void f2_up(f2 v, float& lo, float& hi) {
     asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
 }
-__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
-    f2 d;
-    asm("add.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
 __device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
     f2 d;
     asm("sub.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
@@ -565,8 +560,12 @@ __device__ __forceinline__ void force_group(const ForceArgs& A, uint32_t g, F32S
     constexpr int kCE = F32Shared<QUAD, EPT, CB, KMAX>::kCE;
     SpjBuf<QUAD> sb;
     sb.s0 = reinterpret_cast<float4*>(sm.u);
-    sb.s1 = reinterpret_cast<float4*>(sm.u + kCE * 16);
-    sb.s2 = reinterpret_cast<float2*>(sm.u + kCE * 32);
+    sb.s1 = nullptr;  // a monopole chunk holds the first array only
+    sb.s2 = nullptr;
+    if constexpr (QUAD) {
+        sb.s1 = reinterpret_cast<float4*>(sm.u + kCE * 16);
+        sb.s2 = reinterpret_cast<float2*>(sm.u + kCE * 32);
+    }
     const uint32_t ni = A.g_count[g], gf = A.g_first[g];
     const unsigned long long off = A.g_off[g];
     const uint32_t len = A.g_len[g];
