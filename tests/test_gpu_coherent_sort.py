@@ -210,6 +210,25 @@ def test_coherent_sort_ensemble_keeps_systems_in_their_segments(G, ctx):
             gr = ref.groups()
             np.testing.assert_array_equal(groups["first"][gsel] - a, gr["first"])
             np.testing.assert_array_equal(groups["count"][gsel], gr["count"])
+        # new data for the same systems keeps the order: the next call is
+        # coherent and equals a fresh ensemble's on the same data
+        p_new = p_now + 1e-3 * rng.normal(size=p_now.shape)
+        ps.set(p_new, vel, mass, eps)
+        tree.calc_force_all_and_write_back(ps)
+        assert tree.stats()["sort_coherent"] == 1
+        _, _, acc, pot = ps.get()
+        fresh = G.ParticleSystem(ctx, n)
+        ftree = G.Tree(ctx, theta=0.5, n_leaf=8, n_grp=64, quad=True)
+        try:
+            fresh.set_systems(off)
+            fresh.set(p_new, vel, mass, eps)
+            ftree.calc_force_all_and_write_back(fresh)
+            _, _, acc_f, pot_f = fresh.get()
+            np.testing.assert_array_equal(acc, acc_f)
+            np.testing.assert_array_equal(pot, pot_f)
+        finally:
+            ftree.close()
+            fresh.close()
     finally:
         tree.close()
         ps.close()
@@ -248,6 +267,25 @@ def test_set_keeps_the_order_for_the_coherent_sort(G, ctx):
             finally:
                 ftree.close()
                 fresh.close()
+        # device arrays take the same path
+        torch = pytest.importorskip("torch")
+        pos4 = new[0] + new[1] / 256.0
+        dev = [torch.tensor(a, device="cuda", dtype=torch.float64).contiguous()
+               for a in (pos4, new[1], new[2], new[3])]
+        torch.cuda.synchronize()
+        ps.set(*dev)
+        tree.calc_force_all_and_write_back(ps)
+        assert tree.stats()["sort_coherent"] == 1
+        p, _, acc, pot = ps.get()
+        np.testing.assert_array_equal(p, pos4)
+        fresh, ftree = _setup(G, ctx, pos4, new[1], new[2], new[3], quad=True)
+        try:
+            _, _, acc_f, pot_f = fresh.get()
+            np.testing.assert_array_equal(acc, acc_f)
+            np.testing.assert_array_equal(pot, pot_f)
+        finally:
+            ftree.close()
+            fresh.close()
     finally:
         tree.close()
         ps.close()
