@@ -118,8 +118,8 @@ STAGE_BYTES = {
     # index), passes 1-7 read and write (key, index)
     "ms_sort": (8 + 12 + 7 * 24, 0),
     # permutation and 8 FP64 fields + id gathered, written in key order,
-    # FP32 hi/lo copies written
-    "ms_permute": (4 + 64 + 4 + 64 + 4 + 32, 0),
+    # FP32 hi/lo copies and the three products m x written
+    "ms_permute": (4 + 64 + 4 + 64 + 4 + 32 + 24, 0),
     # sorted keys, per-position first differing level and leaf level; node
     # records written
     "ms_build": (16 + 4, 37),

@@ -34,6 +34,9 @@ void free_particles(fdps_tree* t) {
     dev_free(t->vals_b);
     dev_free(t->pf_hi);
     dev_free(t->pf_lo);
+    dev_free(t->pmx);
+    dev_free(t->pmy);
+    dev_free(t->pmz);
     dev_free(t->head);
     dev_free(t->sort_hist);
     dev_free(t->bt_count);
@@ -53,6 +56,8 @@ int ensure_particles(fdps_tree* t, int64_t n) {
               dev_alloc(&t->keys_b, n) == cudaSuccess && dev_alloc(&t->vals_a, n) == cudaSuccess &&
               dev_alloc(&t->vals_b, n) == cudaSuccess && dev_alloc(&t->pf_hi, n) == cudaSuccess &&
               dev_alloc(&t->pf_lo, n) == cudaSuccess && dev_alloc(&t->head, n) == cudaSuccess &&
+              dev_alloc(&t->pmx, n) == cudaSuccess && dev_alloc(&t->pmy, n) == cudaSuccess &&
+              dev_alloc(&t->pmz, n) == cudaSuccess &&
               dev_alloc(&t->sort_hist, 2 * 256 * tiles) == cudaSuccess &&
               dev_alloc(&t->bt_count, kMaxLevel * (kBuildWarps + 1) * (tiles + 1) + 32) == cudaSuccess &&
               dev_alloc(&t->coh_bkt, n) == cudaSuccess && dev_alloc(&t->coh_cnt, 3 * ((n + kCohT - 1) / kCohT + 1) + 8) == cudaSuccess;

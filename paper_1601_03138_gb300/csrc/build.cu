@@ -444,6 +444,9 @@ struct MomArgs {
     const double* py;
     const double* pz;
     const double* pm;
+    const double* pmx;  // m x, m y, m z per particle, each product rounded once
+    const double* pmy;
+    const double* pmz;
     const float4* pf_hi;
     const float4* pf_lo;
     const uint32_t* nd_first;
@@ -467,8 +470,11 @@ struct MomArgs {
 
 // Moments of node i, whose children (if any) are complete.  M and S = sum
 // m x in FP64 with every operation rounded on its own: leaves sequentially
-// over their particles, internal nodes over their children in octant
-// order.  Quadrupole: FP64 (Q64) for the FP64 pipeline; otherwise FP32 from
+// over their particles (the products m x come rounded from the reorder,
+// where every lane has a particle; a lane here sums one leaf of up to
+// n_leaf particles, so its multiplications would idle the lanes of the
+// warp's smaller leaves on the narrow FP64 pipe), internal nodes over their
+// children in octant order.  Quadrupole: FP64 (Q64) for the FP64 pipeline; otherwise FP32 from
 // positions relative to the node's COM formed from FP32 hi/lo pairs, and the
 // parallel-axis shift for internal nodes.
 template <bool QUAD, bool Q64>
@@ -481,11 +487,10 @@ __device__ __forceinline__ void node_moments(const MomArgs& A, int64_t i) {
     double M = 0.0, Sx = 0.0, Sy = 0.0, Sz = 0.0;
     if (leaf) {
         for (uint32_t p = f; p < f + cnt; ++p) {
-            const double m = A.pm[p];
-            M = __dadd_rn(M, m);
-            Sx = __dadd_rn(Sx, __dmul_rn(m, A.px[p]));
-            Sy = __dadd_rn(Sy, __dmul_rn(m, A.py[p]));
-            Sz = __dadd_rn(Sz, __dmul_rn(m, A.pz[p]));
+            M = __dadd_rn(M, A.pm[p]);
+            Sx = __dadd_rn(Sx, A.pmx[p]);
+            Sy = __dadd_rn(Sy, A.pmy[p]);
+            Sz = __dadd_rn(Sz, A.pmz[p]);
         }
     } else {
         for (uint32_t c = c0; c < c0 + nc; ++c) {
@@ -908,6 +913,9 @@ int compute_moments(fdps_tree* t, fdps_psys* ps) {
     A.py = ps->y[c];
     A.pz = ps->z[c];
     A.pm = ps->m[c];
+    A.pmx = t->pmx;
+    A.pmy = t->pmy;
+    A.pmz = t->pmz;
     A.pf_hi = t->pf_hi;
     A.pf_lo = t->pf_lo;
     A.nd_first = t->nd_first;

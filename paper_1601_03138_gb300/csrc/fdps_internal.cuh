@@ -233,6 +233,9 @@ struct fdps_tree {
     int64_t cap_tiles = 0;
     float4* pf_hi = nullptr;       // (x_hi, y_hi, z_hi, m) relative to c0
     float4* pf_lo = nullptr;       // (x_lo, y_lo, z_lo, eps^2)
+    double* pmx = nullptr;         // m x, m y, m z of the sorted particles, each product rounded
+    double* pmy = nullptr;         // once (the terms of the centre-of-mass sums, computed where
+    double* pmz = nullptr;         // every lane has a particle)
     uint32_t* head = nullptr;      // per particle: group node starting here (tree build scratch before)
     uint32_t* bt_count = nullptr;  // tree build: per-warp node counts of each level, level totals
     // nodes

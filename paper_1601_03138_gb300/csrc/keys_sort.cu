@@ -1060,7 +1060,8 @@ __global__ void __launch_bounds__(256) k_reorder(
     double* __restrict__ x2, double* __restrict__ y2, double* __restrict__ z2,
     double* __restrict__ vx2, double* __restrict__ vy2, double* __restrict__ vz2,
     double* __restrict__ m2, double* __restrict__ eps2, uint32_t* __restrict__ id2,
-    float4* __restrict__ pf_hi, float4* __restrict__ pf_lo) {
+    float4* __restrict__ pf_hi, float4* __restrict__ pf_lo, double* __restrict__ mx2, double* __restrict__ my2,
+    double* __restrict__ mz2) {
     const bool sorted = !(st->overflow & kSortInvalid);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -1084,6 +1085,9 @@ __global__ void __launch_bounds__(256) k_reorder(
         split_f32(rz, hz, lz);
         pf_hi[i] = make_float4(hx, hy, hz, to_f32(pm));
         pf_lo[i] = make_float4(lx, ly, lz, to_f32(pe * pe));
+        mx2[i] = __dmul_rn(pm, px);
+        my2[i] = __dmul_rn(pm, py);
+        mz2[i] = __dmul_rn(pm, pz);
     }
 }
 
@@ -1260,7 +1264,7 @@ int reorder_particles(fdps_tree* t, fdps_psys* ps) {
     k_reorder<<<grid, 256, 0, ctx->stream>>>(
         t->st, n, t->perm, t->sys_box, ps->d_sys, ps->x[c], ps->y[c], ps->z[c], ps->vx[c], ps->vy[c], ps->vz[c],
         ps->m[c], ps->eps[c], ps->id[c], ps->x[o], ps->y[o], ps->z[o], ps->vx[o], ps->vy[o],
-        ps->vz[o], ps->m[o], ps->eps[o], ps->id[o], t->pf_hi, t->pf_lo);
+        ps->vz[o], ps->m[o], ps->eps[o], ps->id[o], t->pf_hi, t->pf_lo, t->pmx, t->pmy, t->pmz);
     FDPS_LAUNCH_CHECK(ctx);
     ps->cur = o;
     return FDPS_OK;
