@@ -79,6 +79,8 @@ def parse():
                     help="one JSON line per workload configuration: Plummer 2^20 (10 steps), "
                          "Hernquist 2^24 at theta 0.3/0.5/0.7, clumpy 2^26; with force errors "
                          "against the FP64 direct sum on a random subsample and energy drift")
+    ap.add_argument("--no-other", action="store_true",
+                    help="skip the other workload configurations measured after the headline run")
     ap.add_argument("--largest", action="store_true",
                     help="the clumpy mixture at the largest particle count that fits the device "
                          "(one JSON line: throughput, force error, drift, bytes per particle)")
@@ -365,6 +367,88 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def time_run(G, torch, ps, tree, dt, steps, warmup=1):
+    """ms per step of `steps` graph-replayed KDK steps after `warmup`, with
+    the last step's statistics."""
+    stream = torch.cuda.ExternalStream(tree.ctx.stream)
+    tree.calc_force_all_and_write_back(ps)
+    tree.run(ps, dt, warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    tree.run(ps, dt, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, tree.stats()
+
+
+def other_configs(G, torch, main_inputs, args):
+    """The other workload configurations, measured in the same run (one GPU):
+    Hernquist 2^24 at theta 0.3 and 0.7 on the benchmark's own particles,
+    Plummer 2^20, the clumpy mixture at 2^26 and the 4096-cluster ensemble,
+    each with the parameters the autotuner picks for it, timed over a few
+    graph-replayed steps (interactions/s from the last step's count; no
+    accuracy checks here, `--suite` has them)."""
+    import ics
+    out = {}
+
+    def single(name, inputs, theta, n_leaf, n_grp, tile, dt, steps):
+        ctx = G.Context(0)
+        ps = G.ParticleSystem(ctx, len(inputs[0]))
+        tree = G.Tree(ctx, theta=theta, n_leaf=n_leaf, n_grp=n_grp, quad=True, tile_depth=tile)
+        try:
+            ps.set(*inputs)
+            ms, st = time_run(G, torch, ps, tree, dt, steps)
+            inter = st["interactions_epj"] + st["interactions_spj"]
+            out[name] = {"workload": f"N={len(inputs[0])} theta={theta} quad n_leaf={n_leaf} n_grp={n_grp} "
+                                     f"tile={tile} dt={dt:.6g}",
+                         "value": inter / (ms / 1e3), "unit": "interactions/s", "ms_per_step": ms,
+                         "steps": steps, "interactions_per_step": inter}
+        finally:
+            tree.close()
+            ps.close()
+            ctx.close()
+
+    jobs = [("hernquist16m-theta0.3", lambda: single("hernquist16m-theta0.3", main_inputs, 0.3, 16, 256, 512,
+                                                      1.0 / 512.0, 3)),
+            ("hernquist16m-theta0.7", lambda: single("hernquist16m-theta0.7", main_inputs, 0.7, 16, 256, 512,
+                                                      1.0 / 512.0, 5)),
+            ("plummer1m", lambda: single("plummer1m", ics.make_config("plummer1m"), 0.5, 16, 128, 0,
+                                         1.0 / 256.0, 10)),
+            ("clumpy64m", lambda: single("clumpy64m", ics.make_config("clumpy64m"), 0.5, 16, 256, 512,
+                                         1.0 / 512.0, 2))]
+
+    def ensemble():
+        cfg = ics.CONFIGS["ensemble4096"]
+        pos, vel, mass, eps, off = ics.ensemble(4096, cfg["seed"])
+        ctx = G.Context(0)
+        ps = G.ParticleSystem(ctx, len(pos))
+        tree = G.Tree(ctx, theta=cfg["theta"], n_leaf=8, n_grp=256, tile_depth=512, block=64, i_per_thread=5)
+        try:
+            ps.set_systems(off)
+            ps.set(pos, vel, mass, eps)
+            steps = 10
+            ms, st = time_run(G, torch, ps, tree, cfg["dt"], steps, warmup=3)
+            out["ensemble4096"] = {"workload": f"4096 Plummer clusters, N log-uniform [256, 65536] (total "
+                                               f"{len(pos)}), theta 0.5 monopole, n_leaf 8, n_grp 256, "
+                                               f"tile 512, block 64 x 5, dt {cfg['dt']:.6g}",
+                                   "value": 4096 / (ms / 1e3), "unit": "systems*steps/s", "ms_per_step": ms,
+                                   "steps": steps,
+                                   "interactions_per_step": st["interactions_epj"] + st["interactions_spj"]}
+        finally:
+            tree.close()
+            ps.close()
+            ctx.close()
+
+    jobs.append(("ensemble4096", ensemble))
+    for name, job in jobs:
+        try:
+            job()
+        except Exception as e:  # reported in the line; the headline stands on its own
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_1601_03138_gb300 as G
@@ -502,6 +586,10 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(pos, mass, eps, args, args.cpu_seconds)
 
+    other = None
+    if rank == 0 and world == 1 and not args.no_other:
+        other = other_configs(G, torch, (pos, vel, mass, eps), args)
+
     if rank == 0:
         line = {"metric": "particle-interactions/s", "value": value, "unit": "interactions/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -521,7 +609,8 @@ def run_ours(args, rank, world, local_rank):
                              "n_nodes": last["n_nodes"], "n_groups": last["n_groups"],
                              "fp64_fallbacks": last["fp64_fallbacks"]},
                 "interactions_per_s_force_kernel": (inter / args.steps) / statistics.median(
-                    [f / 1e3 for f in force_ms])}
+                    [f / 1e3 for f in force_ms]),
+                "other_configs": other}
         print(json.dumps(line), flush=True)
     tree.close()
     ps.close()
