@@ -267,18 +267,50 @@ def test_set_keeps_the_order_for_the_coherent_sort(G, ctx):
             finally:
                 ftree.close()
                 fresh.close()
-        # device arrays take the same path
+        # device arrays and page-locked host arrays (read by the device over
+        # the link) take the same path
         torch = pytest.importorskip("torch")
-        pos4 = new[0] + new[1] / 256.0
-        dev = [torch.tensor(a, device="cuda", dtype=torch.float64).contiguous()
-               for a in (pos4, new[1], new[2], new[3])]
-        torch.cuda.synchronize()
-        ps.set(*dev)
+        dev = lambda a: torch.tensor(a, device="cuda", dtype=torch.float64).contiguous()
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        pos4 = new[0]
+        for wrap in (dev, pin):
+            pos4 = pos4 + new[1] / 256.0
+            args = [wrap(a) for a in (pos4, new[1], new[2], new[3])]
+            torch.cuda.synchronize()
+            ps.set(*args)
+            tree.calc_force_all_and_write_back(ps)
+            assert tree.stats()["sort_coherent"] == 1
+            p, _, acc, pot = ps.get()
+            np.testing.assert_array_equal(p, pos4)
+            fresh, ftree = _setup(G, ctx, pos4, new[1], new[2], new[3], quad=True)
+            try:
+                _, _, acc_f, pot_f = fresh.get()
+                np.testing.assert_array_equal(acc, acc_f)
+                np.testing.assert_array_equal(pot, pot_f)
+            finally:
+                ftree.close()
+                fresh.close()
+    finally:
+        tree.close()
+        ps.close()
+
+
+@pytest.mark.parametrize("n", [1, 2, 5])
+def test_set_twice_on_tiny_systems(G, ctx, n):
+    """Systems too small for the coherent sort: a second set still keeps the
+    order, and the results equal a fresh system's."""
+    rng = np.random.default_rng(ics.SEED_BASE + 69 + n)
+    pos, vel = rng.normal(size=(n, 3)), rng.normal(size=(n, 3))
+    mass, eps = rng.uniform(0.5, 1.5, n), np.full(n, 0.05)
+    ps, tree = _setup(G, ctx, pos, vel, mass, eps, quad=True)
+    try:
+        pos2 = pos[::-1].copy()
+        ps.set(pos2, vel, mass, eps)
         tree.calc_force_all_and_write_back(ps)
-        assert tree.stats()["sort_coherent"] == 1
-        p, _, acc, pot = ps.get()
-        np.testing.assert_array_equal(p, pos4)
-        fresh, ftree = _setup(G, ctx, pos4, new[1], new[2], new[3], quad=True)
+        p, v, acc, pot = ps.get()
+        np.testing.assert_array_equal(p, pos2)
+        np.testing.assert_array_equal(v, vel)
+        fresh, ftree = _setup(G, ctx, pos2, vel, mass, eps, quad=True)
         try:
             _, _, acc_f, pot_f = fresh.get()
             np.testing.assert_array_equal(acc, acc_f)
