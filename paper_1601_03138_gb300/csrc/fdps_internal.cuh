@@ -90,12 +90,21 @@ struct DevState {
 // the 29 dropped bits, as an integer) converted by one correctly rounded
 // int-to-float conversion and scaled by a power of two.  Values whose parts
 // would leave the FP32 normal range take the FP64 instructions.
+// The FP64 instructions for the rare values outside the integer path's
+// exponent range, in a function of their own: inlined, the compiler may
+// predicate them into the common path, where they would still take their
+// cycles on the narrow FP64 pipe.
+static __device__ __noinline__ float2 split_f32_fp64(double v) {
+    const float hi = __double2float_rn(v);
+    return make_float2(hi, __double2float_rn(v - (double)hi));
+}
 __device__ __forceinline__ void split_f32(double v, float& hi, float& lo) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     const int e = (int)((b >> 52) & 0x7FF);
     if (e < 949 || e > 1149) {
-        hi = __double2float_rn(v);
-        lo = __double2float_rn(v - (double)hi);
+        const float2 r = split_f32_fp64(v);
+        hi = r.x;
+        lo = r.y;
         return;
     }
     const unsigned long long sig = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
