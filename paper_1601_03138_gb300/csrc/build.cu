@@ -791,14 +791,6 @@ __device__ __forceinline__ double unord64(unsigned long long o) {
     unsigned long long u = (o >> 63) ? (o & 0x7FFFFFFFFFFFFFFFull) : ~o;
     return __longlong_as_double((long long)u);
 }
-__device__ __forceinline__ uint32_t quantise(double x, double lo, double s) {
-    double t = __dsub_rn(x, lo);
-    double u = __dmul_rn(t, s);
-    double f = floor(u);
-    f = f > (double)kQMax ? (double)kQMax : f;
-    f = f < 0.0 ? 0.0 : f;
-    return (uint32_t)f;
-}
 
 // FP64 box of each group (min / max over its particles), its grid box (the
 // quantised corners: quantisation is monotone, so these are the minimum and

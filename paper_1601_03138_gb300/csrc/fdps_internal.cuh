@@ -127,6 +127,23 @@ __device__ __forceinline__ void split_f32(double v, float& hi, float& lo) {
     const float p2 = __uint_as_float((unsigned int)(e - 1075 + 127) << 23);
     lo = __uint_as_float(__float_as_uint(__fmul_rn(__int2float_rn(diff), p2)) ^ sgn);
 }
+// Grid coordinate of x (Sect. 3.2's key reading): q = min(2^21 - 1,
+// floor((x - lo) s)) with the subtraction and the product rounded on their
+// own.
+__device__ __forceinline__ uint32_t quantise(double x, double lo, double s) {
+    const double u = __dmul_rn(__dsub_rn(x, lo), s);
+    // min(2^21 - 1, max(0, floor(u))) from the bits of u, on the integer
+    // pipes (the FP64 pipe is narrow): u <= 0 or u < 1 give 0, u >= 2^21
+    // the clamp, otherwise the significand shifted right by 52 - (e - 1023)
+    const long long b = __double_as_longlong(u);
+    if (b <= 0) return 0;  // +0, or negative (sign bit set)
+    const int e = (int)(b >> 52);
+    if (e < 1023) return 0;
+    if (e >= 1023 + 21) return kQMax;
+    const unsigned long long m = ((unsigned long long)b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    return (uint32_t)(m >> (52 - (e - 1023)));
+}
+
 __device__ __forceinline__ float to_f32(double v) {
     float hi, lo;
     split_f32(v, hi, lo);

@@ -208,13 +208,6 @@ __global__ void __launch_bounds__(256) k_box_seg(const int64_t* __restrict__ off
     }
 }
 
-__device__ __forceinline__ uint32_t quantise(double x, double lo, double s) {
-    const double u = __dmul_rn(__dsub_rn(x, lo), s);
-    // floor as a conversion rounding down (saturating), then the clamp in
-    // integers: the same value as flooring and clamping in FP64
-    const int f = __double2int_rd(u);
-    return (uint32_t)min(max(f, 0), (int)kQMax);
-}
 
 // Spread the low 21 bits of v to every third bit (bit b -> bit 3b).
 __device__ __forceinline__ uint64_t spread3(uint32_t v) {

@@ -1,8 +1,9 @@
-"""The FP64 -> FP32 hi/lo split and the centre-of-mass quotient of the
-moments kernels, restated on the CPU in exact arithmetic and checked
-against their definitions: hi = RN32(v), lo = RN32(v - hi) (numpy's
-float32 rounding), and RN(S / M) (the correctly rounded quotient of the
-exact rationals).  CPU only."""
+"""The FP64 -> FP32 hi/lo split, the centre-of-mass quotient of the
+moments kernels and the grid quantisation's floor, restated on the CPU in
+exact arithmetic and checked against their definitions: hi = RN32(v), lo =
+RN32(v - hi) (numpy's float32 rounding), RN(S / M) (the correctly rounded
+quotient of the exact rationals), and min(2^21 - 1, max(0, floor(u))).
+CPU only."""
 import struct
 from fractions import Fraction
 
@@ -113,3 +114,50 @@ def test_quotient_without_the_correction_step_is_caught():
         q0 = float(Fraction(S) * Fraction(y))
         wrong += q0 != float(Fraction(S) / Fraction(M))
     assert wrong > 0
+
+
+QMAX = (1 << 21) - 1
+
+
+def floor_bits(u):
+    """The kernels' clamped floor of u from its bits (integer operations)."""
+    b = bits(u)
+    if b >= 1 << 63 or b == 0:  # negative (sign bit set) or +0
+        return 0
+    e = b >> 52
+    if e < 1023:
+        return 0
+    if e >= 1023 + 21:
+        return QMAX
+    m = (b & ((1 << 52) - 1)) | (1 << 52)
+    return m >> (52 - (e - 1023))
+
+
+def test_quantisation_floor_from_bits_equals_clamped_floor():
+    rng = np.random.default_rng(1601)
+    vals = [0.0, -0.0, 5e-324, 1e-300, 0.5, 1.0, np.nextafter(1.0, 0.0), np.nextafter(1.0, 2.0),
+            float(QMAX), np.nextafter(float(QMAX), 0.0), float(QMAX) + 0.5, np.nextafter(2.0 ** 21, 0.0),
+            2.0 ** 21, 2.0 ** 21 + 1.0, 1e300, float("inf"), -1.0, -1e-300, -2.0 ** 22]
+    ints = rng.integers(0, 1 << 21, 2000).astype(float)
+    vals += list(ints) + [np.nextafter(v, 0.0) for v in ints] + [np.nextafter(v, np.inf) for v in ints]
+    vals += list(rng.uniform(-10.0, 2.0 ** 21 + 10.0, 4000)) + list(2.0 ** rng.uniform(-60, 30, 2000))
+    for u in vals:
+        want = 0 if u < 1.0 else (QMAX if u >= 2.0 ** 21 else int(Fraction(u)) // 1)
+        assert floor_bits(float(u)) == want, u
+
+
+def test_quantisation_floor_planted_mistake_is_caught():
+    """An off-by-one shift (the exponent bias taken as 1022) fails the
+    definition: the check is not vacuous."""
+    def wrong(u):
+        b = bits(u)
+        if b >= 1 << 63 or b == 0:
+            return 0
+        e = b >> 52
+        if e < 1023:
+            return 0
+        if e >= 1023 + 21:
+            return QMAX
+        m = (b & ((1 << 52) - 1)) | (1 << 52)
+        return m >> (52 - (e - 1022))
+    assert any(wrong(u) != min(QMAX, int(u)) for u in (1.0, 3.5, 1000.25))
