@@ -264,9 +264,13 @@ __device__ __forceinline__ float wendland_c6(float r, float invH) {
     return kWc6 * invH * invH * invH * u8 * poly;
 }
 
-__global__ void __launch_bounds__(kSBlock) k_short_pairs(ShortPairArgs A) {
+// MODE is the cutoff type (FDPS_CUTOFF_*), fixed at compile time so that
+// the pair loop carries no selection between them.
+template <int MODE>
+__global__ void __launch_bounds__(kSBlock, 8) k_short_pairs(ShortPairArgs A) {
     __shared__ float4 s_h[kSW][kSTile];
     __shared__ float4 s_l[kSW][kSTile];
+    __shared__ float s_ih[kSW][kSTile];  // 1 / h_j (scatter and symmetric types)
     __shared__ uint32_t s_p[kSW][kSTile];
     __shared__ uint32_t s_first[kSW][32];
     __shared__ uint32_t s_start[kSW][32];
@@ -294,9 +298,11 @@ __global__ void __launch_bounds__(kSBlock) k_short_pairs(ShortPairArgs A) {
             const bool act = sl < nsl && i < ni;
             const uint32_t pi = gf + (act ? i : 0u);
             const float4 ih = A.pf_hi[pi], il = A.pf_lo[pi];
-            const double hi64 = A.h ? A.h[pi] : A.r_fixed;
+            const double hi64 = MODE != 0 ? A.h[pi] : A.r_fixed;
             const float hif = (float)hi64;
-            const float invHi = 1.0f / (A.mode == 0 ? (float)A.r_fixed : hif);
+            const float invHi = 1.0f / (MODE == 0 ? (float)A.r_fixed : hif);
+            // the cutoff of the fixed and gather types is the lane's own
+            const float ci = MODE == 0 ? (float)A.r_fixed : hif, ci2 = ci * ci;
             uint32_t cnt = 0, cands = 0, fbk = 0;
             float sum = 0.0f;
             for (uint32_t base = 0; base < len; base += 32) {
@@ -325,8 +331,10 @@ __global__ void __launch_bounds__(kSBlock) k_short_pairs(ShortPairArgs A) {
                             if (s_start[w][src + step] <= item) src += step;
                         const uint32_t pj = s_first[w][src] + (item - s_start[w][src]);
                         const float4 lo = A.pf_lo[pj];
+                        const float hj = MODE >= 2 ? (float)A.h[pj] : 0.0f;
                         s_h[w][k] = A.pf_hi[pj];
-                        s_l[w][k] = make_float4(lo.x, lo.y, lo.z, A.h ? (float)A.h[pj] : 0.0f);
+                        s_l[w][k] = make_float4(lo.x, lo.y, lo.z, hj);
+                        if (MODE >= 2) s_ih[w][k] = 1.0f / hj;
                         s_p[w][k] = pj;
                     }
                     __syncwarp();
@@ -339,11 +347,9 @@ __global__ void __launch_bounds__(kSBlock) k_short_pairs(ShortPairArgs A) {
                             const float dy = (jh.y - ih.y) + (jl.y - il.y);
                             const float dz = (jh.z - ih.z) + (jl.z - il.z);
                             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                            const float cf = A.mode == 0 ? (float)A.r_fixed
-                                           : A.mode == 1 ? hif
-                                           : A.mode == 2 ? jl.w
-                                                         : fmaxf(hif, jl.w);
-                            const float c2 = cf * cf;
+                            float c2 = ci2;
+                            if (MODE == 2) c2 = jl.w * jl.w;
+                            if (MODE == 3) c2 = fmaxf(hif, jl.w) * fmaxf(hif, jl.w);
                             const float a = fmaxf(fmaxf(fabsf(dx), fabsf(dy)), fabsf(dz));
                             const float Ea = 8.0f * kU * a + Eabs;
                             const float M = 8.0f * kU * (r2 + c2) + 6.0f * a * Ea + 3.0f * Ea * Ea;
@@ -360,21 +366,21 @@ __global__ void __launch_bounds__(kSBlock) k_short_pairs(ShortPairArgs A) {
                                 const double ez = __dsub_rn(A.z[pj], A.z[pi]);
                                 const double e2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)),
                                                             __dmul_rn(ez, ez));
-                                const double hj64 = A.h ? A.h[pj] : A.r_fixed;
-                                const double cc = A.mode == 0 ? A.r_fixed
-                                                : A.mode == 1 ? hi64
-                                                : A.mode == 2 ? hj64
-                                                              : (hi64 > hj64 ? hi64 : hj64);
+                                const double hj64 = MODE != 0 ? A.h[pj] : A.r_fixed;
+                                const double cc = MODE == 0 ? A.r_fixed
+                                                : MODE == 1 ? hi64
+                                                : MODE == 2 ? hj64
+                                                            : (hi64 > hj64 ? hi64 : hj64);
                                 nb = e2 < __dmul_rn(cc, cc);
                             }
                             if (nb) {
                                 ++cnt;
                                 const float r = sqrtf(r2);
                                 float wk;
-                                if (A.mode == 3)
-                                    wk = 0.5f * (wendland_c6(r, invHi) + wendland_c6(r, 1.0f / jl.w));
-                                else if (A.mode == 2)
-                                    wk = wendland_c6(r, 1.0f / jl.w);
+                                if (MODE == 3)
+                                    wk = 0.5f * (wendland_c6(r, invHi) + wendland_c6(r, s_ih[w][k]));
+                                else if (MODE == 2)
+                                    wk = wendland_c6(r, s_ih[w][k]);
                                 else
                                     wk = wendland_c6(r, invHi);
                                 sum = fmaf(jh.w, wk, sum);
@@ -527,11 +533,12 @@ int launch_short_pairs(fdps_tree* t, fdps_psys* ps, int mode, double r_fixed, ui
     A.info = info3;
     A.mode = mode;
     A.r_fixed = r_fixed;
+    void (*kern)(ShortPairArgs) = mode == 0 ? k_short_pairs<0> : mode == 1 ? k_short_pairs<1>
+                                : mode == 2 ? k_short_pairs<2> : k_short_pairs<3>;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_short_pairs, kSBlock, 0) != cudaSuccess ||
-        per_sm < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSBlock, 0) != cudaSuccess || per_sm < 1)
         per_sm = 4;
-    k_short_pairs<<<per_sm * ctx->sm_count, kSBlock, 0, ctx->stream>>>(A);
+    kern<<<per_sm * ctx->sm_count, kSBlock, 0, ctx->stream>>>(A);
     FDPS_LAUNCH_CHECK(ctx);
     return FDPS_OK;
 }
