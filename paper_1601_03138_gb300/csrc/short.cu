@@ -301,8 +301,25 @@ __global__ void __launch_bounds__(kSBlock, 8) k_short_pairs(ShortPairArgs A) {
             const double hi64 = MODE != 0 ? A.h[pi] : A.r_fixed;
             const float hif = (float)hi64;
             const float invHi = 1.0f / (MODE == 0 ? (float)A.r_fixed : hif);
-            // the cutoff of the fixed and gather types is the lane's own
+            // the cutoff of the fixed and gather types is the lane's own, and
+            // so are two thresholds on r^2 that decide every pair the pair
+            // bound below decides on the same side: M <= Mmax for r^2 <= c^2
+            // (a <= r <= c), and for r^2 > c^2, with a <= r <= (r^2 + c^2) /
+            // (2c), M <= (56u + 192u^2 + beta) r^2 + (8u + beta) c^2 + 3 Eabs^2,
+            // beta = 3 Eabs / c (slack for the FP32 evaluation of both); a
+            // cutoff within a few Eabs sends every pair to the FP64 sequence
             const float ci = MODE == 0 ? (float)A.r_fixed : hif, ci2 = ci * ci;
+            float lo_thr = -INFINITY, hi_thr = INFINITY;
+            if (MODE <= 1) {
+                const float beta = 3.0001f * Eabs / ci;
+                if (beta < 0.25f) {
+                    const float tq = fmaf(8.0f * kU, ci, Eabs);
+                    const float Mmax = 64.0f * kU * ci2 + 6.0f * ci * Eabs + 3.0f * tq * tq;
+                    lo_thr = ci2 - (1.01f * Mmax + 4.0f * kU * ci2);
+                    hi_thr = (ci2 * (1.0f + 8.0f * kU + beta) + 3.0f * Eabs * Eabs) * (1.0f + 16.0f * kU) /
+                             (1.0f - (56.0f * kU + 192.0f * kU * kU + beta));
+                }
+            }
             uint32_t cnt = 0, cands = 0, fbk = 0;
             float sum = 0.0f;
             for (uint32_t base = 0; base < len; base += 32) {
@@ -347,18 +364,20 @@ __global__ void __launch_bounds__(kSBlock, 8) k_short_pairs(ShortPairArgs A) {
                             const float dy = (jh.y - ih.y) + (jl.y - il.y);
                             const float dz = (jh.z - ih.z) + (jl.z - il.z);
                             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                            float c2 = ci2;
-                            if (MODE == 2) c2 = jl.w * jl.w;
-                            if (MODE == 3) c2 = fmaxf(hif, jl.w) * fmaxf(hif, jl.w);
-                            const float a = fmaxf(fmaxf(fabsf(dx), fabsf(dy)), fabsf(dz));
-                            const float Ea = 8.0f * kU * a + Eabs;
-                            const float M = 8.0f * kU * (r2 + c2) + 6.0f * a * Ea + 3.0f * Ea * Ea;
-                            bool nb;
-                            if (r2 < c2 - M) {
-                                nb = true;
-                            } else if (r2 > c2 + M) {
-                                nb = false;
-                            } else {  // the exact FP64 sequence
+                            bool near;  // inside the bound: the FP64 sequence decides
+                            bool nb = false;
+                            if (MODE <= 1) {
+                                nb = r2 < lo_thr;
+                                near = !nb && !(r2 > hi_thr);
+                            } else {
+                                const float c2 = MODE == 2 ? jl.w * jl.w : fmaxf(hif, jl.w) * fmaxf(hif, jl.w);
+                                const float a = fmaxf(fmaxf(fabsf(dx), fabsf(dy)), fabsf(dz));
+                                const float Ea = 8.0f * kU * a + Eabs;
+                                const float M = 8.0f * kU * (r2 + c2) + 6.0f * a * Ea + 3.0f * Ea * Ea;
+                                nb = r2 < c2 - M;
+                                near = !nb && !(r2 > c2 + M);
+                            }
+                            if (near) {  // the exact FP64 sequence
                                 ++fbk;
                                 const uint32_t pj = s_p[w][k];
                                 const double ex = __dsub_rn(A.x[pj], A.x[pi]);
