@@ -103,9 +103,9 @@ __device__ __forceinline__ WalkState walk_state_init() {
 
 
 // The list of group g, walked by the calling warp (all 32 lanes), with its
-// two frontier buffers fa and fb.
+// two frontier buffers fa and fb and the warp's per-level thresholds thr.
 __device__ __forceinline__ void walk_group(const WalkArgs& A, uint32_t g, uint32_t* fa, uint32_t* fb,
-                                           WalkState& S) {
+                                           float2* thr, WalkState& S) {
     DevState* st = A.st;
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
@@ -134,6 +134,34 @@ __device__ __forceinline__ void walk_group(const WalkArgs& A, uint32_t g, uint32
     const float e0 = 1e-13f * Lf;
     const float mc1 = 1.01f * A.theta2f * 25.0f * kU32, mc2 = 1.01f * A.theta2f * 7.0f * e0,
                 mc3 = 1.01f * A.theta2f * 4.0f * e0 * e0;
+    // The bound's largest value over the cells each side can decide, as two
+    // thresholds on d^2 per level (lane = level): a cell with d^2 <= D0^2 =
+    // ell^2 / theta^2 has M <= D0 + 2 hb (|d_a| <= t_a + hb), so the margin
+    // is at most Mo and d^2 < (ell^2 - Mo) / theta^2 opens it; beyond D0,
+    // with (s + 2 hb)^2 <= 2 s^2 + 8 hb^2 and s = |t| <= (d^2 + D0^2) / (2 D0),
+    // the margin is linear in d^2 and d^2 above hi rejects it.  Slack covers
+    // the thresholds' own FP32 evaluation; outside the filter's range of L
+    // (and at theta = 0, where every cell opens) no threshold decides.
+    __syncwarp();  // the previous group's walk has read thr
+    if (lane <= kMaxLevel) {
+        float lo = -INFINITY, hi = INFINITY;
+        if (!filt) {
+        } else if (A.theta2f == 0.0f) {
+            lo = INFINITY;
+        } else {
+            const float ell = __int_as_float(__float_as_int(Lf) - (lane << 23));
+            const float l2 = ell * ell;
+            const float D0 = sqrtf(l2 / A.theta2f);
+            const float Mb = D0 + 2.0f * hb;
+            const float Mo = fmaf(16.0f * kU32, l2, fmaf(fmaf(mc1, Mb, mc2), Mb, mc3));
+            lo = (l2 - Mo) / A.theta2f * (1.0f - 8.0f * kU32);
+            const float coef = A.theta2f - (8.0f * kU32 * A.theta2f + 2.0f * mc1 + mc2 / (2.0f * D0));
+            const float rhs = l2 * (1.0f + 8.0f * kU32) + 8.0f * mc1 * hb * hb + mc2 * (0.5f * D0 + 2.0f * hb) + mc3;
+            if (coef > 0.0f) hi = rhs * (1.0f + 16.0f * kU32) / coef;
+        }
+        thr[lane] = make_float2(lo, hi);
+    }
+    __syncwarp();
 
     if (S.ovf) {  // counting only: keep the in-chunk cursor small
         S.cbase += S.coff;
@@ -192,17 +220,10 @@ __device__ __forceinline__ void walk_group(const WalkArgs& A, uint32_t g, uint32
                     const float ty = fmaxf(fmaxf(blo.y - dy, dy - bhi.y), 0.0f);
                     const float tz = fmaxf(fmaxf(blo.z - dz, dz - bhi.z), 0.0f);
                     const float d2 = tx * tx + ty * ty + tz * tz;
-                    // L 2^-level, exact: an exponent decrement of the normal FP32 L
-                    const float ell = __int_as_float(__float_as_int(Lf) - (level << 23));
-                    const float l2 = ell * ell;
-                    const float r2 = A.theta2f * d2;
-                    const float T = l2 - r2;
-                    // bound on |T - (ell^2 - theta^2 D^2)|, D the exact distance
-                    const float M = fmaxf(fmaxf(fabsf(dx), fabsf(dy)), fabsf(dz)) + hb;
-                    const float margin = fmaf(8.0f * kU32, l2 + r2, fmaf(fmaf(mc1, M, mc2), M, mc3));
-                    if (filt && T > margin) {
+                    const float2 th = thr[level];
+                    if (d2 < th.x) {
                         open = true;
-                    } else if (filt && T < -margin) {
+                    } else if (d2 > th.y) {
                         open = false;
                     } else {
                         open = open_fp64(L, level, A.theta2, A.nd_com[node], box64);
@@ -323,13 +344,14 @@ __global__ void __launch_bounds__(kWalkBlock, 8) k_walk(WalkArgs A) {
     uint32_t* fa = A.frontier + wid * 2 * (int64_t)A.cap_frontier;
     uint32_t* fb = fa + A.cap_frontier;
     const uint32_t ngroups = (uint32_t)st->n_groups;
+    __shared__ float2 s_thr[kWalkBlock / 32][kMaxLevel + 1];
     WalkState S = walk_state_init();
     for (;;) {
         uint32_t g = 0;
         if (lane == 0) g = atomicAdd(&st->walk_counter, 1u);
         g = __shfl_sync(0xFFFFFFFFu, g, 0);
         if (g >= ngroups) break;
-        walk_group(A, g, fa, fb, S);
+        walk_group(A, g, fa, fb, s_thr[threadIdx.x >> 5], S);
     }
     walk_flush(A, S);
 }

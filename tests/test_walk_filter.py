@@ -129,3 +129,84 @@ def test_filter_with_a_shrunk_bound_contradicts_the_fp64_test():
         if got >= 0 and bool(got) != open_fp64(L, level, theta2, com, box):
             wrong += 1
     assert wrong > 0
+
+
+def level_thresholds(L, level, theta2, box, c0, shrink=1.0):
+    """The walk's per-level thresholds on d^2 for one group (the margin's
+    largest value over the cells each side can decide), in FP32 as the
+    kernel evaluates them: d^2 < lo opens, d^2 > hi rejects."""
+    cc = [(box[a] + box[3 + a]) * 0.5 for a in range(3)]
+    blo = [round_down(box[a] - cc[a]) for a in range(3)]
+    bhi = [round_up(box[3 + a] - cc[a]) for a in range(3)]
+    hb = max(-blo[0], -blo[1], -blo[2], bhi[0], bhi[1], bhi[2])
+    theta2f, Lf = f32(theta2), f32(L)
+    e0 = f32(1e-13) * Lf
+    mc1 = f32(1.01) * theta2f * f32(25.0) * U
+    mc2 = f32(1.01) * theta2f * f32(7.0) * e0
+    mc3 = f32(1.01) * theta2f * f32(4.0) * e0 * e0
+    if theta2f == 0:
+        return f32(np.inf), f32(np.inf)
+    ell = f32(np.ldexp(Lf, -level))
+    l2 = ell * ell
+    D02 = l2 / theta2f
+    D0 = f32(np.sqrt(D02))
+    Mb = D0 + f32(2.0) * hb
+    Mo = f32(16.0) * U * l2 + fma32(fma32(mc1, Mb, mc2), Mb, mc3)
+    lo = (l2 - Mo * f32(shrink)) / theta2f * (f32(1.0) - f32(8.0) * U)
+    coef = theta2f - (f32(8.0) * U * theta2f + f32(2.0) * mc1 + mc2 / (f32(2.0) * D0)) * f32(shrink)
+    rhs = (l2 * (f32(1.0) + f32(8.0) * U * f32(shrink))
+           + (f32(8.0) * mc1 * hb * hb + mc2 * (f32(0.5) * D0 + f32(2.0) * hb) + mc3) * f32(shrink))
+    hi = rhs * (f32(1.0) + f32(16.0) * U) / coef if coef > 0 else f32(np.inf)
+    return lo, hi
+
+
+def filter_thr(L, level, theta2, com, box, c0, fused, shrink=1.0):
+    cc = [(box[a] + box[3 + a]) * 0.5 for a in range(3)]
+    gc = [split(cc[a] - c0[a]) for a in range(3)]
+    blo = [round_down(box[a] - cc[a]) for a in range(3)]
+    bhi = [round_up(box[3 + a] - cc[a]) for a in range(3)]
+    fc = [split(com[a] - c0[a]) for a in range(3)]
+    d = [(fc[a][0] - gc[a][0]) + (fc[a][1] - gc[a][1]) for a in range(3)]
+    t = [max(max(blo[a] - d[a], d[a] - bhi[a]), f32(0.0)) for a in range(3)]
+    if fused:
+        d2 = fma32(t[2], t[2], fma32(t[1], t[1], t[0] * t[0]))
+    else:
+        d2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2]
+    lo, hi = level_thresholds(L, level, theta2, box, c0, shrink)
+    if d2 < lo:
+        return 1
+    if d2 > hi:
+        return 0
+    return -1
+
+
+@pytest.mark.parametrize("fused", [False, True])
+def test_level_thresholds_never_contradict_the_fp64_test(fused):
+    rng = np.random.default_rng(20270 + fused)
+    decided, inside, inside_far = 0, 0, 0
+    for L, level, theta, theta2, c0, box, com, rel, half, dist in _cases(rng, 6000):
+        want = open_fp64(L, level, theta2, com, box)
+        got = filter_thr(L, level, theta2, com, box, c0, fused)
+        if got < 0:
+            inside += 1
+            inside_far += abs(rel) > 1e-5 and half.max() <= dist
+        else:
+            decided += 1
+            assert bool(got) == want, (L, level, theta, rel)
+    assert inside_far == 0
+    assert decided > 0 and inside > 0
+
+
+def test_level_thresholds_shrunk_contradict_the_fp64_test():
+    rng = np.random.default_rng(20272)
+    wrong = 0
+    for L, level, theta, theta2, c0, box, com, rel, half, dist in _cases(rng, 6000):
+        got = filter_thr(L, level, theta2, com, box, c0, False, shrink=1e-3)
+        if got >= 0 and bool(got) != open_fp64(L, level, theta2, com, box):
+            wrong += 1
+    assert wrong > 0
+
+
+def test_level_thresholds_open_everything_at_theta_zero():
+    lo, hi = level_thresholds(1.0, 5, 0.0, np.array([0.1, 0.1, 0.1, 0.2, 0.2, 0.2]), np.zeros(3))
+    assert lo == np.inf and hi == np.inf
