@@ -41,6 +41,10 @@ OPS_SPJ_QUAD = 32
 # superparticle (the paper's cost ratio of a quadrupole to a monopole term,
 # Sect. 5.5); the roofline fraction on this count is reported beside the
 # instruction count's.
+# Short-range mode (algorithmic FP32 operations): a candidate pair's r^2
+# and comparison, a neighbour's Wendland C6 term and sum.
+OPS_SR_CAND = 7
+OPS_SR_NB = 10
 ALG_EPJ = 13
 ALG_SPJ_MONO = 13
 ALG_SPJ_QUAD = 26
@@ -813,6 +817,7 @@ def run_sph(args):
     mass = np.full(n, 1.0 / n)
     hval = 4.2 * n ** (-1.0 / 3.0)
     ctx = G.Context(0)
+    ctx.set_profiling(True)
     ps = G.ParticleSystem(ctx, n)
     tree = G.Tree(ctx, theta=0.5, n_leaf=args.n_leaf, n_grp=args.n_grp)
     ps.set(pos, np.zeros_like(pos), mass, np.full(n, 1e-3))
@@ -826,6 +831,22 @@ def run_sph(args):
         cnt, rho, info = tree.neighbors(ps, G.FDPS_CUTOFF_I, h)
         ts.append(time.perf_counter() - t0)
     t = statistics.median(ts)
+    st = tree.stats()  # stage times of the last call: ms_walk, ms_force = the pair pass
+    # the pair pass against the FP32 peak: per candidate pair r^2 and the
+    # comparison on plain FP32 coordinates (3 subtractions, 3 multiply-adds,
+    # 1 compare), per neighbour the Wendland C6 term and its sum (q = r/H,
+    # 1 - q, three squarings, three multiply-adds of the polynomial, the
+    # product with the normalisation and the mass-weighted sum: 10), plus a
+    # square root on the special-function unit
+    pk, pk_kind = peaks()
+    sm_count = torch.cuda.get_device_properties(0).multi_processor_count
+    peak_ops = sm_count * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6
+    alg = OPS_SR_CAND * float(info[1]) + OPS_SR_NB * float(info[0])
+    t_pair = st["ms_force"] / 1e3
+    roofline = {"bound": "alu", "kernel": "k_short_pairs", "achieved": alg / t_pair / 1e12,
+                "peak": peak_ops / 1e12, "unit": "TFLOP/s", "frac": alg / t_pair / peak_ops,
+                "ops_per_candidate": OPS_SR_CAND, "ops_per_neighbour": OPS_SR_NB,
+                "peak_source": f"{sm_count} SMs x 128 FP32 lanes x sm_max_mhz of {pk_kind} peaks"}
     inner = np.all((pos > hval) & (pos < 1.0 - hval), axis=1)
     line = {"metric": "SPH density neighbour pairs/s", "value": float(info[0]) / t, "unit": "pairs/s",
             "workload": f"uniform cube N={n}, h = 4.2 N^-1/3, i-dependent cutoff, Wendland C6, "
@@ -834,7 +855,10 @@ def run_sph(args):
             "neighbours_mean": float(info[0]) / n, "candidates_per_neighbour": float(info[1]) / float(info[0]),
             "fp64_decisions": int(info[2]),
             "density_interior_mean": float(rho[inner].mean()), "density_interior_std": float(rho[inner].std()),
-            "counts_min_max": [int(cnt.min()), int(cnt.max())]}
+            "counts_min_max": [int(cnt.min()), int(cnt.max())],
+            "stages_ms_last_call": {"tree_and_groups": round(st["ms_total"] - st["ms_walk"] - st["ms_force"], 3),
+                                    "walk": round(st["ms_walk"], 3), "pairs": round(st["ms_force"], 3)},
+            "roofline": roofline}
     print(json.dumps(line), flush=True)
     tree.close()
     ps.close()

@@ -124,8 +124,10 @@ typedef struct {
     double ms_build;           /* octree levels */
     double ms_moments;         /* bottom-up moments */
     double ms_groups;          /* i-group selection and boxes */
-    double ms_walk;            /* interaction lists */
-    double ms_force;           /* force kernel */
+    double ms_walk;            /* interaction lists (after fdps_tree_neighbors:
+                                  the radii's preparation and the neighbour walk) */
+    double ms_force;           /* force kernel (after fdps_tree_neighbors: the
+                                  pair pass) */
     double ms_total;
 } fdps_tree_stats;
 

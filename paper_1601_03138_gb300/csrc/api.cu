@@ -882,6 +882,7 @@ int fdps_tree_neighbors(fdps_tree* t, fdps_psys* ps, int32_t mode, double r_fixe
             }
         }
     }
+    record(t, 7);  // stage times: ms_walk = radii preparation + walk, ms_force = pair pass
     if (out_on_device) {
         d_cnt = counts;
         d_rho = rho;
@@ -900,6 +901,7 @@ int fdps_tree_neighbors(fdps_tree* t, fdps_psys* ps, int32_t mode, double r_fixe
         cleanup();
         return rc;
     }
+    record(t, 8);
     unsigned long long hinfo[3] = {0, 0, 0};
     cudaError_t e = cudaMemcpyAsync(hinfo, d_info, sizeof(hinfo), cudaMemcpyDeviceToHost, s);
     if (!out_on_device) {

@@ -135,14 +135,32 @@ __global__ void __launch_bounds__(kSBlock) k_short_walk(ShortWalkArgs A) {
         __syncwarp();
         while (fsize > 0) {
             uint32_t nsize = 0;
+            // node records (and the cells' radii) one batch ahead, frontier
+            // ids two batches ahead, so that no batch waits on a load that
+            // depends on another load
+            uint32_t node_nx = lane < fsize ? fa[lane] : 0u;
+            uint32_t node_nx2 = lane + 32 < fsize ? fa[lane + 32] : 0u;
+            uint4 rec_nx = make_uint4(0, 0, 0, 0);
+            float hc_nx = 0.f;
+            if (lane < fsize) {
+                rec_nx = A.nd_walk[node_nx];
+                if (A.mode >= 2) hc_nx = (float)A.nd_hmax[node_nx];
+            }
             for (uint32_t base = 0; base < fsize; base += 32) {
                 const uint32_t idx = base + lane;
                 const bool act = idx < fsize;
+                const uint32_t node = node_nx;
+                const uint4 rec = rec_nx;
+                const float hc = hc_nx;
+                if (idx + 32 < fsize) {
+                    node_nx = node_nx2;
+                    rec_nx = A.nd_walk[node_nx];
+                    if (A.mode >= 2) hc_nx = (float)A.nd_hmax[node_nx];
+                }
+                if (idx + 64 < fsize) node_nx2 = fa[idx + 64];
                 bool emit = false;
-                uint32_t nch = 0, child = 0, node = 0;
+                uint32_t nch = 0, child = 0;
                 if (act) {
-                    node = fa[idx];
-                    const uint4 rec = A.nd_walk[node];
                     const int level = (int)((rec.x >> 21) & 31u);
                     const bool leaf = (rec.x >> 26) & 1u;
                     const uint32_t w = (1u << (kMaxLevel - level)) - 1u;
@@ -152,7 +170,6 @@ __global__ void __launch_bounds__(kSBlock) k_short_walk(ShortWalkArgs A) {
                     const float gy = (float)max(0, max((int)qy - (int)(qmax1 + 1), (int)qmin1 - (int)(qy + w + 1)));
                     const float gz = (float)max(0, max((int)qz - (int)(qmax2 + 1), (int)qmin2 - (int)(qz + w + 1)));
                     const float d2 = (gx * gx + gy * gy + gz * gz) * dq2;
-                    const float hc = (A.mode >= 2) ? (float)A.nd_hmax[node] : 0.f;
                     const float R = short_bound(A.mode, A.r_fixed, hc, hg);
                     // margin: FP32 rounding of the bound and of the gaps
                     const bool near = d2 <= R * R * (1.0f + 64.0f * kU);
@@ -192,20 +209,22 @@ __global__ void __launch_bounds__(kSBlock) k_short_walk(ShortWalkArgs A) {
                     if (emit && !ovf) A.pool[cursor + __popc(emask & lt)] = node | kLeafTag;
                     cursor += k;
                 }
-                uint32_t inc = nch;
+                if (__ballot_sync(0xFFFFFFFFu, nch > 0u)) {  // deep in the tree most batches open none
+                    uint32_t inc = nch;
 #pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const uint32_t tv = __shfl_up_sync(0xFFFFFFFFu, inc, off);
-                    if (lane >= off) inc += tv;
-                }
-                const uint32_t tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
-                if (nsize + tot > F) {
-                    if (lane == 0) atomicOr(&st->overflow, kOvfFrontier);
-                    ovf = true;
-                } else {
-                    const uint32_t o = nsize + inc - nch;
-                    for (uint32_t c = 0; c < nch; ++c) fb[o + c] = child + c;
-                    nsize += tot;
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const uint32_t tv = __shfl_up_sync(0xFFFFFFFFu, inc, off);
+                        if (lane >= off) inc += tv;
+                    }
+                    const uint32_t tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
+                    if (nsize + tot > F) {
+                        if (lane == 0) atomicOr(&st->overflow, kOvfFrontier);
+                        ovf = true;
+                    } else {
+                        const uint32_t o = nsize + inc - nch;
+                        for (uint32_t c = 0; c < nch; ++c) fb[o + c] = child + c;
+                        nsize += tot;
+                    }
                 }
             }
             __syncwarp();
@@ -484,15 +503,17 @@ int short_prepare(fdps_tree* t, fdps_psys* ps, int mode, const double* h_user) {
         }
         t->cap_g_hmax = t->cap_groups;
     }
-    k_hmax_leaves<<<grid_for(nn, 256, 4 * ctx->sm_count), 256, 0, s>>>(nn, t->nd_meta, t->nd_first, t->nd_count,
-                                                                      t->sr_h, t->nd_hmax);
-    FDPS_LAUNCH_CHECK(ctx);
-    for (int l = t->h_st.max_level - 1; l >= 0; --l) {
-        const int64_t a = t->h_st.lvl_start[l], b = t->h_st.lvl_start[l + 1];
-        if (b <= a) continue;
-        k_hmax_internal<<<grid_for(b - a, 256, 4 * ctx->sm_count), 256, 0, s>>>(a, b, t->nd_meta, t->nd_child,
-                                                                               t->nd_hmax);
+    if (mode >= 2) {  // the cells' largest radii bound the j-dependent cutoffs only
+        k_hmax_leaves<<<grid_for(nn, 256, 4 * ctx->sm_count), 256, 0, s>>>(nn, t->nd_meta, t->nd_first,
+                                                                          t->nd_count, t->sr_h, t->nd_hmax);
         FDPS_LAUNCH_CHECK(ctx);
+        for (int l = t->h_st.max_level - 1; l >= 0; --l) {
+            const int64_t a = t->h_st.lvl_start[l], b = t->h_st.lvl_start[l + 1];
+            if (b <= a) continue;
+            k_hmax_internal<<<grid_for(b - a, 256, 4 * ctx->sm_count), 256, 0, s>>>(a, b, t->nd_meta,
+                                                                                   t->nd_child, t->nd_hmax);
+            FDPS_LAUNCH_CHECK(ctx);
+        }
     }
     k_group_hmax<<<grid_for(ng, 256, 4 * ctx->sm_count), 256, 0, s>>>(ng, t->g_first, t->g_count, t->sr_h,
                                                                       t->g_hmax);
