@@ -275,10 +275,11 @@ struct ShortPairArgs {
     double r_fixed;
 };
 
+// W(r, H) of the 3D Wendland C6 kernel; zero from q = r / H >= 1 on (the
+// factor (1 - q)^8 clamped at zero, without a branch).
 __device__ __forceinline__ float wendland_c6(float r, float invH) {
     const float q = r * invH;
-    if (q >= 1.0f) return 0.0f;
-    const float u = 1.0f - q, u2 = u * u, u4 = u2 * u2, u8 = u4 * u4;
+    const float u = fmaxf(1.0f - q, 0.0f), u2 = u * u, u4 = u2 * u2, u8 = u4 * u4;
     const float poly = fmaf(q, fmaf(q, fmaf(q, 32.0f, 25.0f), 8.0f), 1.0f);
     return kWc6 * invH * invH * invH * u8 * poly;
 }
@@ -411,18 +412,20 @@ __global__ void __launch_bounds__(kSBlock, 8) k_short_pairs(ShortPairArgs A) {
                                                             : (hi64 > hj64 ? hi64 : hj64);
                                 nb = e2 < __dmul_rn(cc, cc);
                             }
-                            if (nb) {
-                                ++cnt;
-                                const float r = sqrtf(r2);
-                                float wk;
-                                if (MODE == 3)
-                                    wk = 0.5f * (wendland_c6(r, invHi) + wendland_c6(r, s_ih[w][k]));
-                                else if (MODE == 2)
-                                    wk = wendland_c6(r, s_ih[w][k]);
-                                else
-                                    wk = wendland_c6(r, invHi);
-                                sum = fmaf(jh.w, wk, sum);
-                            }
+                            // the kernel for every candidate, kept for the
+                            // neighbours only: a third of the pairs are
+                            // neighbours, so a branch would be taken by some
+                            // lane of nearly every step anyway
+                            const float r = sqrtf(r2);
+                            float wk;
+                            if (MODE == 3)
+                                wk = 0.5f * (wendland_c6(r, invHi) + wendland_c6(r, s_ih[w][k]));
+                            else if (MODE == 2)
+                                wk = wendland_c6(r, s_ih[w][k]);
+                            else
+                                wk = wendland_c6(r, invHi);
+                            cnt += nb ? 1u : 0u;
+                            sum = fmaf(jh.w, nb ? wk : 0.0f, sum);
                         }
                     }
                 }
