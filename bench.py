@@ -85,6 +85,9 @@ def parse():
                          "against the FP64 direct sum on a random subsample and energy drift")
     ap.add_argument("--no-other", action="store_true",
                     help="skip the other workload configurations measured after the headline run")
+    ap.add_argument("--user-law", action="store_true",
+                    help="a user interaction law compiled at run time, timed on the benchmark's lists "
+                         "beside the built-in force kernel")
     ap.add_argument("--largest", action="store_true",
                     help="the clumpy mixture at the largest particle count that fits the device "
                          "(one JSON line: throughput, force error, drift, bytes per particle)")
@@ -801,6 +804,110 @@ def run_config(G, torch, name, model, n, eps, theta, quad, n_leaf, n_grp, steps,
     print(json.dumps(line), flush=True)
 
 
+# A user's gravity law, given to the library as source text (the Force and
+# Law structs of include/fdps_user_force.cuh): softened monopole terms for
+# particles, monopole + traceless quadrupole for superparticles.
+USER_GRAVITY_LAW = r"""
+struct Force {
+    float ax, ay, az, pot;
+    __device__ void clear() { ax = ay = az = pot = 0.f; }
+};
+struct Law {
+    __device__ void operator()(const Epi& i, const Epj* j, int nj, Force& f) const {
+        for (int k = 0; k < nj; ++k) {
+            const float dx = j[k].x - i.x, dy = j[k].y - i.y, dz = j[k].z - i.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, i.eps2)));
+            const float ri = rsqrtf(r2);
+            const float mri = j[k].m * ri, mri3 = mri * ri * ri;
+            f.ax = fmaf(mri3, dx, f.ax);
+            f.ay = fmaf(mri3, dy, f.ay);
+            f.az = fmaf(mri3, dz, f.az);
+            f.pot -= mri;
+        }
+    }
+    __device__ void operator()(const Epi& i, const Spj* j, int nj, Force& f) const {
+        for (int k = 0; k < nj; ++k) {
+            const Spj& s = j[k];
+            const float rx = i.x - s.x, ry = i.y - s.y, rz = i.z - s.z;
+            const float R2 = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, i.eps2)));
+            const float Ri = rsqrtf(R2), Ri2 = Ri * Ri, Ri3 = Ri * Ri2, Ri5 = Ri3 * Ri2;
+            const float qx = fmaf(s.qxx, rx, fmaf(s.qxy, ry, s.qxz * rz));
+            const float qy = fmaf(s.qxy, rx, fmaf(s.qyy, ry, s.qyz * rz));
+            const float qz = fmaf(s.qxz, rx, fmaf(s.qyz, ry, s.qzz * rz));
+            const float rqr = fmaf(rx, qx, fmaf(ry, qy, rz * qz));
+            const float c = fmaf(2.5f * rqr * Ri5, Ri2, s.m * Ri3);
+            f.ax += fmaf(qx, Ri5, -c * rx);
+            f.ay += fmaf(qy, Ri5, -c * ry);
+            f.az += fmaf(qz, Ri5, -c * rz);
+            f.pot -= fmaf(0.5f * rqr, Ri5, s.m * Ri);
+        }
+    }
+};
+"""
+
+
+def run_user_law(args):
+    """A user interaction law compiled at run time (NVRTC) through the C ABI,
+    run over the library's own interaction lists of the benchmark workload,
+    timed beside the built-in force kernel on the same lists: ms per launch
+    and interactions/s, and the FP32 roofline fraction on the measurement
+    plan's algorithmic count."""
+    import torch
+    import paper_1601_03138_gb300 as G
+    from paper_1601_03138_gb300 import build as B
+    B.build()
+    pos, vel, mass, eps = make_inputs(args)
+    n = len(pos)
+    ctx = G.Context(0)
+    ctx.set_profiling(True)
+    stream = torch.cuda.ExternalStream(ctx.stream)
+    ps = G.ParticleSystem(ctx, n)
+    tree = G.Tree(ctx, theta=args.theta, n_leaf=args.n_leaf, n_grp=args.n_grp, quad=not args.mono)
+    law = G.UserLaw(ctx, USER_GRAVITY_LAW)
+    try:
+        ps.set(pos, vel, mass, eps)
+        tree.calc_force_all_and_write_back(ps)  # the built-in kernel on these lists
+        st = tree.stats()
+        tree.calc_force_all_and_write_back(ps)
+        st = tree.stats()
+        builtin_ms = st["ms_force"]
+        out = torch.zeros((n, 4), dtype=torch.float32, device="cuda")
+        for _ in range(args.warmup):
+            law.run(tree, ps, out)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            law.run(tree, ps, out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        _, _, acc, _ = ps.get()
+        a_user = out[:, :3].double().cpu().numpy()
+        rel = np.linalg.norm(a_user - acc, axis=1) / np.linalg.norm(acc, axis=1)
+        inter = st["interactions_epj"] + st["interactions_spj"]
+        pk, pk_kind = peaks()
+        sm_count = torch.cuda.get_device_properties(0).multi_processor_count
+        peak_ops = sm_count * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6
+        alg = st["interactions_epj"] * ALG_EPJ + st["interactions_spj"] * (ALG_SPJ_MONO if args.mono else ALG_SPJ_QUAD)
+        line = {"metric": "user-law interactions/s", "value": inter / (ms / 1e3), "unit": "interactions/s",
+                "workload": workload_name(args), "law": "softened gravity, monopole + quadrupole "
+                                                        "superparticles, one i-particle per thread (header template)",
+                "ms_per_launch": ms, "launches": args.steps, "interactions": inter,
+                "builtin_force_ms": builtin_ms, "user_over_builtin": ms / builtin_ms,
+                "roofline": {"bound": "alu", "frac_algorithmic": alg / (ms / 1e3) / peak_ops,
+                             "builtin_frac_algorithmic": alg / (builtin_ms / 1e3) / peak_ops},
+                "acc_rel_vs_builtin": {"median": float(np.median(rel)), "max": float(rel.max())}}
+        print(json.dumps(line), flush=True)
+    finally:
+        law.close()
+        tree.close()
+        ps.close()
+        ctx.close()
+
+
 def run_sph(args):
     """Short-range mode on n particles of a uniform random unit cube with
     radii h_i = 4.2 n^(-1/3) (about 310 neighbours, the paper's SPH cutoff):
@@ -1012,6 +1119,10 @@ def main():
     if args.largest:
         if rank == 0:
             run_largest(args)
+        return
+    if args.user_law:
+        if rank == 0:
+            run_user_law(args)
         return
     if args.theta_target is not None:
         if rank == 0:
